@@ -1,0 +1,362 @@
+"""Benchmark: single-source top-down BFS GTEPS on a seeded Kronecker graph.
+
+Workload (default): Kronecker (R-MAT A/B/C/D = .57/.19/.19/.05) scale 22,
+edgefactor 16, permuted, symmetrised, self-loops and repeats removed; 64
+seeded roots of degree >= 1 (paper Sec. 5.2-5.3: 64 BFS runs from distinct
+roots, TEPS per run, harmonic mean).  One step = one BFS from each of the 64
+roots.  Each BFS is timed with CUDA events on the stream it runs on, with a
+write of a buffer larger than L2 between runs (outside the events).
+
+TEPS of a run = m_cc / t, m_cc = undirected edges with both ends reached
+(half the degree sum over reached vertices), t = device time of the search
+(initialisation included, graph upload excluded).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs an independent replica on its own GPU
+with its own 64 roots ("replicas only": a single search does not shard);
+value = sum of the ranks' harmonic means, timed region = max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "BFS GTEPS (harmonic mean, 64 roots) & batched queries/s, p50/p99 vs plain"
+UNIT = "GTEPS"
+L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--scale", type=int, default=22)
+    ap.add_argument("--edgefactor", type=int, default=16)
+    ap.add_argument("--roots", type=int, default=64)
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--cpu-sample-roots", type=int, default=8)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--option", action="append", default=[],
+                    help="name=value tunable passed to bfs_graph_set_option")
+    return ap.parse_args(argv)
+
+
+def harmonic_mean(xs):
+    xs = [x for x in xs]
+    return len(xs) / sum(1.0 / x for x in xs)
+
+
+def workload_name(scale, ef, roots):
+    return f"kronecker_scale{scale}_ef{ef}_{roots}roots"
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def algorithmic_bytes(deg_reached_sum, n_reached, n):
+    """Minimum DRAM bytes of one search: per reached vertex its adjacency
+    (4 B/entry), its row_offsets pair (8 B) and one frontier id written and
+    read (8 B); per vertex level and parent written once (8 B); the visited
+    bitmap cleared and left behind (n/4 B)."""
+    return 4.0 * deg_reached_sum + 16.0 * n_reached + 8.25 * n
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    QUERY = ("index,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid=None):
+        self.uuid = uuid
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            cmd = ["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits", "-lms", "200"]
+            if self.uuid:
+                cmd += ["-i", self.uuid]
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(cmd, stdout=self.fh, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 10:
+                continue
+            try:
+                sm.append(float(f[2]))
+                smax.append(float(f[3]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[6:10]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        loaded = [s for s in sm if s > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def build_workload(args, rank):
+    import graphgen
+    ro, col = graphgen.kronecker(args.scale, args.edgefactor, args.seed)
+    roots = graphgen.pick_roots(ro, args.roots, args.seed + 1000 * rank)
+    return ro, col, roots
+
+
+def cpu_baseline(ro, col, roots, k):
+    """The oracle (single-threaded C queue BFS) on the host cores, on a
+    bounded sample of the roots."""
+    import oracle
+    deg = np.diff(ro).astype(np.int64)
+    sample = [int(r) for r in roots[:k]]
+    secs = oracle.time_bfs(ro, col, sample)
+    teps = []
+    for r, s in zip(sample, secs):
+        lv, _ = oracle.bfs(ro, col, r, want_parent=False)
+        mcc = deg[lv >= 0].sum() / 2.0
+        teps.append(mcc / s)
+    return {"value": harmonic_mean(teps) / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{len(sample)} of the {len(roots)} roots, same graph, steady clock around each search",
+            "host_cores_available": os.cpu_count(), "seconds": sum(secs)}
+
+
+def run_reference(args):
+    """--impl reference: the oracle timed on the host as the reference arm."""
+    world, rank, local = dist_env()
+    if rank != 0:
+        return 0
+    ro, col, roots = build_workload(args, 0)
+    import oracle
+    deg = np.diff(ro).astype(np.int64)
+    per_step = max(1, min(args.cpu_sample_roots, len(roots)))
+    mcc_cache = {}
+    teps, step_ms = [], []
+    pos = 0
+    for step in range(args.warmup + args.steps):
+        sample = [int(roots[(pos + i) % len(roots)]) for i in range(per_step)]
+        pos += per_step
+        secs = oracle.time_bfs(ro, col, sample)
+        if step < args.warmup:
+            continue
+        for r, s in zip(sample, secs):
+            if r not in mcc_cache:
+                lv, _ = oracle.bfs(ro, col, r, want_parent=False)
+                mcc_cache[r] = deg[lv >= 0].sum() / 2.0
+            teps.append(mcc_cache[r] / s)
+        step_ms.append(1e3 * sum(secs))
+    value = harmonic_mean(teps) / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic",
+        "config": {"workload": workload_name(args.scale, args.edgefactor, args.roots),
+                   "scale": args.scale, "edgefactor": args.edgefactor, "roots": args.roots,
+                   "n": len(ro) - 1, "m_directed": int(len(col)),
+                   "step": f"{per_step} oracle searches (a bounded sample of the {args.roots} roots)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{per_step} roots per step, {args.steps} steps"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_1604_02844_gb300 as gb
+
+    world, rank, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    gb.load()
+
+    ro, col, roots = build_workload(args, rank)
+    n, m = len(ro) - 1, len(col)
+    g = gb.Graph(ro, col)
+    for kv in args.option:
+        k, v = kv.split("=")
+        g.set_option(k, int(v))
+    stream = torch.cuda.current_stream(dev)
+    level = torch.empty(n, dtype=torch.int32, device=dev)
+    parent = torch.empty(n, dtype=torch.int32, device=dev)
+    deg_d = torch.from_numpy(np.diff(ro).astype(np.int64)).to(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+
+    # per-root edge counts (bookkeeping for TEPS, outside any timed region)
+    mcc, bmin = {}, {}
+    for r in roots:
+        g.run(int(r), level, parent)
+        reached = level >= 0
+        dsum = int(deg_d[reached].sum().item())
+        nr = int(reached.sum().item())
+        mcc[int(r)] = dsum / 2.0
+        bmin[int(r)] = algorithmic_bytes(dsum, nr, n)
+    torch.cuda.synchronize()
+    assert g.status() == gb.BFS_OK, gb.last_error()
+
+    def one_step(record):
+        evs = []
+        for r in roots:
+            flush.fill_(1)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            gb.bfs_run(g.handle, int(r), level, parent, stream)
+            e1.record(stream)
+            evs.append((int(r), e0, e1))
+        return evs
+
+    for _ in range(args.warmup):
+        one_step(False)
+    torch.cuda.synchronize()
+
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        uuid = None
+    runs = []
+    with ClockSampler(uuid) as clocks:
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        all_evs = [one_step(True) for _ in range(args.steps)]
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        if world > 1:
+            dist.barrier()
+    assert g.status() == gb.BFS_OK, gb.last_error()
+    for evs in all_evs:
+        for r, e0, e1 in evs:
+            runs.append((r, e0.elapsed_time(e1) * 1e-3))
+    teps = [mcc[r] / t for r, t in runs]
+    hm = harmonic_mean(teps) / 1e9
+    total_dev = sum(t for _, t in runs)
+    step_ms = 1e3 * total_dev / args.steps
+    mean_t = total_dev / len(runs)
+    mean_bytes = statistics.mean(bmin[r] for r, _ in runs)
+    peak, peak_kind = measured_peaks()
+    achieved = mean_bytes / mean_t / 1e9
+
+    # end to end through the C ABI with pinned host outputs
+    e2e = None
+    if not args.no_e2e:
+        lvh = torch.empty(n, dtype=torch.int32).pin_memory()
+        pah = torch.empty(n, dtype=torch.int32).pin_memory()
+        e2e_teps = []
+        for r in roots:
+            flush.fill_(1)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            gb.bfs_run(g.handle, int(r), lvh, pah, stream)
+            stream.synchronize()
+            e2e_teps.append(mcc[int(r)] / (time.perf_counter() - t0))
+        e2e = {"value": harmonic_mean(e2e_teps) / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": 4 * len(roots), "d2h_bytes_per_step": 8 * n * len(roots),
+               "how": "host wall clock around bfs_run with pinned host level/parent outputs + stream sync, per root"}
+
+    # combine ranks: max timed region, sum of per-rank throughput
+    value = hm
+    if world > 1:
+        t = torch.tensor([hm, total_dev], dtype=torch.float64, device=dev)
+        gathered = [torch.zeros_like(t) for _ in range(world)]
+        dist.all_gather(gathered, t)
+        value = sum(float(x[0]) for x in gathered)
+        step_ms = 1e3 * max(float(x[1]) for x in gathered) / args.steps
+
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu_baseline:
+            cpu = cpu_baseline(ro, col, roots, args.cpu_sample_roots)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": workload_name(args.scale, args.edgefactor, args.roots),
+                       "scale": args.scale, "edgefactor": args.edgefactor, "roots": args.roots,
+                       "n": n, "m_directed": m, "seed": args.seed, "parallelism": "replicas",
+                       "l2": "flushed between searches (512 MiB write); col_idx also > L2",
+                       "options": {k: g.get_option(k) for k in gb.OPTION_NAMES}},
+            "teps_stats": {"min": min(teps) / 1e9, "median": statistics.median(teps) / 1e9,
+                           "max": max(teps) / 1e9, "runs": len(teps)},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
+                         "kernel": "td_kernel", "algorithmic_bytes_per_launch": mean_bytes,
+                         "mean_launch_s": mean_t},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": len(runs),
+            "clocks": clocks.summary(),
+            "wall_s_timed": wall,
+        }
+        print(json.dumps(line), flush=True)
+    g.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,214 @@
+/*
+ * gbbfs.h -- C ABI of the GB300 (sm_103a) breadth-first-search library.
+ *
+ * The method is the level-synchronous top-down BFS of Paredes, Riley and
+ * Lujan, "Breadth First Search Vectorization on the Intel Xeon Phi":
+ *   - problem statement (Sec. 3): given a graph G and a source s, explore the
+ *     edges of G to reach every vertex reachable from s; the result is a BFS
+ *     spanning tree given as a predecessor array P with P[s] = s (Alg. 1);
+ *   - layers (Sec. 3): layer L_k holds the vertices at distance k from s;
+ *     L_k is fully processed before L_{k+1}, in any order inside a layer;
+ *   - one layer step (Alg. 2): for every u in the frontier and every v in
+ *     Adj[u], if v is not yet visited, mark it, put it on the next frontier
+ *     and set P[v] = u;
+ *   - the visited set is a bitmap, vertex v at word v/32, bit v%32
+ *     (Sec. 3.3.1, Listing 1).  Where two threads race on one word the paper
+ *     restores the bitmap afterwards (Alg. 3); this library sets bits with a
+ *     32-bit atomic OR instead, so no restoration step exists.
+ *
+ * Graph layout: CSR with int32 row_offsets[n+1] ("colstarts" in Sec. 3.3.1)
+ * and int32 col_idx[m] ("rows"): Adj[u] = col_idx[row_offsets[u] ..
+ * row_offsets[u+1]-1].  Rows are read as directed out-edges; self-loops and
+ * repeated entries are allowed and change nothing.
+ *
+ * Output conventions (readings of the paper, which writes "infinity" for an
+ * unset predecessor, Sec. 3.1):
+ *   level[v]  = number of edges on a shortest path s -> v, -1 if unreached;
+ *   parent[v] = a neighbour u with (u,v) in the CSR and level[u] = level[v]-1
+ *               (any one of them: the race of Sec. 3.2 is benign), parent[s]
+ *               = s, -1 if unreached.
+ * Levels are unique and exact; parents are valid but not unique.
+ *
+ * Errors: functions return a bfs_status (0 = success, negative = error);
+ * functions that return a pointer return NULL on error.  bfs_last_error()
+ * and bfs_last_status() describe the most recent failure on the calling host
+ * thread.  No call aborts the process or traps the GPU: device-side failures
+ * (a bounded wait that ran out, a queue overflow) are recorded in a per-graph
+ * status word read by bfs_graph_status().
+ *
+ * Threading: a bfs_graph may be used from several host threads, but its BFS
+ * workspace is shared, so runs on one graph are serialised on the device
+ * (a run on a new stream first waits for the previous run's event).
+ */
+#ifndef GBBFS_H
+#define GBBFS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bfs_graph bfs_graph;   /* opaque, owned by the library */
+typedef struct bfs_server bfs_server; /* opaque, owned by the library */
+
+typedef enum {
+    BFS_OK = 0,
+    BFS_NOT_READY = 1,          /* bfs_poll: the query is still running   */
+    BFS_ERR_INVALID_ARG = -1,   /* bad pointer, size, root or option       */
+    BFS_ERR_INVALID_GRAPH = -2, /* CSR failed validation                   */
+    BFS_ERR_OOM = -3,           /* device or host allocation failed        */
+    BFS_ERR_CUDA = -4,          /* a CUDA runtime call failed              */
+    BFS_ERR_DEPTH = -5,         /* a level does not fit the uint8 output   */
+    BFS_ERR_TIMEOUT = -6,       /* a bounded device wait ran out           */
+    BFS_ERR_BUSY = -7           /* no free slot / HBM budget exhausted     */
+} bfs_status;
+
+/* Tunables of a graph (bfs_graph_set_option).  Defaults are chosen at
+ * bfs_graph_create from the device; the autotuner overrides them. */
+typedef enum {
+    BFS_OPT_BLOCK = 1,          /* threads per CTA: 256, 512 or 1024                  */
+    BFS_OPT_CTAS_PER_SM = 2,    /* resident CTAs per SM of the persistent grid (>=1)  */
+    BFS_OPT_WARP_DEGREE = 3,    /* a frontier vertex with degree >= this is expanded
+                                   by one warp, below it by one thread (>= 1)          */
+    BFS_OPT_CTA_DEGREE = 4,     /* degree >= this: expanded by a whole CTA (>= 64)     */
+    BFS_OPT_SEGMENT = 5,        /* high-degree adjacency is cut into pieces of at most
+                                   this many edges, each expanded by one CTA (>= 256)  */
+    BFS_OPT_TIMEOUT_NS = 6,     /* limit of every device-side wait, in ns (>= 0)        */
+    BFS_OPT_LAYER_STATS = 7,    /* 1: record per-layer counters (Table 1 columns)      */
+    BFS_OPT_MAX_CTAS = 8,       /* cap on the persistent grid size (0 = no cap)        */
+    BFS_OPT_BATCH_WIDTH = 9,    /* sources per bit-parallel batch: 8..64, multiple of 8 */
+    BFS_OPT_BATCH_BLOCK = 10    /* threads per CTA of the batched kernels: 256 or 512   */
+} bfs_option;
+
+/* ---- library ------------------------------------------------------------ */
+
+/* ABI version of this header (increments on incompatible change). */
+int bfs_abi_version(void);
+
+/* Message and code of the most recent failure on this host thread. */
+const char *bfs_last_error(void);
+int bfs_last_status(void);
+
+/* ---- graph -------------------------------------------------------------- */
+
+/*
+ * Upload a CSR graph (Sec. 3.3.1) to the current CUDA device.
+ *   row_offsets : n+1 int32 entries; host or device memory (detected)
+ *   col_idx     : m int32 entries; host or device memory; may be NULL if m == 0
+ *   n, m        : 1 <= n <= INT32_MAX - 1, 0 <= m <= INT32_MAX
+ * The library copies both arrays into device memory it owns; the caller
+ * keeps ownership of its arrays.  The copy is validated on the device:
+ * row_offsets[0] == 0, non-decreasing, row_offsets[n] == m, and every
+ * column in [0, n).  On any failure returns NULL and sets bfs_last_status()
+ * to BFS_ERR_INVALID_GRAPH, BFS_ERR_INVALID_ARG, BFS_ERR_OOM or
+ * BFS_ERR_CUDA.  Synchronous (returns once the graph is resident).
+ */
+bfs_graph *bfs_graph_create(const int32_t *row_offsets, const int32_t *col_idx,
+                            int64_t n, int64_t m);
+
+/* Free the graph and its workspaces after all its work has finished.
+ * NULL is accepted.  Returns BFS_OK or BFS_ERR_CUDA. */
+int bfs_graph_destroy(bfs_graph *g);
+
+int64_t bfs_graph_num_vertices(const bfs_graph *g);
+int64_t bfs_graph_num_edges(const bfs_graph *g);
+
+/* Device pointers of the library-owned CSR copy (read-only for callers). */
+const int32_t *bfs_graph_device_row_offsets(const bfs_graph *g);
+const int32_t *bfs_graph_device_col_idx(const bfs_graph *g);
+
+/* Set / read a tunable.  Invalid values give BFS_ERR_INVALID_ARG. */
+int bfs_graph_set_option(bfs_graph *g, int option, int64_t value);
+int64_t bfs_graph_get_option(const bfs_graph *g, int option);
+
+/*
+ * Single-source top-down BFS from `root` (Alg. 2 with atomic bitmap updates).
+ *   root       : 0 <= root < n, else BFS_ERR_INVALID_ARG
+ *   level_out  : int32[n], device memory or host memory (detected)
+ *   parent_out : int32[n], device or host memory, or NULL to skip parents
+ *   stream     : a cudaStream_t (NULL = the legacy default stream)
+ * Stream-ordered and asynchronous when both outputs are device memory: the
+ * whole search (initialisation, every layer, termination) runs as one
+ * persistent cooperative kernel with no host round trip per layer.  With
+ * host outputs the library searches into its own device buffers and copies
+ * the results back on `stream` (pinned host memory keeps this asynchronous;
+ * pageable memory makes the copy synchronous).  Caller-owned outputs must
+ * stay valid until the stream reaches the end of the run.
+ * Returns enqueue-time errors only; device-side errors (BFS_ERR_TIMEOUT, a
+ * queue overflow reported as BFS_ERR_CUDA) are read with bfs_graph_status.
+ */
+int bfs_run(bfs_graph *g, int32_t root, int32_t *level_out, int32_t *parent_out,
+            void *stream);
+
+/* Wait for the graph's last run and return its device-side status
+ * (BFS_OK, BFS_ERR_TIMEOUT or BFS_ERR_CUDA); clears the status word. */
+int bfs_graph_status(bfs_graph *g);
+
+/*
+ * Per-layer counters of the last bfs_run, the columns of Table 1: for layer
+ * d, vertices[d] = frontier entries expanded, edges[d] = adjacency entries
+ * scanned, traversed[d] = vertices first reached.  Recorded only while
+ * BFS_OPT_LAYER_STATS is 1.  Arrays are host int64[max_layers].  Returns the
+ * number of layers (<= max_layers are written) or a negative bfs_status.
+ * Synchronous.
+ */
+int bfs_graph_layer_stats(bfs_graph *g, int64_t *vertices, int64_t *edges,
+                          int64_t *traversed, int32_t max_layers);
+
+/* Copy the visited bitmap of the last bfs_run (uint32 words, vertex v at
+ * word v>>5, bit v&31; Sec. 3.3.1, Listing 1) to host memory `words_out` of
+ * `nwords` >= ceil(n/32) entries.  Synchronous. */
+int bfs_graph_visited_bitmap(bfs_graph *g, uint32_t *words_out, int64_t nwords);
+
+/*
+ * Batched BFS: k sources searched together, bit-parallel, `BATCH_WIDTH`
+ * (default 64) sources per uint64 visit/frontier word per vertex.  Not in
+ * the paper; it reuses the layer step of Alg. 2 with one bit per source.
+ *   roots     : host int32[k], each in [0, n)
+ *   k         : >= 0
+ *   level_out : uint8[k][n] source-major, device or host memory; level of
+ *               vertex v from roots[i] at level_out[i*n + v], 0xFF = unreached
+ * Synchronous.  Returns BFS_ERR_DEPTH if some level exceeds 254.
+ */
+int bfs_run_batch(bfs_graph *g, const int32_t *roots, int32_t k, uint8_t *level_out);
+
+/* ---- serving ------------------------------------------------------------ */
+
+/*
+ * A request loop over resident graphs with continuous batching: queries on
+ * one graph are packed into the lanes of bit-parallel batches as they
+ * arrive; a lane freed by a finished query is given to the next waiting one
+ * while the batch keeps running.  Work is admitted while the device memory
+ * it needs fits `hbm_budget_bytes` (0 = a default fraction of free memory).
+ * The server runs its own host thread and CUDA stream.
+ */
+bfs_server *bfs_server_create(int64_t hbm_budget_bytes);
+int bfs_server_destroy(bfs_server *s);
+
+/* Register a graph (not owned: keep it alive until bfs_server_destroy).
+ * Returns a graph id >= 0 or a negative bfs_status. */
+int bfs_server_add_graph(bfs_server *s, bfs_graph *g);
+
+/* Queue one BFS query.  level_out: host uint8[n] of that graph, written as in
+ * bfs_run_batch (0xFF = unreached); it must stay valid until bfs_poll
+ * reports completion.  *ticket receives the query's id. */
+int bfs_submit(bfs_server *s, int graph_id, int32_t root, uint8_t *level_out,
+               uint64_t *ticket);
+
+/* BFS_OK when the query is complete (level_out filled), BFS_NOT_READY while
+ * it runs, or a negative bfs_status.  Never blocks. */
+int bfs_poll(bfs_server *s, uint64_t ticket);
+
+/* Block until every submitted query has completed (or failed). */
+int bfs_server_drain(bfs_server *s);
+
+/* Submission and completion times of a query, ns on a monotonic clock. */
+int bfs_ticket_times(bfs_server *s, uint64_t ticket, int64_t *t_submit_ns,
+                     int64_t *t_done_ns);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GBBFS_H */

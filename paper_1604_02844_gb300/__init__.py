@@ -1,0 +1,295 @@
+"""GB300-native level-synchronous top-down BFS (Paredes, Riley, Lujan,
+"Breadth First Search Vectorization on the Intel Xeon Phi").
+
+A thin ctypes binding over the C ABI in ``include/gbbfs.h`` (``libgbbfs.so``,
+built in-tree by ``build.py``).  Every step of the search runs in the
+library's CUDA kernels; this module only marshals arguments.  PyTorch is used
+for device buffers and streams.  There is no CPU fallback: if the library is
+missing the import-time load raises.
+
+Functions keep the C names (``bfs_graph_create``, ``bfs_run``,
+``bfs_run_batch``, ``bfs_server_create``, ``bfs_submit``, ``bfs_poll`` ...);
+``Graph`` and ``Server`` wrap them for convenience.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgbbfs.so")
+
+# bfs_status
+BFS_OK = 0
+BFS_NOT_READY = 1
+BFS_ERR_INVALID_ARG = -1
+BFS_ERR_INVALID_GRAPH = -2
+BFS_ERR_OOM = -3
+BFS_ERR_CUDA = -4
+BFS_ERR_DEPTH = -5
+BFS_ERR_TIMEOUT = -6
+BFS_ERR_BUSY = -7
+
+# bfs_option
+BFS_OPT_BLOCK = 1
+BFS_OPT_CTAS_PER_SM = 2
+BFS_OPT_WARP_DEGREE = 3
+BFS_OPT_CTA_DEGREE = 4
+BFS_OPT_SEGMENT = 5
+BFS_OPT_TIMEOUT_NS = 6
+BFS_OPT_LAYER_STATS = 7
+BFS_OPT_MAX_CTAS = 8
+BFS_OPT_BATCH_WIDTH = 9
+BFS_OPT_BATCH_BLOCK = 10
+
+OPTION_NAMES = {
+    "block": BFS_OPT_BLOCK, "ctas_per_sm": BFS_OPT_CTAS_PER_SM,
+    "warp_degree": BFS_OPT_WARP_DEGREE, "cta_degree": BFS_OPT_CTA_DEGREE,
+    "segment": BFS_OPT_SEGMENT, "timeout_ns": BFS_OPT_TIMEOUT_NS,
+    "layer_stats": BFS_OPT_LAYER_STATS, "max_ctas": BFS_OPT_MAX_CTAS,
+    "batch_width": BFS_OPT_BATCH_WIDTH, "batch_block": BFS_OPT_BATCH_BLOCK,
+}
+
+# every symbol include/gbbfs.h declares, with (restype, argtypes)
+_P = ctypes.c_void_p
+_I32, _I64, _U64, _INT = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_int
+SIGNATURES = {
+    "bfs_abi_version": (_INT, []),
+    "bfs_last_error": (ctypes.c_char_p, []),
+    "bfs_last_status": (_INT, []),
+    "bfs_graph_create": (_P, [_P, _P, _I64, _I64]),
+    "bfs_graph_destroy": (_INT, [_P]),
+    "bfs_graph_num_vertices": (_I64, [_P]),
+    "bfs_graph_num_edges": (_I64, [_P]),
+    "bfs_graph_device_row_offsets": (_P, [_P]),
+    "bfs_graph_device_col_idx": (_P, [_P]),
+    "bfs_graph_set_option": (_INT, [_P, _INT, _I64]),
+    "bfs_graph_get_option": (_I64, [_P, _INT]),
+    "bfs_run": (_INT, [_P, _I32, _P, _P, _P]),
+    "bfs_graph_status": (_INT, [_P]),
+    "bfs_graph_layer_stats": (_INT, [_P, _P, _P, _P, _I32]),
+    "bfs_graph_visited_bitmap": (_INT, [_P, _P, _I64]),
+    "bfs_run_batch": (_INT, [_P, _P, _I32, _P]),
+    "bfs_server_create": (_P, [_I64]),
+    "bfs_server_destroy": (_INT, [_P]),
+    "bfs_server_add_graph": (_INT, [_P, _P]),
+    "bfs_submit": (_INT, [_P, _INT, _I32, _P, ctypes.POINTER(_U64)]),
+    "bfs_poll": (_INT, [_P, _U64]),
+    "bfs_server_drain": (_INT, [_P]),
+    "bfs_ticket_times": (_INT, [_P, _U64, ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
+}
+
+
+class BfsError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"[{status}] {message}")
+        self.status = status
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libgbbfs.so; raises if it has not been built (no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it first (python -c 'import __graft_entry__ as g; "
+                           "g.build()'); this package has no CPU fallback")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def last_error() -> str:
+    return load().bfs_last_error().decode(errors="replace")
+
+
+def _check(status: int) -> int:
+    if status < 0:
+        raise BfsError(status, last_error())
+    return status
+
+
+def _ptr(a) -> int:
+    """Address of a torch tensor or numpy array (contiguous)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        assert a.is_contiguous(), "tensor must be contiguous"
+        return a.data_ptr()
+    if isinstance(a, np.ndarray):
+        assert a.flags["C_CONTIGUOUS"], "array must be C-contiguous"
+        return a.ctypes.data
+    return int(a)
+
+
+def _stream_handle(stream) -> int:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+# ---- C-named functions ----------------------------------------------------
+
+def bfs_abi_version() -> int:
+    return load().bfs_abi_version()
+
+
+def bfs_graph_create(row_offsets, col_idx, n: int | None = None, m: int | None = None) -> int:
+    """Upload a CSR; arrays may be numpy, host or CUDA tensors (int32)."""
+    n = (len(row_offsets) - 1) if n is None else n
+    m = len(col_idx) if m is None else m
+    h = load().bfs_graph_create(_ptr(row_offsets), _ptr(col_idx) if m > 0 else None, n, m)
+    if not h:
+        raise BfsError(load().bfs_last_status(), last_error())
+    return h
+
+
+def bfs_graph_destroy(g) -> None:
+    _check(load().bfs_graph_destroy(g))
+
+
+def bfs_run(g, root: int, level_out, parent_out=None, stream=None) -> None:
+    _check(load().bfs_run(g, int(root), _ptr(level_out), _ptr(parent_out), _stream_handle(stream)))
+
+
+def bfs_graph_status(g) -> int:
+    return _check(load().bfs_graph_status(g))
+
+
+def bfs_run_batch(g, roots, level_out) -> None:
+    r = np.ascontiguousarray(roots, dtype=np.int32)
+    _check(load().bfs_run_batch(g, r.ctypes.data, int(r.shape[0]), _ptr(level_out)))
+
+
+def bfs_graph_set_option(g, option, value: int) -> None:
+    opt = OPTION_NAMES[option] if isinstance(option, str) else int(option)
+    _check(load().bfs_graph_set_option(g, opt, int(value)))
+
+
+def bfs_graph_get_option(g, option) -> int:
+    opt = OPTION_NAMES[option] if isinstance(option, str) else int(option)
+    v = load().bfs_graph_get_option(g, opt)
+    return _check(v) if v < 0 else v
+
+
+def bfs_graph_layer_stats(g, max_layers: int = 256):
+    v = np.zeros(max_layers, np.int64)
+    e = np.zeros(max_layers, np.int64)
+    t = np.zeros(max_layers, np.int64)
+    L = _check(load().bfs_graph_layer_stats(g, v.ctypes.data, e.ctypes.data, t.ctypes.data, max_layers))
+    return v[:L], e[:L], t[:L]
+
+
+def bfs_graph_visited_bitmap(g, n: int) -> np.ndarray:
+    words = np.zeros((n + 31) // 32, np.uint32)
+    _check(load().bfs_graph_visited_bitmap(g, words.ctypes.data, words.shape[0]))
+    return words
+
+
+def bfs_server_create(hbm_budget_bytes: int = 0) -> int:
+    h = load().bfs_server_create(int(hbm_budget_bytes))
+    if not h:
+        raise BfsError(load().bfs_last_status(), last_error())
+    return h
+
+
+def bfs_server_destroy(s) -> None:
+    _check(load().bfs_server_destroy(s))
+
+
+def bfs_server_add_graph(s, g) -> int:
+    return _check(load().bfs_server_add_graph(s, g))
+
+
+def bfs_submit(s, graph_id: int, root: int, level_out) -> int:
+    t = ctypes.c_uint64(0)
+    _check(load().bfs_submit(s, int(graph_id), int(root), _ptr(level_out), ctypes.byref(t)))
+    return t.value
+
+
+def bfs_poll(s, ticket: int) -> int:
+    return _check(load().bfs_poll(s, int(ticket)))
+
+
+def bfs_server_drain(s) -> None:
+    _check(load().bfs_server_drain(s))
+
+
+def bfs_ticket_times(s, ticket: int):
+    a, b = ctypes.c_int64(0), ctypes.c_int64(0)
+    _check(load().bfs_ticket_times(s, int(ticket), ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
+# ---- convenience wrappers -------------------------------------------------
+
+class Graph:
+    """A resident CSR graph.  ``run`` returns CUDA tensors (level, parent)."""
+
+    def __init__(self, row_offsets, col_idx, **options):
+        self.n = len(row_offsets) - 1
+        self.m = len(col_idx)
+        self.handle = bfs_graph_create(row_offsets, col_idx, self.n, self.m)
+        for k, v in options.items():
+            self.set_option(k, v)
+
+    def set_option(self, name, value):
+        bfs_graph_set_option(self.handle, name, value)
+
+    def get_option(self, name):
+        return bfs_graph_get_option(self.handle, name)
+
+    def run(self, root: int, level_out=None, parent_out=None, want_parent: bool = True, stream=None):
+        import torch
+        if level_out is None:
+            level_out = torch.empty(self.n, dtype=torch.int32, device="cuda")
+        if parent_out is None and want_parent:
+            parent_out = torch.empty(self.n, dtype=torch.int32, device="cuda")
+        bfs_run(self.handle, root, level_out, parent_out, stream)
+        return level_out, parent_out
+
+    def status(self) -> int:
+        return bfs_graph_status(self.handle)
+
+    def run_batch(self, roots, level_out=None):
+        import torch
+        roots = np.ascontiguousarray(roots, dtype=np.int32)
+        if level_out is None:
+            level_out = torch.empty((roots.shape[0], self.n), dtype=torch.uint8, device="cuda")
+        bfs_run_batch(self.handle, roots, level_out)
+        return level_out
+
+    def layer_stats(self, max_layers: int = 256):
+        return bfs_graph_layer_stats(self.handle, max_layers)
+
+    def visited_bitmap(self):
+        return bfs_graph_visited_bitmap(self.handle, self.n)
+
+    def close(self):
+        if self.handle:
+            bfs_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -1,0 +1,102 @@
+// internal.cuh -- shared declarations of the BFS library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <mutex>
+#include <string>
+
+#include "../../include/gbbfs.h"
+
+namespace gbbfs {
+
+// ---- error reporting -------------------------------------------------------
+int set_error(int status, const std::string &msg);  // records, returns status
+int cuda_error(cudaError_t e, const char *what);      // records BFS_ERR_CUDA
+void clear_error();
+
+#define GB_CUDA(call)                                         \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return cuda_error(e_, #call);  \
+    } while (0)
+
+// ---- device status bits (sticky until bfs_graph_status reads them) --------
+enum : unsigned {
+    ST_TIMEOUT = 1u,   // a bounded wait gave up
+    ST_OVERFLOW = 2u,  // a queue append would have run past its capacity
+    ST_DEPTH = 4u,     // a level did not fit the uint8 batch encoding
+};
+
+// ---- control block of the persistent single-source kernel ------------------
+// Counters rotate over three sets: layer d reads set d%3, appends to set
+// (d+1)%3 and clears set (d+2)%3, which nobody touches during layer d.
+struct TdCtrl {
+    unsigned count[3];      // entries in the small-item frontier queue
+    unsigned work[3];       // small-queue chunk dispenser
+    unsigned big_count[3];  // entries in the large-item frontier queue
+    unsigned big_work[3];   // large-queue item dispenser
+    unsigned bar_count;     // grid barrier arrivals
+    unsigned bar_gen;       // grid barrier generation
+    unsigned exit_count;    // CTAs that left the kernel
+    unsigned status;        // ST_* bits
+    unsigned layers;        // layers of the last search
+    unsigned pad[3];
+};
+
+struct Options {
+    int block = 512;
+    int ctas_per_sm = 0;      // 0 = as many as fit
+    int warp_degree = 16;
+    int cta_degree = 1024;
+    int segment = 4096;
+    int64_t timeout_ns = 4000000000LL;
+    int layer_stats = 0;
+    int max_ctas = 0;
+    int batch_width = 64;
+    int batch_block = 512;
+};
+
+constexpr int kMaxStatLayers = 256;
+
+struct Graph {
+    int device = 0;
+    int num_sms = 0;
+    int64_t n = 0, m = 0;
+    int32_t *d_row_offsets = nullptr;
+    int32_t *d_col_idx = nullptr;  // padded: m rounded up to 4, plus 4 entries
+
+    // single-source workspace
+    uint32_t *d_bitmap = nullptr;  // words rounded up to a multiple of 4
+    int64_t bitmap_words = 0;
+    int32_t *d_q[2][3] = {};       // [buffer][u, beg, len] small-item queue
+    int32_t *d_bq[2][3] = {};      // [buffer][u, beg, len] large-item queue
+    int64_t qcap = 0, bqcap = 0;
+    TdCtrl *d_ctrl = nullptr;
+    int64_t *d_stats = nullptr;    // [kMaxStatLayers][3]
+    int32_t *d_level_tmp = nullptr;   // used when outputs are host memory
+    int32_t *d_parent_tmp = nullptr;
+
+    cudaEvent_t ws_event = nullptr;  // end of the last run on the workspace
+    cudaStream_t last_stream = nullptr;
+    bool ran = false;
+
+    // batched (bit-parallel) workspace, allocated on first use
+    void *batch_ws = nullptr;
+
+    Options opt;
+    std::mutex mu;
+};
+
+// implemented in topdown.cu
+int td_launch(Graph *g, int32_t root, int32_t *level, int32_t *parent, cudaStream_t s);
+int td_grid_size(Graph *g, int block);
+
+// implemented in msbfs.cu
+int ms_run_batch(Graph *g, const int32_t *roots, int32_t k, uint8_t *level_out);
+void ms_free(Graph *g);
+
+bool is_device_pointer(const void *p);
+
+}  // namespace gbbfs

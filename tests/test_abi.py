@@ -1,0 +1,78 @@
+"""C ABI checks that need no GPU: the library builds, loads, exports every
+symbol include/gbbfs.h declares, and rejects bad arguments on the host."""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+import paper_1604_02844_gb300 as gb
+from paper_1604_02844_gb300 import build as lib_build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "gbbfs.h")
+
+
+def header_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    return sorted(set(re.findall(r"\b(bfs_[a-z_0-9]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    lib_build.build()
+    return gb.load()
+
+
+def test_header_declares_the_boundary():
+    names = header_functions()
+    for required in ("bfs_graph_create", "bfs_graph_destroy", "bfs_run", "bfs_run_batch",
+                     "bfs_submit", "bfs_poll", "bfs_server_create", "bfs_graph_status"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in header_functions():
+        assert hasattr(lib, name), name
+    out = subprocess.run(["nm", "-D", "--defined-only", gb.LIB_PATH], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(line.split()[-1] for line in out.splitlines() if line.strip())
+    missing = [n for n in header_functions() if n not in exported]
+    assert not missing, missing
+
+
+def test_binding_covers_the_header():
+    assert set(gb.SIGNATURES) == set(header_functions())
+
+
+def test_abi_version(lib):
+    assert gb.bfs_abi_version() == 1
+
+
+def test_host_side_argument_errors(lib):
+    ro = np.array([0, 1, 2], np.int32)
+    col = np.array([1, 0], np.int32)
+    # n out of range, missing col_idx: rejected before any CUDA call
+    assert not lib.bfs_graph_create(ro.ctypes.data, col.ctypes.data, 0, 2)
+    assert lib.bfs_last_status() == gb.BFS_ERR_INVALID_ARG
+    assert "n" in gb.last_error()
+    assert not lib.bfs_graph_create(ro.ctypes.data, None, 2, 2)
+    assert lib.bfs_last_status() == gb.BFS_ERR_INVALID_ARG
+    assert not lib.bfs_graph_create(None, col.ctypes.data, 2, 2)
+    assert lib.bfs_run(None, 0, None, None, None) == gb.BFS_ERR_INVALID_ARG
+    assert lib.bfs_graph_status(None) == gb.BFS_ERR_INVALID_ARG
+    assert lib.bfs_run_batch(None, None, 0, None) == gb.BFS_ERR_INVALID_ARG
+    assert lib.bfs_graph_set_option(None, gb.BFS_OPT_BLOCK, 512) == gb.BFS_ERR_INVALID_ARG
+    assert lib.bfs_graph_destroy(None) == gb.BFS_OK
+    with pytest.raises(gb.BfsError):
+        gb.bfs_graph_create(ro, col, 0, 2)
+
+
+def test_missing_library_fails_loudly(tmp_path, monkeypatch):
+    monkeypatch.setattr(gb, "_lib", None)
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        gb.load(str(tmp_path / "nope.so"))
