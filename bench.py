@@ -52,6 +52,8 @@ def parse_args(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--option", action="append", default=[],
                     help="name=value tunable passed to bfs_graph_set_option")
+    ap.add_argument("--profile-layers", action="store_true",
+                    help="print the per-layer counters and device times of one search to stderr")
     return ap.parse_args(argv)
 
 
@@ -247,6 +249,18 @@ def run_ours(args):
         bmin[int(r)] = algorithmic_bytes(dsum, nr, n)
     torch.cuda.synchronize()
     assert g.status() == gb.BFS_OK, gb.last_error()
+
+    if args.profile_layers and rank == 0:
+        g.set_option("layer_stats", 1)
+        for r in roots[:2]:
+            g.run(int(r), level, parent)
+            torch.cuda.synchronize()
+            v, e, t = g.layer_stats()
+            ts = g.layer_times()
+            print(json.dumps({"root": int(r), "layers": [
+                {"d": d, "vertices": int(v[d]), "edges": int(e[d]), "new": int(t[d]),
+                 "t_end_us": round(ts[d] / 1e3, 2)} for d in range(len(v))]}), file=sys.stderr)
+        g.set_option("layer_stats", 0)
 
     def one_step(record):
         evs = []

@@ -78,7 +78,10 @@ typedef enum {
     BFS_OPT_LAYER_STATS = 7,    /* 1: record per-layer counters (Table 1 columns)      */
     BFS_OPT_MAX_CTAS = 8,       /* cap on the persistent grid size (0 = no cap)        */
     BFS_OPT_BATCH_WIDTH = 9,    /* sources per bit-parallel batch: 8..64, multiple of 8 */
-    BFS_OPT_BATCH_BLOCK = 10    /* threads per CTA of the batched kernels: 256 or 512   */
+    BFS_OPT_BATCH_BLOCK = 10,   /* threads per CTA of the batched kernels: 256 or 512   */
+    BFS_OPT_MODE = 11           /* expansion of bfs_run: 0 = edge-balanced units (work
+                                   items bounded in edges; BLOCK 256 or 512), 1 = one
+                                   item per frontier vertex binned by degree           */
 } bfs_option;
 
 /* ---- library ------------------------------------------------------------ */
@@ -155,6 +158,11 @@ int bfs_graph_status(bfs_graph *g);
  */
 int bfs_graph_layer_stats(bfs_graph *g, int64_t *vertices, int64_t *edges,
                           int64_t *traversed, int32_t max_layers);
+
+/* Device time at the end of each layer of the last bfs_run, ns since the
+ * kernel started (recorded with BFS_OPT_LAYER_STATS = 1).  Returns the
+ * number of layers or a negative bfs_status.  Synchronous. */
+int bfs_graph_layer_times(bfs_graph *g, int64_t *t_end_ns, int32_t max_layers);
 
 /* Copy the visited bitmap of the last bfs_run (uint32 words, vertex v at
  * word v>>5, bit v&31; Sec. 3.3.1, Listing 1) to host memory `words_out` of

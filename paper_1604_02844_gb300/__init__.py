@@ -43,6 +43,8 @@ BFS_OPT_LAYER_STATS = 7
 BFS_OPT_MAX_CTAS = 8
 BFS_OPT_BATCH_WIDTH = 9
 BFS_OPT_BATCH_BLOCK = 10
+BFS_OPT_MODE = 11
+MODE_UNITS, MODE_BINNED = 0, 1
 
 OPTION_NAMES = {
     "block": BFS_OPT_BLOCK, "ctas_per_sm": BFS_OPT_CTAS_PER_SM,
@@ -50,6 +52,7 @@ OPTION_NAMES = {
     "segment": BFS_OPT_SEGMENT, "timeout_ns": BFS_OPT_TIMEOUT_NS,
     "layer_stats": BFS_OPT_LAYER_STATS, "max_ctas": BFS_OPT_MAX_CTAS,
     "batch_width": BFS_OPT_BATCH_WIDTH, "batch_block": BFS_OPT_BATCH_BLOCK,
+    "mode": BFS_OPT_MODE,
 }
 
 # every symbol include/gbbfs.h declares, with (restype, argtypes)
@@ -70,6 +73,7 @@ SIGNATURES = {
     "bfs_run": (_INT, [_P, _I32, _P, _P, _P]),
     "bfs_graph_status": (_INT, [_P]),
     "bfs_graph_layer_stats": (_INT, [_P, _P, _P, _P, _I32]),
+    "bfs_graph_layer_times": (_INT, [_P, _P, _I32]),
     "bfs_graph_visited_bitmap": (_INT, [_P, _P, _I64]),
     "bfs_run_batch": (_INT, [_P, _P, _I32, _P]),
     "bfs_server_create": (_P, [_I64]),
@@ -192,6 +196,12 @@ def bfs_graph_layer_stats(g, max_layers: int = 256):
     return v[:L], e[:L], t[:L]
 
 
+def bfs_graph_layer_times(g, max_layers: int = 256) -> np.ndarray:
+    t = np.zeros(max_layers, np.int64)
+    L = _check(load().bfs_graph_layer_times(g, t.ctypes.data, max_layers))
+    return t[:L]
+
+
 def bfs_graph_visited_bitmap(g, n: int) -> np.ndarray:
     words = np.zeros((n + 31) // 32, np.uint32)
     _check(load().bfs_graph_visited_bitmap(g, words.ctypes.data, words.shape[0]))
@@ -273,6 +283,9 @@ class Graph:
 
     def layer_stats(self, max_layers: int = 256):
         return bfs_graph_layer_stats(self.handle, max_layers)
+
+    def layer_times(self, max_layers: int = 256):
+        return bfs_graph_layer_times(self.handle, max_layers)
 
     def visited_bitmap(self):
         return bfs_graph_visited_bitmap(self.handle, self.n)

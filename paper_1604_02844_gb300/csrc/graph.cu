@@ -73,11 +73,15 @@ static void free_graph(Graph *g)
     cudaFree(g->d_row_offsets);
     cudaFree(g->d_col_idx);
     cudaFree(g->d_bitmap);
-    for (int b = 0; b < 2; ++b)
+    for (int b = 0; b < 2; ++b) {
         for (int j = 0; j < 3; ++j) {
             cudaFree(g->d_q[b][j]);
             cudaFree(g->d_bq[b][j]);
+            cudaFree(g->d_eq[b][j]);
+            cudaFree(g->d_hq[b][j]);
         }
+        for (int j = 0; j < 2; ++j) cudaFree(g->d_uq[b][j]);
+    }
     cudaFree(g->d_ctrl);
     cudaFree(g->d_stats);
     cudaFree(g->d_level_tmp);
@@ -86,11 +90,25 @@ static void free_graph(Graph *g)
     delete g;
 }
 
-// Large-item queue capacity: a vertex of degree d >= cta_degree becomes
-// ceil(d / segment) items, so the items of one layer are at most
-// m / segment + m / cta_degree (+1).  Options keep segment >= 256 and
-// cta_degree >= 64, the bounds used here.
+// Large-item queue capacity (binned mode): a vertex of degree d >=
+// cta_degree becomes ceil(d / segment) items, so the items of one layer are
+// at most m / segment + m / cta_degree (+1).  Options keep segment >= 256
+// and cta_degree >= 64, the bounds used here.
 static int64_t big_queue_capacity(int64_t m) { return m / 256 + m / 64 + 2; }
+
+// Binned-mode queues, allocated the first time that mode runs.
+static int alloc_binned(Graph *g)
+{
+    if (g->d_q[0][0]) return BFS_OK;
+    g->qcap = g->n;
+    g->bqcap = big_queue_capacity(g->m);
+    for (int b = 0; b < 2; ++b)
+        for (int j = 0; j < 3; ++j) {
+            GB_CUDA(cudaMalloc(&g->d_q[b][j], (size_t)g->qcap * 4));
+            GB_CUDA(cudaMalloc(&g->d_bq[b][j], (size_t)g->bqcap * 4));
+        }
+    return BFS_OK;
+}
 
 }  // namespace gbbfs
 
@@ -154,21 +172,23 @@ bfs_graph *bfs_graph_create(const int32_t *row_offsets, const int32_t *col_idx, 
         return nullptr;
     }
 
-    // single-source workspace
+    // single-source workspace (units mode; the binned-mode queues are lazy)
     g->bitmap_words = ((n + 31) / 32 + 3) / 4 * 4;
-    g->qcap = n;
-    g->bqcap = big_queue_capacity(m);
+    g->hcap = td_units_hub_capacity(m);
     if ((e = cudaMalloc(&g->d_bitmap, (size_t)g->bitmap_words * 4)) != cudaSuccess) return fail(e, "cudaMalloc(bitmap)");
-    for (int b = 0; b < 2; ++b)
+    for (int b = 0; b < 2; ++b) {
         for (int j = 0; j < 3; ++j) {
-            if ((e = cudaMalloc(&g->d_q[b][j], (size_t)g->qcap * 4)) != cudaSuccess) return fail(e, "cudaMalloc(queue)");
-            if ((e = cudaMalloc(&g->d_bq[b][j], (size_t)g->bqcap * 4)) != cudaSuccess) return fail(e, "cudaMalloc(big queue)");
+            if ((e = cudaMalloc(&g->d_eq[b][j], (size_t)n * 4)) != cudaSuccess) return fail(e, "cudaMalloc(entry queue)");
+            if ((e = cudaMalloc(&g->d_hq[b][j], (size_t)g->hcap * 4)) != cudaSuccess) return fail(e, "cudaMalloc(hub queue)");
         }
-    if ((e = cudaMalloc(&g->d_ctrl, sizeof(TdCtrl))) != cudaSuccess) return fail(e, "cudaMalloc(ctrl)");
-    if ((e = cudaMemset(g->d_ctrl, 0, sizeof(TdCtrl))) != cudaSuccess) return fail(e, "cudaMemset(ctrl)");
+        for (int j = 0; j < 2; ++j)
+            if ((e = cudaMalloc(&g->d_uq[b][j], (size_t)n * 4)) != cudaSuccess) return fail(e, "cudaMalloc(unit queue)");
+    }
+    if ((e = cudaMalloc(&g->d_ctrl, sizeof(Ctrl))) != cudaSuccess) return fail(e, "cudaMalloc(ctrl)");
+    if ((e = cudaMemset(g->d_ctrl, 0, sizeof(Ctrl))) != cudaSuccess) return fail(e, "cudaMemset(ctrl)");
     if ((e = cudaMemset(g->d_bitmap, 0, (size_t)g->bitmap_words * 4)) != cudaSuccess) return fail(e, "cudaMemset(bitmap)");
-    if ((e = cudaMalloc(&g->d_stats, sizeof(int64_t) * 3 * kMaxStatLayers)) != cudaSuccess) return fail(e, "cudaMalloc(stats)");
-    if ((e = cudaMemset(g->d_stats, 0, sizeof(int64_t) * 3 * kMaxStatLayers)) != cudaSuccess) return fail(e, "cudaMemset(stats)");
+    if ((e = cudaMalloc(&g->d_stats, sizeof(int64_t) * 4 * kMaxStatLayers)) != cudaSuccess) return fail(e, "cudaMalloc(stats)");
+    if ((e = cudaMemset(g->d_stats, 0, sizeof(int64_t) * 4 * kMaxStatLayers)) != cudaSuccess) return fail(e, "cudaMemset(stats)");
     if ((e = cudaEventCreateWithFlags(&g->ws_event, cudaEventDisableTiming)) != cudaSuccess) return fail(e, "cudaEventCreate");
     if ((e = cudaDeviceSynchronize()) != cudaSuccess) return fail(e, "cudaDeviceSynchronize");
     return reinterpret_cast<bfs_graph *>(g);
@@ -238,6 +258,10 @@ int bfs_graph_set_option(bfs_graph *gh, int option, int64_t v)
         if (v != 256 && v != 512) return bad("BATCH_BLOCK must be 256 or 512");
         o.batch_block = (int)v;
         break;
+    case BFS_OPT_MODE:
+        if (v != MODE_UNITS && v != MODE_BINNED) return bad("MODE must be 0 (units) or 1 (binned)");
+        o.mode = (int)v;
+        break;
     default:
         return bad("unknown option");
     }
@@ -259,6 +283,7 @@ int64_t bfs_graph_get_option(const bfs_graph *gh, int option)
     case BFS_OPT_MAX_CTAS: return o.max_ctas;
     case BFS_OPT_BATCH_WIDTH: return o.batch_width;
     case BFS_OPT_BATCH_BLOCK: return o.batch_block;
+    case BFS_OPT_MODE: return o.mode;
     default: return set_error(BFS_ERR_INVALID_ARG, "bfs_graph_get_option: unknown option");
     }
 }
@@ -286,7 +311,16 @@ int bfs_run(bfs_graph *gh, int32_t root, int32_t *level_out, int32_t *parent_out
     }
     // one workspace: a run on another stream waits for the previous run
     if (g->ran && s != g->last_stream) GB_CUDA(cudaStreamWaitEvent(s, g->ws_event, 0));
-    int rc = td_launch(g, root, d_level, d_parent, s);
+    if (g->opt.mode == MODE_UNITS && g->opt.block == 1024)
+        return set_error(BFS_ERR_INVALID_ARG, "bfs_run: the units mode takes BLOCK 256 or 512");
+    int rc;
+    if (g->opt.mode == MODE_BINNED) {
+        rc = alloc_binned(g);
+        if (rc != BFS_OK) return rc;
+        rc = td_launch(g, root, d_level, d_parent, s);
+    } else {
+        rc = td_units_launch(g, root, d_level, d_parent, s);
+    }
     if (rc != BFS_OK) return rc;
     if (!lvl_dev) GB_CUDA(cudaMemcpyAsync(level_out, d_level, (size_t)g->n * 4, cudaMemcpyDeviceToHost, s));
     if (!par_dev) GB_CUDA(cudaMemcpyAsync(parent_out, d_parent, (size_t)g->n * 4, cudaMemcpyDeviceToHost, s));
@@ -321,14 +355,31 @@ int bfs_graph_layer_stats(bfs_graph *gh, int64_t *vertices, int64_t *edges, int6
     if (g->ran) GB_CUDA(cudaEventSynchronize(g->ws_event));
     unsigned layers = 0;
     GB_CUDA(cudaMemcpy(&layers, &g->d_ctrl->layers, sizeof(unsigned), cudaMemcpyDeviceToHost));
-    int64_t buf[3 * kMaxStatLayers];
+    int64_t buf[4 * kMaxStatLayers];
     GB_CUDA(cudaMemcpy(buf, g->d_stats, sizeof(buf), cudaMemcpyDeviceToHost));
     int L = (int)std::min<unsigned>(layers, kMaxStatLayers);
     for (int d = 0; d < L && d < max_layers; ++d) {
-        vertices[d] = buf[3 * d + 0];
-        edges[d] = buf[3 * d + 1];
-        traversed[d] = buf[3 * d + 2];
+        vertices[d] = buf[4 * d + 0];
+        edges[d] = buf[4 * d + 1];
+        traversed[d] = buf[4 * d + 2];
     }
+    return L;
+}
+
+int bfs_graph_layer_times(bfs_graph *gh, int64_t *t_end_ns, int32_t max_layers)
+{
+    clear_error();
+    if (!gh || max_layers < 0 || (max_layers > 0 && !t_end_ns))
+        return set_error(BFS_ERR_INVALID_ARG, "bfs_graph_layer_times: bad argument");
+    Graph *g = reinterpret_cast<Graph *>(gh);
+    std::lock_guard<std::mutex> lk(g->mu);
+    if (g->ran) GB_CUDA(cudaEventSynchronize(g->ws_event));
+    unsigned layers = 0;
+    GB_CUDA(cudaMemcpy(&layers, &g->d_ctrl->layers, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    int64_t buf[4 * kMaxStatLayers];
+    GB_CUDA(cudaMemcpy(buf, g->d_stats, sizeof(buf), cudaMemcpyDeviceToHost));
+    int L = (int)std::min<unsigned>(layers, kMaxStatLayers);
+    for (int d = 0; d < L && d < max_layers; ++d) t_end_ns[d] = buf[4 * d + 3];
     return L;
 }
 

@@ -29,21 +29,27 @@ enum : unsigned {
     ST_DEPTH = 4u,     // a level did not fit the uint8 batch encoding
 };
 
-// ---- control block of the persistent single-source kernel ------------------
+// ---- control block of the persistent single-source kernels ----------------
 // Counters rotate over three sets: layer d reads set d%3, appends to set
 // (d+1)%3 and clears set (d+2)%3, which nobody touches during layer d.
-struct TdCtrl {
-    unsigned count[3];      // entries in the small-item frontier queue
-    unsigned work[3];       // small-queue chunk dispenser
-    unsigned big_count[3];  // entries in the large-item frontier queue
-    unsigned big_work[3];   // large-queue item dispenser
-    unsigned bar_count;     // grid barrier arrivals
-    unsigned bar_gen;       // grid barrier generation
-    unsigned exit_count;    // CTAs that left the kernel
-    unsigned status;        // ST_* bits
-    unsigned layers;        // layers of the last search
-    unsigned pad[3];
+// The last CTA to leave a search returns every counter to zero.
+struct Ctrl {
+    unsigned long long eu_count[3];  // units mode: (units << 32) | entries
+    unsigned hub_count[3];           // units mode: hub slices
+    unsigned work[3];                // work-item dispenser (both modes)
+    unsigned count[3];               // binned mode: small-item queue size
+    unsigned big_count[3];           // binned mode: large-item queue size
+    unsigned big_work[3];            // binned mode: large-item dispenser
+    unsigned bar_count;              // grid barrier arrivals
+    unsigned bar_gen;                // grid barrier generation
+    unsigned exit_count;             // CTAs that left the kernel
+    unsigned status;                 // ST_* bits
+    unsigned layers;                 // layers of the last search
 };
+using TdCtrl = Ctrl;
+using UnitCtrl = Ctrl;
+
+enum { MODE_UNITS = 0, MODE_BINNED = 1 };
 
 struct Options {
     int block = 512;
@@ -56,6 +62,7 @@ struct Options {
     int max_ctas = 0;
     int batch_width = 64;
     int batch_block = 512;
+    int mode = MODE_UNITS;
 };
 
 constexpr int kMaxStatLayers = 256;
@@ -70,11 +77,16 @@ struct Graph {
     // single-source workspace
     uint32_t *d_bitmap = nullptr;  // words rounded up to a multiple of 4
     int64_t bitmap_words = 0;
-    int32_t *d_q[2][3] = {};       // [buffer][u, beg, len] small-item queue
-    int32_t *d_bq[2][3] = {};      // [buffer][u, beg, len] large-item queue
+    int32_t *d_eq[2][3] = {};      // units mode: [buffer][u, beg, len] entries
+    int32_t *d_uq[2][2] = {};      // units mode: [buffer][first entry, count]
+    int32_t *d_hq[2][3] = {};      // units mode: [buffer][u, beg, len] hub slices
+    int64_t hcap = 0;
+    int32_t *d_q[2][3] = {};       // binned mode (lazy): small-item queue
+    int32_t *d_bq[2][3] = {};      // binned mode (lazy): large-item queue
     int64_t qcap = 0, bqcap = 0;
-    TdCtrl *d_ctrl = nullptr;
-    int64_t *d_stats = nullptr;    // [kMaxStatLayers][3]
+    Ctrl *d_ctrl = nullptr;
+    int64_t *d_stats = nullptr;    // [kMaxStatLayers][4]: vertices, edges, new, t_end_ns
+    int last_grid = 0;
     int32_t *d_level_tmp = nullptr;   // used when outputs are host memory
     int32_t *d_parent_tmp = nullptr;
 
@@ -89,9 +101,13 @@ struct Graph {
     std::mutex mu;
 };
 
-// implemented in topdown.cu
+// implemented in topdown.cu (degree-binned mode; its queues are allocated
+// on first use by graph.cu)
 int td_launch(Graph *g, int32_t root, int32_t *level, int32_t *parent, cudaStream_t s);
-int td_grid_size(Graph *g, int block);
+
+// implemented in topdown_units.cu (edge-balanced units mode)
+int td_units_launch(Graph *g, int32_t root, int32_t *level, int32_t *parent, cudaStream_t s);
+int64_t td_units_hub_capacity(int64_t m);
 
 // implemented in msbfs.cu
 int ms_run_batch(Graph *g, const int32_t *roots, int32_t k, uint8_t *level_out);

@@ -50,7 +50,7 @@ struct TdParams {
     int32_t *qu[2], *qb[2], *ql[2];  // small-item queue [buffer]
     int32_t *bu[2], *bb[2], *bl[2];  // large-item queue [buffer]
     TdCtrl *ctrl;
-    int64_t *stats;  // [kMaxStatLayers][3] or null
+    int64_t *stats;  // [kMaxStatLayers][4] or null
     int32_t n;
     int32_t root;
     int32_t warp_degree, cta_degree, segment;
@@ -270,6 +270,7 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) td_kernel(TdParams p)
     const unsigned G = gridDim.x;
     TdCtrl *c = p.ctrl;
     const OutBuf ob{s_ou, s_ob, s_ol, &s_ocnt, &s_gbase};
+    const uint64_t t_start = globaltimer();
 
     // ---- initialisation (a1) ------------------------------------------------
     {
@@ -284,7 +285,7 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) td_kernel(TdParams p)
             p.bitmap[w] = (w == rw) ? (1u << (p.root & 31)) : 0u;
         if (blockIdx.x == 0) {
             if (p.stats)
-                for (int i = tid; i < 3 * kMaxStatLayers; i += BLOCK) p.stats[i] = 0;
+                for (int i = tid; i < 4 * kMaxStatLayers; i += BLOCK) p.stats[i] = 0;
             if (tid == 0) {
                 const int rb = p.ro[p.root], len = p.ro[p.root + 1] - rb;
                 unsigned cnt = 0, bcnt = 0;
@@ -430,12 +431,14 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) td_kernel(TdParams p)
             }
             __syncthreads();
             if (tid == 0) {
-                atomicAdd((unsigned long long *)&p.stats[3 * d + 0], s_stat[0]);
-                atomicAdd((unsigned long long *)&p.stats[3 * d + 1], s_stat[1]);
-                atomicAdd((unsigned long long *)&p.stats[3 * d + 2], s_stat[2]);
+                atomicAdd((unsigned long long *)&p.stats[4 * d + 0], s_stat[0]);
+                atomicAdd((unsigned long long *)&p.stats[4 * d + 1], s_stat[1]);
+                atomicAdd((unsigned long long *)&p.stats[4 * d + 2], s_stat[2]);
             }
         }
         ok = grid_sync(c, G, p.timeout_ns, &s_ok);
+        if (p.stats && d < kMaxStatLayers && blockIdx.x == 0 && tid == 0)
+            p.stats[4 * d + 3] = (int64_t)(globaltimer() - t_start);
     }
 
     // ---- exit: the last CTA out returns the control block to zero ----------
@@ -472,31 +475,11 @@ int launch_block(Graph *g, const TdParams &prm, cudaStream_t s)
     void *args[] = {&p};
     e = cudaLaunchCooperativeKernel((const void *)kern, dim3(grid), dim3(BLOCK), args, 0, s);
     if (e != cudaSuccess) return cuda_error(e, "cudaLaunchCooperativeKernel(td_kernel)");
+    g->last_grid = grid;
     return BFS_OK;
 }
 
-template <int BLOCK>
-int grid_for_block(Graph *g)
-{
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, td_kernel<BLOCK>, BLOCK, 0) != cudaSuccess) return -1;
-    if (g->opt.ctas_per_sm > 0) per_sm = std::min(per_sm, g->opt.ctas_per_sm);
-    int grid = per_sm * g->num_sms;
-    if (g->opt.max_ctas > 0) grid = std::min(grid, g->opt.max_ctas);
-    return grid;
-}
-
 }  // namespace
-
-int td_grid_size(Graph *g, int block)
-{
-    switch (block) {
-    case 256: return grid_for_block<256>(g);
-    case 512: return grid_for_block<512>(g);
-    case 1024: return grid_for_block<1024>(g);
-    default: return -1;
-    }
-}
 
 int td_launch(Graph *g, int32_t root, int32_t *level, int32_t *parent, cudaStream_t s)
 {

@@ -95,6 +95,26 @@ def test_erdos_renyi_scale16():
             check_root(g, ro, col, r)
 
 
+def test_units_boundaries():
+    """Degrees around the unit target T = 2*BLOCK and the hub slice length:
+    a root whose neighbours have degrees T-1, T, T+1, 2T, 2T+1, ... exercises
+    unit cutting, hub slicing and the last partial slice."""
+    for block in (256, 512):
+        T = 2 * block
+        degs = [1, 2, T - 1, T, T + 1, 2 * T - 1, 2 * T, 2 * T + 1, 5 * T + 3]
+        edges, nxt = [], 1 + len(degs)
+        for i, dgr in enumerate(degs):
+            hub = 1 + i
+            edges.append((0, hub))
+            for _ in range(dgr - 1):
+                edges.append((hub, nxt))
+                nxt += 1
+        ro, col = csr_from_edges(nxt, edges, False)
+        with gb.Graph(ro, col, block=block) as g:
+            for r in (0, 3, nxt - 1):
+                check_root(g, ro, col, r)
+
+
 def test_dense_clique_shares_bitmap_words():
     n = 200
     e = [(u, v) for u in range(n) for v in range(u + 1, n)]
@@ -147,9 +167,12 @@ def test_long_path_many_layers():
 
 
 @pytest.mark.parametrize("opts", [
-    dict(block=256), dict(block=1024), dict(warp_degree=1), dict(warp_degree=64),
-    dict(cta_degree=64, segment=256), dict(cta_degree=100000), dict(max_ctas=1),
-    dict(max_ctas=7, block=256), dict(ctas_per_sm=1), dict(layer_stats=1),
+    dict(block=256), dict(block=512, ctas_per_sm=1), dict(max_ctas=1), dict(max_ctas=7, block=256),
+    dict(layer_stats=1),
+    dict(mode=1), dict(mode=1, block=256), dict(mode=1, block=1024), dict(mode=1, warp_degree=1),
+    dict(mode=1, warp_degree=64), dict(mode=1, cta_degree=64, segment=256),
+    dict(mode=1, cta_degree=100000), dict(mode=1, max_ctas=1), dict(mode=1, max_ctas=7, block=256),
+    dict(mode=1, ctas_per_sm=1), dict(mode=1, layer_stats=1),
 ], ids=lambda o: ",".join(f"{k}={v}" for k, v in o.items()))
 def test_options_keep_results_exact(opts):
     ro, col = graphgen.kronecker(14, 16, 6)
@@ -207,9 +230,10 @@ def test_device_resident_inputs_and_streams():
         np.testing.assert_array_equal(lv.cpu().numpy(), ref)
 
 
-def test_layer_stats_match_table1_columns():
+@pytest.mark.parametrize("mode", [0, 1])
+def test_layer_stats_match_table1_columns(mode):
     ro, col = graphgen.kronecker(16, 16, 1)
-    with gb.Graph(ro, col, layer_stats=1) as g:
+    with gb.Graph(ro, col, layer_stats=1, mode=mode) as g:
         for r in graphgen.pick_roots(ro, 3, 1):
             lv, _ = check_root(g, ro, col, r)
             v, e, t = g.layer_stats()
@@ -217,6 +241,16 @@ def test_layer_stats_match_table1_columns():
             np.testing.assert_array_equal(v, ov)
             np.testing.assert_array_equal(e, oe)
             np.testing.assert_array_equal(t, ot)
+            times = g.layer_times()
+            assert len(times) == len(v) and np.all(np.diff(times) >= 0) and times[0] > 0
+
+
+def test_units_mode_rejects_block_1024():
+    ro, col, _ = path_graph(10, 0)
+    with gb.Graph(ro, col, block=1024) as g:
+        with pytest.raises(gb.BfsError) as ei:
+            g.run(0)
+        assert ei.value.status == gb.BFS_ERR_INVALID_ARG
 
 
 def test_invalid_csr_rejected_on_device():
