@@ -79,9 +79,11 @@ typedef enum {
     BFS_OPT_MAX_CTAS = 8,       /* cap on the persistent grid size (0 = no cap)        */
     BFS_OPT_BATCH_WIDTH = 9,    /* sources per bit-parallel batch: 8..64, multiple of 8 */
     BFS_OPT_BATCH_BLOCK = 10,   /* threads per CTA of the batched kernels: 256 or 512   */
-    BFS_OPT_MODE = 11           /* expansion of bfs_run: 0 = edge-balanced units (work
-                                   items bounded in edges; BLOCK 256 or 512), 1 = one
-                                   item per frontier vertex binned by degree           */
+    BFS_OPT_MODE = 11           /* expansion of bfs_run: 0 = edge-balanced units run by
+                                   whole CTAs, 1 = one item per frontier vertex binned
+                                   by degree (thread / warp / CTA), 2 = edge-balanced
+                                   units run by independent warps.  Modes 0 and 2 take
+                                   BLOCK 256 or 512                                      */
 } bfs_option;
 
 /* ---- library ------------------------------------------------------------ */

@@ -259,7 +259,8 @@ int bfs_graph_set_option(bfs_graph *gh, int option, int64_t v)
         o.batch_block = (int)v;
         break;
     case BFS_OPT_MODE:
-        if (v != MODE_UNITS && v != MODE_BINNED) return bad("MODE must be 0 (units) or 1 (binned)");
+        if (v != MODE_UNITS && v != MODE_BINNED && v != MODE_WARP)
+            return bad("MODE must be 0 (units), 1 (binned) or 2 (warp)");
         o.mode = (int)v;
         break;
     default:
@@ -311,13 +312,15 @@ int bfs_run(bfs_graph *gh, int32_t root, int32_t *level_out, int32_t *parent_out
     }
     // one workspace: a run on another stream waits for the previous run
     if (g->ran && s != g->last_stream) GB_CUDA(cudaStreamWaitEvent(s, g->ws_event, 0));
-    if (g->opt.mode == MODE_UNITS && g->opt.block == 1024)
-        return set_error(BFS_ERR_INVALID_ARG, "bfs_run: the units mode takes BLOCK 256 or 512");
+    if (g->opt.mode != MODE_BINNED && g->opt.block == 1024)
+        return set_error(BFS_ERR_INVALID_ARG, "bfs_run: the units and warp modes take BLOCK 256 or 512");
     int rc;
     if (g->opt.mode == MODE_BINNED) {
         rc = alloc_binned(g);
         if (rc != BFS_OK) return rc;
         rc = td_launch(g, root, d_level, d_parent, s);
+    } else if (g->opt.mode == MODE_WARP) {
+        rc = td_warp_launch(g, root, d_level, d_parent, s);
     } else {
         rc = td_units_launch(g, root, d_level, d_parent, s);
     }

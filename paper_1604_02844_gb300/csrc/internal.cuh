@@ -49,7 +49,7 @@ struct Ctrl {
 using TdCtrl = Ctrl;
 using UnitCtrl = Ctrl;
 
-enum { MODE_UNITS = 0, MODE_BINNED = 1 };
+enum { MODE_UNITS = 0, MODE_BINNED = 1, MODE_WARP = 2 };
 
 struct Options {
     int block = 512;
@@ -108,6 +108,10 @@ int td_launch(Graph *g, int32_t root, int32_t *level, int32_t *parent, cudaStrea
 // implemented in topdown_units.cu (edge-balanced units mode)
 int td_units_launch(Graph *g, int32_t root, int32_t *level, int32_t *parent, cudaStream_t s);
 int64_t td_units_hub_capacity(int64_t m);
+
+// implemented in topdown_warp.cu (warp-private pipelines; shares the units
+// mode's queues)
+int td_warp_launch(Graph *g, int32_t root, int32_t *level, int32_t *parent, cudaStream_t s);
 
 // implemented in msbfs.cu
 int ms_run_batch(Graph *g, const int32_t *roots, int32_t k, uint8_t *level_out);

@@ -520,7 +520,9 @@ int td_units_launch(Graph *g, int32_t root, int32_t *level, int32_t *parent, cud
     }
 }
 
-// hub slices per layer are at most m/T + m/T (+1) with T >= 512
-int64_t td_units_hub_capacity(int64_t m) { return m / 256 + 2; }
+// Hub slices of one layer: a vertex of degree d > T gives ceil(d/T) <= 2d/T
+// slices, so a layer has at most 2m/T of them.  The smallest slice length
+// in use is 256 (the warp mode), hence m/128 (+2).
+int64_t td_units_hub_capacity(int64_t m) { return m / 128 + 2; }
 
 }  // namespace gbbfs

@@ -1,0 +1,572 @@
+// topdown_warp.cu -- single-source level-synchronous top-down BFS with
+// warp-private work pipelines (expansion mode 2).
+//
+// Method as in topdown.cu / topdown_units.cu (Alg. 2 with an atomic
+// visited bitmap, word v>>5 bit v&31 as in Listing 1; P[s] = s; layer L_d
+// finished before L_{d+1}, Sec. 3); one persistent cooperative kernel per
+// search.  The difference is who works together: every warp runs its own
+// pipeline with only __syncwarp, so the 20-30 warps of an SM overlap each
+// other's memory latency instead of meeting at CTA barriers.
+//
+// Frontier layout (built by the warps that discover the vertices):
+//   entry  (u, beg, len), 1 <= len <= W          -- a vertex and its list
+//   unit   (first entry, count), count <= 32, < 2W edges
+//   hub slice (u, beg, len <= W) for vertices of degree > W
+// A warp flushes its shared-memory buffer of newly reached vertices by
+// reserving entries and units with one 64-bit atomicAdd and cutting units
+// where the running edge count crosses a multiple of W or every 32 entries.
+//
+// Work items of a layer (hub slices, then units) are dealt round-robin to
+// the grid's warps.  Per item a warp: stages the adjacency into its shared
+// buffer with cp.async (issued one item ahead), tests the visited word of
+// every staged edge (8 loads per lane in flight) and compacts the unvisited
+// ones in place with ballots (pass A), then claims those with atomicOr and
+// queues the winners (pass B).  Descriptors and entries of the next items
+// are prefetched into registers while the current item is processed.
+//
+// All waits are bounded (grid barrier timeout -> ST_TIMEOUT, clean exit).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "device_common.cuh"
+#include "internal.cuh"
+
+namespace gbbfs {
+namespace {
+
+using namespace dev;
+
+constexpr int W = 256;       // unit edge target and hub slice length
+constexpr int MAXI = 2 * W;  // edges of one work item are < MAXI
+constexpr int OBW = 128;     // out-buffer entries per warp
+constexpr int UA = 8;        // pass A: visited-word loads per lane in flight
+constexpr int UB = 4;        // pass B: claims per lane in flight
+
+struct WParams {
+    const int32_t *__restrict__ ro;
+    const int32_t *__restrict__ col;
+    int32_t *level;
+    int32_t *parent;  // may be null
+    uint32_t *bitmap;
+    int32_t *eu[2], *eb[2], *el[2];  // entries [buffer]
+    int32_t *us[2], *uc[2];          // units [buffer]
+    int32_t *hu[2], *hb[2], *hl[2];  // hub slices [buffer]
+    Ctrl *ctrl;
+    int64_t *stats;  // [kMaxStatLayers][4] or null
+    int32_t n;
+    int32_t root;
+    uint32_t ecap, ucap, hcap;
+    int32_t bitmap_words;
+    uint64_t timeout_ns;
+};
+
+struct WarpSmem {
+    int32_t stage[2][MAXI];  // staged adjacency; pass A compacts candidates in place
+    uint16_t ce[MAXI];       // candidate -> edge index inside the item
+    int32_t off[2][33];      // item entries: prefix of lengths
+    int32_t iu[2][32];       // item entries: vertex
+    int32_t ou[OBW], ob[OBW], ol[OBW];  // out buffer
+    int32_t ust[OBW];        // unit starts during a flush
+};
+
+template <int WPB>
+struct CtaSmem {
+    WarpSmem w[WPB];
+    int ok;
+    unsigned nU, nH;
+    unsigned long long st[3];
+};
+
+// A work item as seen by one lane: the lane's entry (if any) and the item's
+// entry count.
+struct Item {
+    int u, b, l;  // this lane's entry (l = 0 if none)
+    int cnt;      // entries in the item (uniform)
+};
+
+// Descriptor of item `id`: hub slice (id < nH) or unit.  Uniform loads.
+struct Desc {
+    int a, c;  // unit: first entry, count; hub: index into the hub queue, -1
+};
+
+__device__ __forceinline__ Desc load_desc(const WParams &p, int qi, unsigned nH, unsigned n_items, unsigned id)
+{
+    Desc d{0, 0};
+    if (id >= n_items) return d;
+    if (id < nH) {
+        d.a = (int)id;
+        d.c = -1;
+    } else {
+        d.a = __ldcg(p.us[qi] + (id - nH));
+        d.c = __ldcg(p.uc[qi] + (id - nH));
+        if (d.c < 0 || d.c > 32) {  // cannot happen for units cut by warp_flush
+            atomicOr(&p.ctrl->status, ST_OVERFLOW);
+            d.c = 0;
+        }
+    }
+    return d;
+}
+
+__device__ __forceinline__ Item load_item(const WParams &p, int qi, const Desc &d, bool valid)
+{
+    const int lane = threadIdx.x & 31;
+    Item it{0, 0, 0, 0};
+    if (!valid) return it;
+    if (d.c < 0) {
+        it.cnt = 1;
+        if (lane == 0) {
+            it.u = __ldcg(p.hu[qi] + d.a);
+            it.b = __ldcg(p.hb[qi] + d.a);
+            it.l = __ldcg(p.hl[qi] + d.a);
+        }
+    } else {
+        it.cnt = d.c;
+        if (lane < d.c) {
+            it.u = __ldcg(p.eu[qi] + d.a + lane);
+            it.b = __ldcg(p.eb[qi] + d.a + lane);
+            it.l = __ldcg(p.el[qi] + d.a + lane);
+        }
+    }
+    if (it.l < 0 || it.l > MAXI) {
+        atomicOr(&p.ctrl->status, ST_OVERFLOW);
+        it.l = 0;
+    }
+    return it;
+}
+
+// Prefix-sum the item's lengths into off[buf], record vertices, and issue the
+// cp.async copies of its adjacency into stage[buf].  Commits one group per
+// lane.  Returns the item's edge count (uniform).
+__device__ __forceinline__ int stage_item(WarpSmem &ws, const WParams &p, const Item &it, int buf)
+{
+    const int lane = threadIdx.x & 31;
+    int inc = it.l;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(FULL, inc, o);
+        if (lane >= o) inc += y;
+    }
+    int et = __shfl_sync(FULL, inc, 31);
+    if (et >= MAXI) {  // cannot happen: units < 2W edges, slices <= W
+        if (lane == 0) atomicOr(&p.ctrl->status, ST_OVERFLOW);
+        et = 0;
+    }
+    const int off = inc - it.l;
+    if (lane < it.cnt) {
+        ws.off[buf][lane] = off;
+        ws.iu[buf][lane] = it.u;
+    }
+    if (lane == 0) ws.off[buf][it.cnt] = et;
+    if (et > 0) {
+        // short lists: the owning lane copies them
+        if (it.l < 32)
+            for (int k = 0; k < it.l; ++k) cp_async4(&ws.stage[buf][off + k], p.col + it.b + k);
+        // long lists: the whole warp strides over each
+        unsigned big = __ballot_sync(FULL, it.l >= 32);
+        while (big) {
+            const int src = __ffs(big) - 1;
+            big &= big - 1;
+            const int bo = __shfl_sync(FULL, off, src);
+            const int bb = __shfl_sync(FULL, it.b, src);
+            const int bl = __shfl_sync(FULL, it.l, src);
+            for (int k = lane; k < bl; k += 32) cp_async4(&ws.stage[buf][bo + k], p.col + bb + k);
+        }
+    }
+    cp_async_commit();
+    return et;
+}
+
+// Write the warp's out buffer to the entry queue, cut it into units.
+__device__ __noinline__ void warp_flush(WarpSmem &ws, const WParams &p, int set_out, int qo, int c)
+{
+    constexpr int PER = OBW / 32;
+    const int lane = threadIdx.x & 31;
+    const int i0 = min(lane * PER, c), i1 = min(i0 + PER, c);
+    int sum = 0;
+    for (int i = i0; i < i1; ++i) sum += ws.ol[i];
+    int inc = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(FULL, inc, o);
+        if (lane >= o) inc += y;
+    }
+    const int toff = inc - sum;
+    int nu = 0;
+    {
+        int off = toff;
+        for (int i = i0; i < i1; ++i) {
+            const bool start = (i % 32 == 0) || (off / W != (off - ws.ol[i - 1]) / W);
+            nu += start;
+            off += ws.ol[i];
+        }
+    }
+    int uinc = nu;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(FULL, uinc, o);
+        if (lane >= o) uinc += y;
+    }
+    const int units = __shfl_sync(FULL, uinc, 31);
+    unsigned long long base = 0;
+    if (lane == 0)
+        base = atomicAdd(&p.ctrl->eu_count[set_out], ((unsigned long long)units << 32) | (unsigned long long)c);
+    base = __shfl_sync(FULL, base, 0);
+    const unsigned ebase = (unsigned)(base & 0xffffffffull), ubase = (unsigned)(base >> 32);
+    {
+        int k = uinc - nu, off = toff;
+        for (int i = i0; i < i1; ++i) {
+            const bool start = (i % 32 == 0) || (off / W != (off - ws.ol[i - 1]) / W);
+            if (start) ws.ust[k++] = i;
+            off += ws.ol[i];
+        }
+    }
+    __syncwarp();
+    for (int i = lane; i < c; i += 32) {
+        const unsigned gi = ebase + (unsigned)i;
+        if (gi < p.ecap) {
+            p.eu[qo][gi] = ws.ou[i];
+            p.eb[qo][gi] = ws.ob[i];
+            p.el[qo][gi] = ws.ol[i];
+        } else {
+            atomicOr(&p.ctrl->status, ST_OVERFLOW);
+        }
+    }
+    for (int k = lane; k < units; k += 32) {
+        const int s = ws.ust[k];
+        const int e = (k + 1 < units) ? ws.ust[k + 1] : c;
+        const unsigned gk = ubase + (unsigned)k;
+        if (gk < p.ucap) {
+            p.us[qo][gk] = (int32_t)(ebase + (unsigned)s);
+            p.uc[qo][gk] = e - s;
+        } else {
+            atomicOr(&p.ctrl->status, ST_OVERFLOW);
+        }
+    }
+    __syncwarp();
+}
+
+// Passes A and B over the staged item in stage[buf] with `et` edges.
+__device__ __forceinline__ void process_item(WarpSmem &ws, const WParams &p, int buf, int et, int cnt,
+                                             int next_level, int set_out, int qo, int &ocnt, unsigned &my_new)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = lanemask_lt();
+    int32_t *stg = ws.stage[buf];
+    // pass A: visited filter, candidates compacted in place
+    int nc = 0;
+    for (int base = 0; base < et; base += 32 * UA) {
+        int v[UA];
+        unsigned w[UA];
+#pragma unroll
+        for (int k = 0; k < UA; ++k) {
+            const int e = base + k * 32 + lane;
+            v[k] = e < et ? stg[e] : -1;
+        }
+#pragma unroll
+        for (int k = 0; k < UA; ++k) w[k] = v[k] >= 0 ? __ldcg(p.bitmap + ((unsigned)v[k] >> 5)) : 0xffffffffu;
+        __syncwarp();
+#pragma unroll
+        for (int k = 0; k < UA; ++k) {
+            const bool c = v[k] >= 0 && !(w[k] & (1u << (v[k] & 31)));
+            const unsigned m = __ballot_sync(FULL, c);
+            if (c) {
+                const int pos = nc + __popc(m & lt);
+                stg[pos] = v[k];
+                ws.ce[pos] = (uint16_t)(base + k * 32 + lane);
+            }
+            nc += __popc(m);
+        }
+    }
+    __syncwarp();
+    // pass B: claim; winners write level/parent and are queued
+    for (int c0 = 0; c0 < nc; c0 += 32 * UB) {
+        int v[UB], e[UB];
+        bool win[UB];
+#pragma unroll
+        for (int k = 0; k < UB; ++k) {
+            const int i = c0 + k * 32 + lane;
+            v[k] = i < nc ? stg[i] : -1;
+            e[k] = i < nc ? (int)ws.ce[i] : 0;
+        }
+#pragma unroll
+        for (int k = 0; k < UB; ++k) {
+            win[k] = false;
+            if (v[k] >= 0) {
+                const unsigned bit = 1u << (v[k] & 31);
+                win[k] = !(atomicOr(p.bitmap + ((unsigned)v[k] >> 5), bit) & bit);
+            }
+        }
+        int rb[UB], len[UB];
+#pragma unroll
+        for (int k = 0; k < UB; ++k) {
+            rb[k] = 0;
+            len[k] = 0;
+            if (win[k]) {
+                int lo = 0, hi = cnt;  // source entry: largest j with off[j] <= e
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    if (ws.off[buf][mid] <= e[k]) lo = mid;
+                    else hi = mid;
+                }
+                p.level[v[k]] = next_level;
+                if (p.parent) p.parent[v[k]] = ws.iu[buf][lo];
+                rb[k] = __ldg(p.ro + v[k]);
+                len[k] = __ldg(p.ro + v[k] + 1) - rb[k];
+                ++my_new;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < UB; ++k) {
+            const bool small = win[k] && len[k] >= 1 && len[k] <= W;
+            const unsigned m = __ballot_sync(FULL, small);
+            if (m) {
+                if (ocnt + __popc(m) > OBW) {
+                    warp_flush(ws, p, set_out, qo, ocnt);
+                    ocnt = 0;
+                }
+                if (small) {
+                    const int pos = ocnt + __popc(m & lt);
+                    ws.ou[pos] = v[k];
+                    ws.ob[pos] = rb[k];
+                    ws.ol[pos] = len[k];
+                }
+                ocnt += __popc(m);
+            }
+            if (win[k] && len[k] > W) {  // hub: slices of W edges
+                const int nseg = (len[k] + W - 1) / W;
+                unsigned gi = atomicAdd(&p.ctrl->hub_count[set_out], (unsigned)nseg);
+                for (int s = 0; s < nseg; ++s, ++gi) {
+                    if (gi < p.hcap) {
+                        p.hu[qo][gi] = v[k];
+                        p.hb[qo][gi] = rb[k] + s * W;
+                        p.hl[qo][gi] = min(W, len[k] - s * W);
+                    } else {
+                        atomicOr(&p.ctrl->status, ST_OVERFLOW);
+                    }
+                }
+            }
+        }
+    }
+    __syncwarp();
+}
+
+template <int WPB>
+__global__ void __launch_bounds__(WPB * 32, (24 / WPB) > 0 ? (24 / WPB) : 1) td_warp_kernel(WParams p)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    CtaSmem<WPB> &cs = *reinterpret_cast<CtaSmem<WPB> *>(smem_raw);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    WarpSmem &ws = cs.w[warp];
+    const unsigned G = gridDim.x;
+    const unsigned GW = G * WPB;
+    const unsigned gw = blockIdx.x * WPB + warp;
+    Ctrl *c = p.ctrl;
+    const uint64_t t_start = globaltimer();
+
+    // ---- initialisation (Alg. 1: P = infinity except P[s] = s; vis = {s}) --
+    {
+        const int64_t stride = (int64_t)G * WPB * 32;
+        for (int64_t i = (int64_t)blockIdx.x * WPB * 32 + tid; i < p.n; i += stride) {
+            const bool is_root = (i == p.root);
+            p.level[i] = is_root ? 0 : -1;
+            if (p.parent) p.parent[i] = is_root ? p.root : -1;
+        }
+        const int rw = p.root >> 5;
+        for (int64_t w = (int64_t)blockIdx.x * WPB * 32 + tid; w < p.bitmap_words; w += stride)
+            p.bitmap[w] = (w == rw) ? (1u << (p.root & 31)) : 0u;
+        if (blockIdx.x == 0) {
+            if (p.stats)
+                for (int i = tid; i < 4 * kMaxStatLayers; i += WPB * 32) p.stats[i] = 0;
+            if (tid == 0) {
+                const int rb = p.ro[p.root], len = p.ro[p.root + 1] - rb;
+                c->eu_count[0] = 0;
+                c->hub_count[0] = 0;
+                if (len >= 1 && len <= W) {
+                    p.eu[0][0] = p.root;
+                    p.eb[0][0] = rb;
+                    p.el[0][0] = len;
+                    p.us[0][0] = 0;
+                    p.uc[0][0] = 1;
+                    c->eu_count[0] = (1ull << 32) | 1ull;
+                } else if (len > W) {
+                    const int nseg = (len + W - 1) / W;
+                    for (int s = 0; s < nseg && (unsigned)s < p.hcap; ++s) {
+                        p.hu[0][s] = p.root;
+                        p.hb[0][s] = rb + s * W;
+                        p.hl[0][s] = min(W, len - s * W);
+                    }
+                    c->hub_count[0] = (unsigned)nseg;
+                }
+            }
+        }
+    }
+    bool ok = grid_sync(&c->bar_count, &c->bar_gen, &c->status, G, p.timeout_ns, &cs.ok);
+
+    for (int d = 0; ok; ++d) {
+        const int set_in = d % 3, set_out = (d + 1) % 3, set_rst = (d + 2) % 3;
+        if (tid == 0) {
+            const unsigned long long eu = ld_relaxed64(&c->eu_count[set_in]);
+            cs.nU = min((unsigned)(eu >> 32), p.ucap);
+            cs.nH = min(ld_relaxed(&c->hub_count[set_in]), p.hcap);
+            if (p.stats) cs.st[0] = cs.st[1] = cs.st[2] = 0;
+        }
+        __syncthreads();
+        const unsigned nH = cs.nH, n_items = cs.nU + cs.nH;
+        if (n_items == 0) {
+            if (blockIdx.x == 0 && tid == 0) c->layers = (unsigned)d;
+            break;
+        }
+        if (blockIdx.x == 0 && tid == 0) {
+            c->eu_count[set_rst] = 0;
+            c->hub_count[set_rst] = 0;
+        }
+        const int qi = d & 1, qo = qi ^ 1;
+        const int next_level = d + 1;
+        unsigned my_new = 0;
+        unsigned long long my_vertices = 0, my_edges = 0;
+        int ocnt = 0;
+
+        // software pipeline over this warp's items gw, gw+GW, ...
+        unsigned id = gw;
+        Desc d0 = load_desc(p, qi, nH, n_items, id);
+        Item cur = load_item(p, qi, d0, id < n_items);
+        int buf = 0;
+        int et_cur = (id < n_items) ? stage_item(ws, p, cur, buf) : 0;
+        int cnt_cur = cur.cnt;
+        if (id < n_items && lane == 0)
+            my_vertices += (d0.c < 0) ? (cur.b == __ldg(p.ro + cur.u) ? 1 : 0) : (unsigned)cur.cnt;
+        Desc d1 = load_desc(p, qi, nH, n_items, id + GW);
+        Item nxt = load_item(p, qi, d1, id + GW < n_items);
+        Desc d2 = load_desc(p, qi, nH, n_items, id + 2 * GW);
+        while (id < n_items) {
+            const unsigned id1 = id + GW, id2 = id + 2 * GW;
+            int et_nxt = 0;
+            if (id1 < n_items) {
+                et_nxt = stage_item(ws, p, nxt, buf ^ 1);
+                if (lane == 0)
+                    my_vertices += (d1.c < 0) ? (nxt.b == __ldg(p.ro + nxt.u) ? 1 : 0) : (unsigned)nxt.cnt;
+            } else {
+                cp_async_commit();  // keep one group per item on every lane
+            }
+            const int cnt_nxt = nxt.cnt;
+            const Item nn = load_item(p, qi, d2, id2 < n_items);
+            const Desc d3 = load_desc(p, qi, nH, n_items, id2 + GW);
+            asm volatile("cp.async.wait_group 1;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) my_edges += (unsigned long long)et_cur;
+            process_item(ws, p, buf, et_cur, cnt_cur, next_level, set_out, qo, ocnt, my_new);
+            buf ^= 1;
+            id = id1;
+            et_cur = et_nxt;
+            cnt_cur = cnt_nxt;
+            d1 = d2;
+            nxt = nn;
+            d2 = d3;
+        }
+        cp_async_wait_all();
+        __syncwarp();
+        if (ocnt > 0) warp_flush(ws, p, set_out, qo, ocnt);
+
+        if (p.stats && d < kMaxStatLayers) {
+            unsigned long long a = my_vertices, e = my_edges, t = my_new;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                a += __shfl_down_sync(FULL, a, o);
+                e += __shfl_down_sync(FULL, e, o);
+                t += __shfl_down_sync(FULL, t, o);
+            }
+            if (lane == 0) {
+                atomicAdd(&cs.st[0], a);
+                atomicAdd(&cs.st[1], e);
+                atomicAdd(&cs.st[2], t);
+            }
+            __syncthreads();
+            if (tid == 0) {
+                atomicAdd((unsigned long long *)&p.stats[4 * d + 0], cs.st[0]);
+                atomicAdd((unsigned long long *)&p.stats[4 * d + 1], cs.st[1]);
+                atomicAdd((unsigned long long *)&p.stats[4 * d + 2], cs.st[2]);
+            }
+        }
+        ok = grid_sync(&c->bar_count, &c->bar_gen, &c->status, G, p.timeout_ns, &cs.ok);
+        if (p.stats && d < kMaxStatLayers && blockIdx.x == 0 && tid == 0)
+            p.stats[4 * d + 3] = (int64_t)(globaltimer() - t_start);
+    }
+
+    __syncthreads();
+    if (tid == 0) {
+        __threadfence();
+        const unsigned old = atomicAdd(&c->exit_count, 1u);
+        if (old == G - 1) {
+            for (int j = 0; j < 3; ++j) {
+                c->eu_count[j] = 0;
+                c->hub_count[j] = 0;
+                c->work[j] = 0;
+            }
+            c->bar_count = 0;
+            c->exit_count = 0;
+            __threadfence();
+        }
+    }
+}
+
+template <int WPB>
+int launch(Graph *g, const WParams &prm, cudaStream_t s)
+{
+    auto kern = td_warp_kernel<WPB>;
+    const int smem = (int)sizeof(CtaSmem<WPB>);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute(td_warp_kernel)");
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, WPB * 32, smem);
+    if (e != cudaSuccess) return cuda_error(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor(td_warp_kernel)");
+    if (per_sm < 1) return set_error(BFS_ERR_CUDA, "td_warp_kernel: no CTA fits on an SM");
+    if (g->opt.ctas_per_sm > 0) per_sm = std::min(per_sm, g->opt.ctas_per_sm);
+    int grid = per_sm * g->num_sms;
+    if (g->opt.max_ctas > 0) grid = std::min(grid, g->opt.max_ctas);
+    WParams p = prm;
+    void *args[] = {&p};
+    e = cudaLaunchCooperativeKernel((const void *)kern, dim3(grid), dim3(WPB * 32), args, (size_t)smem, s);
+    if (e != cudaSuccess) return cuda_error(e, "cudaLaunchCooperativeKernel(td_warp_kernel)");
+    g->last_grid = grid;
+    return BFS_OK;
+}
+
+}  // namespace
+
+int td_warp_launch(Graph *g, int32_t root, int32_t *level, int32_t *parent, cudaStream_t s)
+{
+    WParams p;
+    p.ro = g->d_row_offsets;
+    p.col = g->d_col_idx;
+    p.level = level;
+    p.parent = parent;
+    p.bitmap = g->d_bitmap;
+    for (int b = 0; b < 2; ++b) {
+        p.eu[b] = g->d_eq[b][0];
+        p.eb[b] = g->d_eq[b][1];
+        p.el[b] = g->d_eq[b][2];
+        p.us[b] = g->d_uq[b][0];
+        p.uc[b] = g->d_uq[b][1];
+        p.hu[b] = g->d_hq[b][0];
+        p.hb[b] = g->d_hq[b][1];
+        p.hl[b] = g->d_hq[b][2];
+    }
+    p.ctrl = g->d_ctrl;
+    p.stats = g->opt.layer_stats ? g->d_stats : nullptr;
+    p.n = (int32_t)g->n;
+    p.root = root;
+    p.ecap = (uint32_t)g->n;
+    p.ucap = (uint32_t)g->n;
+    p.hcap = (uint32_t)std::min<int64_t>(g->hcap, 0x7FFFFFFFLL);
+    p.bitmap_words = (int32_t)g->bitmap_words;
+    p.timeout_ns = (uint64_t)g->opt.timeout_ns;
+    switch (g->opt.block) {
+    case 256: return launch<8>(g, p, s);
+    case 512: return launch<16>(g, p, s);
+    default: return set_error(BFS_ERR_INVALID_ARG, "warp mode supports BLOCK 256 or 512");
+    }
+}
+
+}  // namespace gbbfs

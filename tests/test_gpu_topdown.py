@@ -99,9 +99,8 @@ def test_units_boundaries():
     """Degrees around the unit target T = 2*BLOCK and the hub slice length:
     a root whose neighbours have degrees T-1, T, T+1, 2T, 2T+1, ... exercises
     unit cutting, hub slicing and the last partial slice."""
-    for block in (256, 512):
-        T = 2 * block
-        degs = [1, 2, T - 1, T, T + 1, 2 * T - 1, 2 * T, 2 * T + 1, 5 * T + 3]
+    for mode, block, T in ((0, 256, 512), (0, 512, 1024), (2, 256, 256)):
+        degs = [1, 2, 31, 32, 33, T - 1, T, T + 1, 2 * T - 1, 2 * T, 2 * T + 1, 5 * T + 3]
         edges, nxt = [], 1 + len(degs)
         for i, dgr in enumerate(degs):
             hub = 1 + i
@@ -110,7 +109,7 @@ def test_units_boundaries():
                 edges.append((hub, nxt))
                 nxt += 1
         ro, col = csr_from_edges(nxt, edges, False)
-        with gb.Graph(ro, col, block=block) as g:
+        with gb.Graph(ro, col, block=block, mode=mode) as g:
             for r in (0, 3, nxt - 1):
                 check_root(g, ro, col, r)
 
@@ -173,6 +172,8 @@ def test_long_path_many_layers():
     dict(mode=1, warp_degree=64), dict(mode=1, cta_degree=64, segment=256),
     dict(mode=1, cta_degree=100000), dict(mode=1, max_ctas=1), dict(mode=1, max_ctas=7, block=256),
     dict(mode=1, ctas_per_sm=1), dict(mode=1, layer_stats=1),
+    dict(mode=2), dict(mode=2, block=512), dict(mode=2, max_ctas=1), dict(mode=2, max_ctas=5),
+    dict(mode=2, ctas_per_sm=1), dict(mode=2, layer_stats=1),
 ], ids=lambda o: ",".join(f"{k}={v}" for k, v in o.items()))
 def test_options_keep_results_exact(opts):
     ro, col = graphgen.kronecker(14, 16, 6)
@@ -230,7 +231,7 @@ def test_device_resident_inputs_and_streams():
         np.testing.assert_array_equal(lv.cpu().numpy(), ref)
 
 
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 2])
 def test_layer_stats_match_table1_columns(mode):
     ro, col = graphgen.kronecker(16, 16, 1)
     with gb.Graph(ro, col, layer_stats=1, mode=mode) as g:
@@ -245,12 +246,21 @@ def test_layer_stats_match_table1_columns(mode):
             assert len(times) == len(v) and np.all(np.diff(times) >= 0) and times[0] > 0
 
 
-def test_units_mode_rejects_block_1024():
+@pytest.mark.parametrize("mode", [0, 2])
+def test_units_modes_reject_block_1024(mode):
     ro, col, _ = path_graph(10, 0)
-    with gb.Graph(ro, col, block=1024) as g:
+    with gb.Graph(ro, col, block=1024, mode=mode) as g:
         with pytest.raises(gb.BfsError) as ei:
             g.run(0)
         assert ei.value.status == gb.BFS_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_modes_agree_on_kronecker_scale18(mode):
+    ro, col = graphgen.kronecker(18, 16, 2)
+    with gb.Graph(ro, col, mode=mode) as g:
+        for r in graphgen.pick_roots(ro, 6, 2):
+            check_root(g, ro, col, r)
 
 
 def test_invalid_csr_rejected_on_device():
