@@ -137,8 +137,12 @@ __device__ __forceinline__ Item load_item(const WParams &p, int qi, const Desc &
 }
 
 // Prefix-sum the item's lengths into off[buf], record vertices, and issue the
-// cp.async copies of its adjacency into stage[buf].  Commits one group per
-// lane.  Returns the item's edge count (uniform).
+// cp.async copies of its adjacency into stage[buf].  Consecutive lanes copy
+// consecutive edges of the concatenated lists (coalesced); the entry of each
+// edge comes from a warp-level search: the entries starting inside a batch
+// of 32 edges form a bit mask (redux.or), and a popc over it counts the
+// entry boundaries before each lane.  Commits one group per lane.  Returns
+// the item's edge count (uniform).
 __device__ __forceinline__ int stage_item(WarpSmem &ws, const WParams &p, const Item &it, int buf)
 {
     const int lane = threadIdx.x & 31;
@@ -154,25 +158,21 @@ __device__ __forceinline__ int stage_item(WarpSmem &ws, const WParams &p, const 
         et = 0;
     }
     const int off = inc - it.l;
-    if (lane < it.cnt) {
+    const bool real = lane < it.cnt;
+    if (real) {
         ws.off[buf][lane] = off;
         ws.iu[buf][lane] = it.u;
     }
     if (lane == 0) ws.off[buf][it.cnt] = et;
-    if (et > 0) {
-        // short lists: the owning lane copies them
-        if (it.l < 32)
-            for (int k = 0; k < it.l; ++k) cp_async4(&ws.stage[buf][off + k], p.col + it.b + k);
-        // long lists: the whole warp strides over each
-        unsigned big = __ballot_sync(FULL, it.l >= 32);
-        while (big) {
-            const int src = __ffs(big) - 1;
-            big &= big - 1;
-            const int bo = __shfl_sync(FULL, off, src);
-            const int bb = __shfl_sync(FULL, it.b, src);
-            const int bl = __shfl_sync(FULL, it.l, src);
-            for (int k = lane; k < bl; k += 32) cp_async4(&ws.stage[buf][bo + k], p.col + bb + k);
-        }
+    for (int base = 0; base < et; base += 32) {
+        unsigned starts = (real && off > base && off < base + 32) ? (1u << (off - base)) : 0u;
+        starts = __reduce_or_sync(FULL, starts);
+        const int j0 = __popc(__ballot_sync(FULL, real && off <= base)) - 1;
+        const int j = j0 + __popc(starts & ((2u << lane) - 1u));
+        const int jb = __shfl_sync(FULL, it.b, j & 31);
+        const int jo = __shfl_sync(FULL, off, j & 31);
+        const int e = base + lane;
+        if (e < et) cp_async4(&ws.stage[buf][e], p.col + jb + (e - jo));
     }
     cp_async_commit();
     return et;
@@ -265,7 +265,9 @@ __device__ __forceinline__ void process_item(WarpSmem &ws, const WParams &p, int
             v[k] = e < et ? stg[e] : -1;
         }
 #pragma unroll
-        for (int k = 0; k < UA; ++k) w[k] = v[k] >= 0 ? __ldcg(p.bitmap + ((unsigned)v[k] >> 5)) : 0xffffffffu;
+        // L1-cached read: bits are only ever set during a search, so a stale
+        // word can only send an already visited vertex on to the atomicOr
+        for (int k = 0; k < UA; ++k) w[k] = v[k] >= 0 ? __ldca(p.bitmap + ((unsigned)v[k] >> 5)) : 0xffffffffu;
         __syncwarp();
 #pragma unroll
         for (int k = 0; k < UA; ++k) {
@@ -334,14 +336,24 @@ __device__ __forceinline__ void process_item(WarpSmem &ws, const WParams &p, int
                 }
                 ocnt += __popc(m);
             }
-            if (win[k] && len[k] > W) {  // hub: slices of W edges
-                const int nseg = (len[k] + W - 1) / W;
-                unsigned gi = atomicAdd(&p.ctrl->hub_count[set_out], (unsigned)nseg);
-                for (int s = 0; s < nseg; ++s, ++gi) {
-                    if (gi < p.hcap) {
-                        p.hu[qo][gi] = v[k];
-                        p.hb[qo][gi] = rb[k] + s * W;
-                        p.hl[qo][gi] = min(W, len[k] - s * W);
+            // hubs: slices of W edges, written by the whole warp
+            unsigned hm = __ballot_sync(FULL, win[k] && len[k] > W);
+            while (hm) {
+                const int src = __ffs(hm) - 1;
+                hm &= hm - 1;
+                const int hv = __shfl_sync(FULL, v[k], src);
+                const int hb = __shfl_sync(FULL, rb[k], src);
+                const int hl = __shfl_sync(FULL, len[k], src);
+                const int nseg = (hl + W - 1) / W;
+                unsigned gi = 0;
+                if (lane == 0) gi = atomicAdd(&p.ctrl->hub_count[set_out], (unsigned)nseg);
+                gi = __shfl_sync(FULL, gi, 0);
+                for (int s = lane; s < nseg; s += 32) {
+                    const unsigned g = gi + (unsigned)s;
+                    if (g < p.hcap) {
+                        p.hu[qo][g] = hv;
+                        p.hb[qo][g] = hb + s * W;
+                        p.hl[qo][g] = min(W, hl - s * W);
                     } else {
                         atomicOr(&p.ctrl->status, ST_OVERFLOW);
                     }
