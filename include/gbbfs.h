@@ -105,7 +105,10 @@ int bfs_last_status(void);
  * The library copies both arrays into device memory it owns; the caller
  * keeps ownership of its arrays.  The copy is validated on the device:
  * row_offsets[0] == 0, non-decreasing, row_offsets[n] == m, and every
- * column in [0, n).  On any failure returns NULL and sets bfs_last_status()
+ * column in [0, n).  Internally the vertices are renumbered by decreasing
+ * degree class (hubs first) so that the visited-bit tests of most edges hit
+ * a small, cache-resident part of the bitmap; every result is returned in
+ * the caller's numbering.  On any failure returns NULL and sets bfs_last_status()
  * to BFS_ERR_INVALID_GRAPH, BFS_ERR_INVALID_ARG, BFS_ERR_OOM or
  * BFS_ERR_CUDA.  Synchronous (returns once the graph is resident).
  */
@@ -118,10 +121,6 @@ int bfs_graph_destroy(bfs_graph *g);
 
 int64_t bfs_graph_num_vertices(const bfs_graph *g);
 int64_t bfs_graph_num_edges(const bfs_graph *g);
-
-/* Device pointers of the library-owned CSR copy (read-only for callers). */
-const int32_t *bfs_graph_device_row_offsets(const bfs_graph *g);
-const int32_t *bfs_graph_device_col_idx(const bfs_graph *g);
 
 /* Set / read a tunable.  Invalid values give BFS_ERR_INVALID_ARG. */
 int bfs_graph_set_option(bfs_graph *g, int option, int64_t value);

@@ -66,8 +66,6 @@ SIGNATURES = {
     "bfs_graph_destroy": (_INT, [_P]),
     "bfs_graph_num_vertices": (_I64, [_P]),
     "bfs_graph_num_edges": (_I64, [_P]),
-    "bfs_graph_device_row_offsets": (_P, [_P]),
-    "bfs_graph_device_col_idx": (_P, [_P]),
     "bfs_graph_set_option": (_INT, [_P, _INT, _I64]),
     "bfs_graph_get_option": (_I64, [_P, _INT]),
     "bfs_run": (_INT, [_P, _I32, _P, _P, _P]),

@@ -72,6 +72,8 @@ static void free_graph(Graph *g)
     ms_free(g);
     cudaFree(g->d_row_offsets);
     cudaFree(g->d_col_idx);
+    cudaFree(g->d_perm);
+    cudaFree(g->d_orig);
     cudaFree(g->d_bitmap);
     for (int b = 0; b < 2; ++b) {
         for (int j = 0; j < 3; ++j) {
@@ -144,32 +146,49 @@ bfs_graph *bfs_graph_create(const int32_t *row_offsets, const int32_t *col_idx, 
     if ((e = cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device)) != cudaSuccess)
         return fail(e, "cudaDeviceGetAttribute");
 
-    const int64_t col_alloc = ((m + 3) / 4) * 4 + 4;  // 16-byte tail for vector reads
-    if ((e = cudaMalloc(&g->d_row_offsets, (size_t)(n + 1) * 4)) != cudaSuccess) return fail(e, "cudaMalloc(row_offsets)");
-    if ((e = cudaMalloc(&g->d_col_idx, (size_t)col_alloc * 4)) != cudaSuccess) return fail(e, "cudaMalloc(col_idx)");
-    if ((e = cudaMemcpy(g->d_row_offsets, row_offsets, (size_t)(n + 1) * 4, cudaMemcpyDefault)) != cudaSuccess)
-        return fail(e, "cudaMemcpy(row_offsets)");
-    if (m > 0 && (e = cudaMemcpy(g->d_col_idx, col_idx, (size_t)m * 4, cudaMemcpyDefault)) != cudaSuccess)
-        return fail(e, "cudaMemcpy(col_idx)");
-    if ((e = cudaMemset(g->d_col_idx + m, 0, (size_t)(col_alloc - m) * 4)) != cudaSuccess) return fail(e, "cudaMemset(col tail)");
+    // the caller's CSR, copied to temporary device arrays and validated there
+    int32_t *t_ro = nullptr, *t_col = nullptr;
+    auto fail_tmp = [&](cudaError_t e2, const char *what) -> bfs_graph * {
+        cudaFree(t_ro);
+        cudaFree(t_col);
+        return fail(e2, what);
+    };
+    if ((e = cudaMalloc(&t_ro, (size_t)(n + 1) * 4)) != cudaSuccess) return fail_tmp(e, "cudaMalloc(row_offsets copy)");
+    if ((e = cudaMalloc(&t_col, (size_t)std::max<int64_t>(m, 1) * 4)) != cudaSuccess) return fail_tmp(e, "cudaMalloc(col_idx copy)");
+    if ((e = cudaMemcpy(t_ro, row_offsets, (size_t)(n + 1) * 4, cudaMemcpyDefault)) != cudaSuccess)
+        return fail_tmp(e, "cudaMemcpy(row_offsets)");
+    if (m > 0 && (e = cudaMemcpy(t_col, col_idx, (size_t)m * 4, cudaMemcpyDefault)) != cudaSuccess)
+        return fail_tmp(e, "cudaMemcpy(col_idx)");
 
     // validation
     unsigned *d_flags = nullptr;
-    if ((e = cudaMalloc(&d_flags, sizeof(unsigned))) != cudaSuccess) return fail(e, "cudaMalloc(flags)");
+    if ((e = cudaMalloc(&d_flags, sizeof(unsigned))) != cudaSuccess) return fail_tmp(e, "cudaMalloc(flags)");
     cudaMemset(d_flags, 0, sizeof(unsigned));
-    validate_csr_kernel<<<g->num_sms * 4, 256>>>(g->d_row_offsets, g->d_col_idx, n, m, d_flags);
+    validate_csr_kernel<<<g->num_sms * 4, 256>>>(t_ro, t_col, n, m, d_flags);
     unsigned flags = 0;
     e = cudaMemcpy(&flags, d_flags, sizeof(unsigned), cudaMemcpyDeviceToHost);
     cudaFree(d_flags);
-    if (e != cudaSuccess) return fail(e, "validate_csr_kernel");
+    if (e != cudaSuccess) return fail_tmp(e, "validate_csr_kernel");
     if (flags) {
         std::string why;
         if (flags & 4u) why += " row_offsets[0] != 0 or row_offsets[n] != m;";
         if (flags & 1u) why += " row_offsets not non-decreasing within [0, m];";
         if (flags & 2u) why += " a column index outside [0, n);";
         set_error(BFS_ERR_INVALID_GRAPH, "bfs_graph_create: invalid CSR:" + why);
+        cudaFree(t_ro);
+        cudaFree(t_col);
         free_graph(g);
         return nullptr;
+    }
+    // internal degree-ordered numbering (relabel.cu)
+    {
+        const int rc = relabel_graph(g, t_ro, t_col);
+        cudaFree(t_ro);
+        cudaFree(t_col);
+        if (rc != BFS_OK) {
+            free_graph(g);
+            return nullptr;
+        }
     }
 
     // single-source workspace (units mode; the binned-mode queues are lazy)
@@ -207,8 +226,6 @@ int bfs_graph_destroy(bfs_graph *gh)
 
 int64_t bfs_graph_num_vertices(const bfs_graph *gh) { return gh ? reinterpret_cast<const Graph *>(gh)->n : -1; }
 int64_t bfs_graph_num_edges(const bfs_graph *gh) { return gh ? reinterpret_cast<const Graph *>(gh)->m : -1; }
-const int32_t *bfs_graph_device_row_offsets(const bfs_graph *gh) { return gh ? reinterpret_cast<const Graph *>(gh)->d_row_offsets : nullptr; }
-const int32_t *bfs_graph_device_col_idx(const bfs_graph *gh) { return gh ? reinterpret_cast<const Graph *>(gh)->d_col_idx : nullptr; }
 
 int bfs_graph_set_option(bfs_graph *gh, int option, int64_t v)
 {
@@ -395,8 +412,15 @@ int bfs_graph_visited_bitmap(bfs_graph *gh, uint32_t *words_out, int64_t nwords)
     if (nwords < need) return set_error(BFS_ERR_INVALID_ARG, "bfs_graph_visited_bitmap: nwords < ceil(n/32)");
     std::lock_guard<std::mutex> lk(g->mu);
     if (g->ran) GB_CUDA(cudaEventSynchronize(g->ws_event));
-    GB_CUDA(cudaMemcpy(words_out, g->d_bitmap, (size_t)need * 4, cudaMemcpyDeviceToHost));
-    return BFS_OK;
+    uint32_t *d_out = nullptr;
+    GB_CUDA(cudaMalloc(&d_out, (size_t)need * 4));
+    int rc = bitmap_to_caller(g, d_out);
+    if (rc == BFS_OK) {
+        cudaError_t e = cudaMemcpy(words_out, d_out, (size_t)need * 4, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) rc = cuda_error(e, "cudaMemcpy(bitmap)");
+    }
+    cudaFree(d_out);
+    return rc;
 }
 
 int bfs_run_batch(bfs_graph *gh, const int32_t *roots, int32_t k, uint8_t *level_out)

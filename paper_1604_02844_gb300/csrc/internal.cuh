@@ -71,8 +71,11 @@ struct Graph {
     int device = 0;
     int num_sms = 0;
     int64_t n = 0, m = 0;
+    // CSR in the library's internal numbering (degree-ordered, relabel.cu)
     int32_t *d_row_offsets = nullptr;
     int32_t *d_col_idx = nullptr;  // padded: m rounded up to 4, plus 4 entries
+    int32_t *d_perm = nullptr;     // caller id -> internal id
+    int32_t *d_orig = nullptr;     // internal id -> caller id
 
     // single-source workspace
     uint32_t *d_bitmap = nullptr;  // words rounded up to a multiple of 4
@@ -116,6 +119,10 @@ int td_warp_launch(Graph *g, int32_t root, int32_t *level, int32_t *parent, cuda
 // implemented in msbfs.cu
 int ms_run_batch(Graph *g, const int32_t *roots, int32_t k, uint8_t *level_out);
 void ms_free(Graph *g);
+
+// implemented in relabel.cu
+int relabel_graph(Graph *g, const int32_t *d_ro, const int32_t *d_col);
+int bitmap_to_caller(Graph *g, uint32_t *d_out);
 
 bool is_device_pointer(const void *p);
 

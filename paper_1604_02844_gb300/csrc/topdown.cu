@@ -46,6 +46,8 @@ struct TdParams {
     const int32_t *__restrict__ col;
     int32_t *level;
     int32_t *parent;  // may be null
+    const int32_t *__restrict__ perm;  // caller id -> internal id
+    const int32_t *__restrict__ orig;  // internal id -> caller id
     uint32_t *bitmap;
     int32_t *qu[2], *qb[2], *ql[2];  // small-item queue [buffer]
     int32_t *bu[2], *bb[2], *bl[2];  // large-item queue [buffer]
@@ -175,8 +177,9 @@ __device__ __forceinline__ void visit(bool valid, int v, int u, int next_level, 
     }
     int rb = 0, len = 0;
     if (win) {
-        p.level[v] = next_level;
-        if (p.parent) p.parent[v] = u;
+        const int ov = __ldg(p.orig + v);  // results leave in the caller's numbering
+        p.level[ov] = next_level;
+        if (p.parent) p.parent[ov] = __ldg(p.orig + u);
         rb = __ldg(p.ro + v);
         len = __ldg(p.ro + v + 1) - rb;
         ++my_new;
@@ -280,24 +283,25 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) td_kernel(TdParams p)
             p.level[i] = is_root ? 0 : -1;
             if (p.parent) p.parent[i] = is_root ? p.root : -1;
         }
-        const int rw = p.root >> 5;
+        const int rint = __ldg(p.perm + p.root);  // the root in internal numbering
+        const int rw = rint >> 5;
         for (int64_t w = (int64_t)blockIdx.x * BLOCK + tid; w < p.bitmap_words; w += stride)
-            p.bitmap[w] = (w == rw) ? (1u << (p.root & 31)) : 0u;
+            p.bitmap[w] = (w == rw) ? (1u << (rint & 31)) : 0u;
         if (blockIdx.x == 0) {
             if (p.stats)
                 for (int i = tid; i < 4 * kMaxStatLayers; i += BLOCK) p.stats[i] = 0;
             if (tid == 0) {
-                const int rb = p.ro[p.root], len = p.ro[p.root + 1] - rb;
+                const int rb = p.ro[rint], len = p.ro[rint + 1] - rb;
                 unsigned cnt = 0, bcnt = 0;
                 if (len > 0 && len < p.cta_degree) {
-                    p.qu[0][0] = p.root;
+                    p.qu[0][0] = rint;
                     p.qb[0][0] = rb;
                     p.ql[0][0] = len;
                     cnt = 1;
                 } else if (len >= p.cta_degree) {
                     const int nseg = (len + p.segment - 1) / p.segment;
                     for (int s = 0; s < nseg && (unsigned)s < p.bqcap; ++s) {
-                        p.bu[0][s] = p.root;
+                        p.bu[0][s] = rint;
                         p.bb[0][s] = rb + s * p.segment;
                         p.bl[0][s] = min(p.segment, len - s * p.segment);
                     }
@@ -488,6 +492,8 @@ int td_launch(Graph *g, int32_t root, int32_t *level, int32_t *parent, cudaStrea
     p.col = g->d_col_idx;
     p.level = level;
     p.parent = parent;
+    p.perm = g->d_perm;
+    p.orig = g->d_orig;
     p.bitmap = g->d_bitmap;
     for (int b = 0; b < 2; ++b) {
         p.qu[b] = g->d_q[b][0];

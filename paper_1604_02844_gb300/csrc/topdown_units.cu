@@ -46,6 +46,8 @@ struct UParams {
     const int32_t *__restrict__ col;
     int32_t *level;
     int32_t *parent;  // may be null
+    const int32_t *__restrict__ perm;  // caller id -> internal id
+    const int32_t *__restrict__ orig;  // internal id -> caller id
     uint32_t *bitmap;
     int32_t *eu[2], *eb[2], *el[2];  // entry queue [buffer]: vertex, adjacency begin, length
     int32_t *us[2], *uc[2];          // unit queue [buffer]: first entry, entry count
@@ -117,7 +119,7 @@ __device__ void load_and_stage(Smem<BLOCK> &sm, const UParams &p, int qi, unsign
             sm.ib[0] = b;
             sm.off[0] = 0;
             sm.off[1] = l;
-            my_vertices += (b == __ldg(p.ro + u)) ? 1ull : 0ull;
+            if (p.stats) my_vertices += (b == __ldg(p.ro + u)) ? 1ull : 0ull;
         }
         __syncthreads();
     } else {
@@ -275,8 +277,9 @@ __device__ void process_item(Smem<BLOCK> &sm, const UParams &p, int buf, int et,
             rb[k] = 0;
             len[k] = 0;
             if (win[k]) {
-                p.level[v[k]] = next_level;
-                if (p.parent) p.parent[v[k]] = u[k];
+                const int ov = __ldg(p.orig + v[k]);  // results leave in the caller's numbering
+                p.level[ov] = next_level;
+                if (p.parent) p.parent[ov] = __ldg(p.orig + u[k]);
                 rb[k] = __ldg(p.ro + v[k]);
                 len[k] = __ldg(p.ro + v[k] + 1) - rb[k];
                 ++my_new;
@@ -330,16 +333,17 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) td_units_kernel(UParams p
             p.level[i] = is_root ? 0 : -1;
             if (p.parent) p.parent[i] = is_root ? p.root : -1;
         }
-        const int rw = p.root >> 5;
+        const int rint = __ldg(p.perm + p.root);  // the root in internal numbering
+        const int rw = rint >> 5;
         for (int64_t w = (int64_t)blockIdx.x * BLOCK + tid; w < p.bitmap_words; w += stride)
-            p.bitmap[w] = (w == rw) ? (1u << (p.root & 31)) : 0u;
+            p.bitmap[w] = (w == rw) ? (1u << (rint & 31)) : 0u;
         if (blockIdx.x == 0) {
             if (p.stats)
                 for (int i = tid; i < 4 * kMaxStatLayers; i += BLOCK) p.stats[i] = 0;
             if (tid == 0) {
-                const int rb = p.ro[p.root], len = p.ro[p.root + 1] - rb;
+                const int rb = p.ro[rint], len = p.ro[rint + 1] - rb;
                 if (len >= 1 && len <= T) {
-                    p.eu[0][0] = p.root;
+                    p.eu[0][0] = rint;
                     p.eb[0][0] = rb;
                     p.el[0][0] = len;
                     p.us[0][0] = 0;
@@ -349,7 +353,7 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) td_units_kernel(UParams p
                 } else if (len > T) {
                     const int nseg = (len + T - 1) / T;
                     for (int s = 0; s < nseg && (unsigned)s < p.hcap; ++s) {
-                        p.hu[0][s] = p.root;
+                        p.hu[0][s] = rint;
                         p.hb[0][s] = rb + s * T;
                         p.hl[0][s] = min(T, len - s * T);
                     }
@@ -493,6 +497,8 @@ int td_units_launch(Graph *g, int32_t root, int32_t *level, int32_t *parent, cud
     p.col = g->d_col_idx;
     p.level = level;
     p.parent = parent;
+    p.perm = g->d_perm;
+    p.orig = g->d_orig;
     p.bitmap = g->d_bitmap;
     for (int b = 0; b < 2; ++b) {
         p.eu[b] = g->d_eq[b][0];

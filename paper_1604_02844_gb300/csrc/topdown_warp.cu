@@ -49,6 +49,8 @@ struct WParams {
     const int32_t *__restrict__ col;
     int32_t *level;
     int32_t *parent;  // may be null
+    const int32_t *__restrict__ perm;  // caller id -> internal id
+    const int32_t *__restrict__ orig;  // internal id -> caller id
     uint32_t *bitmap;
     int32_t *eu[2], *eb[2], *el[2];  // entries [buffer]
     int32_t *us[2], *uc[2];          // units [buffer]
@@ -101,12 +103,8 @@ __device__ __forceinline__ Desc load_desc(const WParams &p, int qi, unsigned nH,
     } else {
         d.a = __ldcg(p.us[qi] + (id - nH));
         d.c = __ldcg(p.uc[qi] + (id - nH));
-        if (d.c < 0 || d.c > 32) {  // cannot happen for units cut by warp_flush
-            atomicOr(&p.ctrl->status, ST_OVERFLOW);
-            d.c = 0;
-        }
     }
-    return d;
+    return d;  // checked where it is used, so the loads stay in flight
 }
 
 __device__ __forceinline__ Item load_item(const WParams &p, int qi, const Desc &d, bool valid)
@@ -122,18 +120,15 @@ __device__ __forceinline__ Item load_item(const WParams &p, int qi, const Desc &
             it.l = __ldcg(p.hl[qi] + d.a);
         }
     } else {
-        it.cnt = d.c;
-        if (lane < d.c) {
+        it.cnt = (d.c < 0 || d.c > 32) ? 0 : d.c;  // a unit holds <= 32 entries
+        if (it.cnt != d.c && lane == 0) atomicOr(&p.ctrl->status, ST_OVERFLOW);
+        if (lane < it.cnt) {
             it.u = __ldcg(p.eu[qi] + d.a + lane);
             it.b = __ldcg(p.eb[qi] + d.a + lane);
             it.l = __ldcg(p.el[qi] + d.a + lane);
         }
     }
-    if (it.l < 0 || it.l > MAXI) {
-        atomicOr(&p.ctrl->status, ST_OVERFLOW);
-        it.l = 0;
-    }
-    return it;
+    return it;  // lengths are checked in stage_item, so the loads stay in flight
 }
 
 // Prefix-sum the item's lengths into off[buf], record vertices, and issue the
@@ -143,9 +138,14 @@ __device__ __forceinline__ Item load_item(const WParams &p, int qi, const Desc &
 // of 32 edges form a bit mask (redux.or), and a popc over it counts the
 // entry boundaries before each lane.  Commits one group per lane.  Returns
 // the item's edge count (uniform).
-__device__ __forceinline__ int stage_item(WarpSmem &ws, const WParams &p, const Item &it, int buf)
+__device__ __forceinline__ int stage_item(WarpSmem &ws, const WParams &p, const Item &it_in, int buf)
 {
     const int lane = threadIdx.x & 31;
+    Item it = it_in;
+    if (it.l < 0 || it.l > MAXI) {  // cannot happen for entries this kernel wrote
+        atomicOr(&p.ctrl->status, ST_OVERFLOW);
+        it.l = 0;
+    }
     int inc = it.l;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -312,8 +312,9 @@ __device__ __forceinline__ void process_item(WarpSmem &ws, const WParams &p, int
                     if (ws.off[buf][mid] <= e[k]) lo = mid;
                     else hi = mid;
                 }
-                p.level[v[k]] = next_level;
-                if (p.parent) p.parent[v[k]] = ws.iu[buf][lo];
+                const int ov = __ldg(p.orig + v[k]);  // results leave in the caller's numbering
+                p.level[ov] = next_level;
+                if (p.parent) p.parent[ov] = __ldg(p.orig + ws.iu[buf][lo]);
                 rb[k] = __ldg(p.ro + v[k]);
                 len[k] = __ldg(p.ro + v[k] + 1) - rb[k];
                 ++my_new;
@@ -385,18 +386,19 @@ __global__ void __launch_bounds__(WPB * 32, (24 / WPB) > 0 ? (24 / WPB) : 1) td_
             p.level[i] = is_root ? 0 : -1;
             if (p.parent) p.parent[i] = is_root ? p.root : -1;
         }
-        const int rw = p.root >> 5;
+        const int rint = __ldg(p.perm + p.root);  // the root in internal numbering
+        const int rw = rint >> 5;
         for (int64_t w = (int64_t)blockIdx.x * WPB * 32 + tid; w < p.bitmap_words; w += stride)
-            p.bitmap[w] = (w == rw) ? (1u << (p.root & 31)) : 0u;
+            p.bitmap[w] = (w == rw) ? (1u << (rint & 31)) : 0u;
         if (blockIdx.x == 0) {
             if (p.stats)
                 for (int i = tid; i < 4 * kMaxStatLayers; i += WPB * 32) p.stats[i] = 0;
             if (tid == 0) {
-                const int rb = p.ro[p.root], len = p.ro[p.root + 1] - rb;
+                const int rb = p.ro[rint], len = p.ro[rint + 1] - rb;
                 c->eu_count[0] = 0;
                 c->hub_count[0] = 0;
                 if (len >= 1 && len <= W) {
-                    p.eu[0][0] = p.root;
+                    p.eu[0][0] = rint;
                     p.eb[0][0] = rb;
                     p.el[0][0] = len;
                     p.us[0][0] = 0;
@@ -405,7 +407,7 @@ __global__ void __launch_bounds__(WPB * 32, (24 / WPB) > 0 ? (24 / WPB) : 1) td_
                 } else if (len > W) {
                     const int nseg = (len + W - 1) / W;
                     for (int s = 0; s < nseg && (unsigned)s < p.hcap; ++s) {
-                        p.hu[0][s] = p.root;
+                        p.hu[0][s] = rint;
                         p.hb[0][s] = rb + s * W;
                         p.hl[0][s] = min(W, len - s * W);
                     }
@@ -447,7 +449,7 @@ __global__ void __launch_bounds__(WPB * 32, (24 / WPB) > 0 ? (24 / WPB) : 1) td_
         int buf = 0;
         int et_cur = (id < n_items) ? stage_item(ws, p, cur, buf) : 0;
         int cnt_cur = cur.cnt;
-        if (id < n_items && lane == 0)
+        if (p.stats && id < n_items && lane == 0)
             my_vertices += (d0.c < 0) ? (cur.b == __ldg(p.ro + cur.u) ? 1 : 0) : (unsigned)cur.cnt;
         Desc d1 = load_desc(p, qi, nH, n_items, id + GW);
         Item nxt = load_item(p, qi, d1, id + GW < n_items);
@@ -457,7 +459,7 @@ __global__ void __launch_bounds__(WPB * 32, (24 / WPB) > 0 ? (24 / WPB) : 1) td_
             int et_nxt = 0;
             if (id1 < n_items) {
                 et_nxt = stage_item(ws, p, nxt, buf ^ 1);
-                if (lane == 0)
+                if (p.stats && lane == 0)
                     my_vertices += (d1.c < 0) ? (nxt.b == __ldg(p.ro + nxt.u) ? 1 : 0) : (unsigned)nxt.cnt;
             } else {
                 cp_async_commit();  // keep one group per item on every lane
@@ -554,6 +556,8 @@ int td_warp_launch(Graph *g, int32_t root, int32_t *level, int32_t *parent, cuda
     p.col = g->d_col_idx;
     p.level = level;
     p.parent = parent;
+    p.perm = g->d_perm;
+    p.orig = g->d_orig;
     p.bitmap = g->d_bitmap;
     for (int b = 0; b < 2; ++b) {
         p.eu[b] = g->d_eq[b][0];
