@@ -42,7 +42,7 @@ constexpr int W = 256;       // unit edge target and hub slice length
 constexpr int MAXI = 2 * W;  // edges of one work item are < MAXI
 constexpr int OBW = 128;     // out-buffer entries per warp
 constexpr int UA = 8;        // pass A: visited-word loads per lane in flight
-constexpr int UB = 4;        // pass B: claims per lane in flight
+constexpr int UB = 2;        // pass B: claims per lane in flight
 
 struct WParams {
     const int32_t *__restrict__ ro;
@@ -69,8 +69,9 @@ struct WarpSmem {
     uint16_t ce[MAXI];       // candidate -> edge index inside the item
     int32_t off[2][33];      // item entries: prefix of lengths
     int32_t iu[2][32];       // item entries: vertex
-    int32_t ou[OBW], ob[OBW], ol[OBW];  // out buffer
-    int32_t ust[OBW];        // unit starts during a flush
+    int32_t wv[OBW], wu[OBW];           // claimed vertices and their sources (internal ids)
+    int32_t ou[OBW], ob[OBW], ol[OBW];  // flush: the new frontier entries
+    int32_t ust[OBW];                   // flush: unit starts
 };
 
 template <int WPB>
@@ -164,6 +165,7 @@ __device__ __forceinline__ int stage_item(WarpSmem &ws, const WParams &p, const 
         ws.iu[buf][lane] = it.u;
     }
     if (lane == 0) ws.off[buf][it.cnt] = et;
+#pragma unroll 4
     for (int base = 0; base < et; base += 32) {
         unsigned starts = (real && off > base && off < base + 32) ? (1u << (off - base)) : 0u;
         starts = __reduce_or_sync(FULL, starts);
@@ -178,14 +180,135 @@ __device__ __forceinline__ int stage_item(WarpSmem &ws, const WParams &p, const 
     return et;
 }
 
-// Write the warp's out buffer to the entry queue, cut it into units.
-__device__ __noinline__ void warp_flush(WarpSmem &ws, const WParams &p, int set_out, int qo, int c)
+// Finish the vertices this warp claimed: write level and parent (in the
+// caller's numbering), read each one's adjacency range, queue the short
+// ones as frontier entries cut into units and the hubs as slices.  All loads
+// of a lane are issued together, so one flush costs about one round trip.
+__device__ __forceinline__ void warp_flush(WarpSmem &ws, const WParams &p, int set_out, int qo, int c,
+                                        int next_level)
 {
     constexpr int PER = OBW / 32;
     const int lane = threadIdx.x & 31;
+    const unsigned lt = lanemask_lt();
     const int i0 = min(lane * PER, c), i1 = min(i0 + PER, c);
+    int rb[PER], re[PER], ov[PER], ou[PER];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int i = i0 + k;
+        if (i < i1) {
+            const int v = ws.wv[i];
+            rb[k] = __ldg(p.ro + v);
+            re[k] = __ldg(p.ro + v + 1);
+            ov[k] = __ldg(p.orig + v);
+            ou[k] = p.parent ? __ldg(p.orig + ws.wu[i]) : 0;
+        }
+    }
+    int nsmall = 0, nslice = 0;
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int i = i0 + k;
+        if (i < i1) {
+            p.level[ov[k]] = next_level;
+            if (p.parent) p.parent[ov[k]] = ou[k];
+            const int len = re[k] - rb[k];
+            nsmall += (len >= 1 && len <= W);
+            nslice += (len > W) ? (len + W - 1) / W : 0;
+        }
+    }
+    // positions of the short entries (in claim order) and the hub slices
+    int sinc = nsmall, hinc = nslice;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(FULL, sinc, o);
+        const int z = __shfl_up_sync(FULL, hinc, o);
+        if (lane >= o) {
+            sinc += y;
+            hinc += z;
+        }
+    }
+    const int cs = __shfl_sync(FULL, sinc, 31);
+    const int total_slices = __shfl_sync(FULL, hinc, 31);
+    unsigned hbase = 0;
+    if (lane == 0 && total_slices > 0) hbase = atomicAdd(&p.ctrl->hub_count[set_out], (unsigned)total_slices);
+    hbase = __shfl_sync(FULL, hbase, 0);
+    {
+        int spos = sinc - nsmall;
+        unsigned hpos = hbase + (unsigned)(hinc - nslice);
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            const int i = i0 + k;
+            if (i < i1) {
+                const int len = re[k] - rb[k];
+                if (len >= 1 && len <= W) {
+                    ws.ou[spos] = ws.wv[i];
+                    ws.ob[spos] = rb[k];
+                    ws.ol[spos] = len;
+                    ++spos;
+                } else if (len > W) {
+                    const int nseg = (len + W - 1) / W;
+                    if (nseg <= 8) {  // a few slices: this lane writes them
+                        for (int sg = 0; sg < nseg; ++sg, ++hpos) {
+                            if (hpos < p.hcap) {
+                                p.hu[qo][hpos] = ws.wv[i];
+                                p.hb[qo][hpos] = rb[k] + sg * W;
+                                p.hl[qo][hpos] = min(W, len - sg * W);
+                            } else {
+                                atomicOr(&p.ctrl->status, ST_OVERFLOW);
+                            }
+                        }
+                    } else {
+                        hpos += (unsigned)nseg;
+                    }
+                }
+            }
+        }
+    }
+    // large hubs: the whole warp writes their slices
+    {
+        unsigned hpos = hbase + (unsigned)(hinc - nslice);
+        int big_v[PER], big_b[PER], big_l[PER];
+        unsigned big_at[PER];
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            const int i = i0 + k;
+            const int len = (i < i1) ? re[k] - rb[k] : 0;
+            big_l[k] = (len > W && (len + W - 1) / W > 8) ? len : 0;
+            big_v[k] = (i < i1) ? ws.wv[i] : 0;
+            big_b[k] = (i < i1) ? rb[k] : 0;
+            big_at[k] = hpos;
+            if (len > W) hpos += (unsigned)((len + W - 1) / W);
+        }
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            unsigned m = __ballot_sync(FULL, big_l[k] > 0);
+            while (m) {
+                const int src = __ffs(m) - 1;
+                m &= m - 1;
+                const int hv = __shfl_sync(FULL, big_v[k], src);
+                const int hb = __shfl_sync(FULL, big_b[k], src);
+                const int hl = __shfl_sync(FULL, big_l[k], src);
+                const unsigned at = __shfl_sync(FULL, big_at[k], src);
+                const int nseg = (hl + W - 1) / W;
+                for (int sg = lane; sg < nseg; sg += 32) {
+                    const unsigned g = at + (unsigned)sg;
+                    if (g < p.hcap) {
+                        p.hu[qo][g] = hv;
+                        p.hb[qo][g] = hb + sg * W;
+                        p.hl[qo][g] = min(W, hl - sg * W);
+                    } else {
+                        atomicOr(&p.ctrl->status, ST_OVERFLOW);
+                    }
+                }
+            }
+        }
+    }
+    __syncwarp();
+    if (cs == 0) return;
+    // cut the short entries into units (<= 32 entries, a new unit where the
+    // running edge count crosses a multiple of W)
+    const int j0 = min(lane * PER, cs), j1 = min(j0 + PER, cs);
     int sum = 0;
-    for (int i = i0; i < i1; ++i) sum += ws.ol[i];
+    for (int j = j0; j < j1; ++j) sum += ws.ol[j];
     int inc = sum;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -196,10 +319,10 @@ __device__ __noinline__ void warp_flush(WarpSmem &ws, const WParams &p, int set_
     int nu = 0;
     {
         int off = toff;
-        for (int i = i0; i < i1; ++i) {
-            const bool start = (i % 32 == 0) || (off / W != (off - ws.ol[i - 1]) / W);
+        for (int j = j0; j < j1; ++j) {
+            const bool start = (j % 32 == 0) || (off / W != (off - ws.ol[j - 1]) / W);
             nu += start;
-            off += ws.ol[i];
+            off += ws.ol[j];
         }
     }
     int uinc = nu;
@@ -211,39 +334,40 @@ __device__ __noinline__ void warp_flush(WarpSmem &ws, const WParams &p, int set_
     const int units = __shfl_sync(FULL, uinc, 31);
     unsigned long long base = 0;
     if (lane == 0)
-        base = atomicAdd(&p.ctrl->eu_count[set_out], ((unsigned long long)units << 32) | (unsigned long long)c);
+        base = atomicAdd(&p.ctrl->eu_count[set_out], ((unsigned long long)units << 32) | (unsigned long long)cs);
     base = __shfl_sync(FULL, base, 0);
     const unsigned ebase = (unsigned)(base & 0xffffffffull), ubase = (unsigned)(base >> 32);
     {
         int k = uinc - nu, off = toff;
-        for (int i = i0; i < i1; ++i) {
-            const bool start = (i % 32 == 0) || (off / W != (off - ws.ol[i - 1]) / W);
-            if (start) ws.ust[k++] = i;
-            off += ws.ol[i];
+        for (int j = j0; j < j1; ++j) {
+            const bool start = (j % 32 == 0) || (off / W != (off - ws.ol[j - 1]) / W);
+            if (start) ws.ust[k++] = j;
+            off += ws.ol[j];
         }
     }
     __syncwarp();
-    for (int i = lane; i < c; i += 32) {
-        const unsigned gi = ebase + (unsigned)i;
+    for (int j = lane; j < cs; j += 32) {
+        const unsigned gi = ebase + (unsigned)j;
         if (gi < p.ecap) {
-            p.eu[qo][gi] = ws.ou[i];
-            p.eb[qo][gi] = ws.ob[i];
-            p.el[qo][gi] = ws.ol[i];
+            p.eu[qo][gi] = ws.ou[j];
+            p.eb[qo][gi] = ws.ob[j];
+            p.el[qo][gi] = ws.ol[j];
         } else {
             atomicOr(&p.ctrl->status, ST_OVERFLOW);
         }
     }
     for (int k = lane; k < units; k += 32) {
-        const int s = ws.ust[k];
-        const int e = (k + 1 < units) ? ws.ust[k + 1] : c;
+        const int s0 = ws.ust[k];
+        const int e0 = (k + 1 < units) ? ws.ust[k + 1] : cs;
         const unsigned gk = ubase + (unsigned)k;
         if (gk < p.ucap) {
-            p.us[qo][gk] = (int32_t)(ebase + (unsigned)s);
-            p.uc[qo][gk] = e - s;
+            p.us[qo][gk] = (int32_t)(ebase + (unsigned)s0);
+            p.uc[qo][gk] = e0 - s0;
         } else {
             atomicOr(&p.ctrl->status, ST_OVERFLOW);
         }
     }
+    (void)lt;
     __syncwarp();
 }
 
@@ -282,8 +406,13 @@ __device__ __forceinline__ void process_item(WarpSmem &ws, const WParams &p, int
         }
     }
     __syncwarp();
-    // pass B: claim; winners write level/parent and are queued
+    // pass B: claim with atomicOr; each winner is queued with its source
     for (int c0 = 0; c0 < nc; c0 += 32 * UB) {
+        // room for a whole batch of winners, flushed outside the claim loop
+        if (ocnt > OBW - 32 * UB) {
+            warp_flush(ws, p, set_out, qo, ocnt, next_level);
+            ocnt = 0;
+        }
         int v[UB], e[UB];
         bool win[UB];
 #pragma unroll
@@ -300,11 +429,10 @@ __device__ __forceinline__ void process_item(WarpSmem &ws, const WParams &p, int
                 win[k] = !(atomicOr(p.bitmap + ((unsigned)v[k] >> 5), bit) & bit);
             }
         }
-        int rb[UB], len[UB];
 #pragma unroll
         for (int k = 0; k < UB; ++k) {
-            rb[k] = 0;
-            len[k] = 0;
+            const unsigned m = __ballot_sync(FULL, win[k]);
+            if (!m) continue;
             if (win[k]) {
                 int lo = 0, hi = cnt;  // source entry: largest j with off[j] <= e
                 while (hi - lo > 1) {
@@ -312,54 +440,12 @@ __device__ __forceinline__ void process_item(WarpSmem &ws, const WParams &p, int
                     if (ws.off[buf][mid] <= e[k]) lo = mid;
                     else hi = mid;
                 }
-                const int ov = __ldg(p.orig + v[k]);  // results leave in the caller's numbering
-                p.level[ov] = next_level;
-                if (p.parent) p.parent[ov] = __ldg(p.orig + ws.iu[buf][lo]);
-                rb[k] = __ldg(p.ro + v[k]);
-                len[k] = __ldg(p.ro + v[k] + 1) - rb[k];
+                const int pos = ocnt + __popc(m & lt);
+                ws.wv[pos] = v[k];
+                ws.wu[pos] = ws.iu[buf][lo];
                 ++my_new;
             }
-        }
-#pragma unroll
-        for (int k = 0; k < UB; ++k) {
-            const bool small = win[k] && len[k] >= 1 && len[k] <= W;
-            const unsigned m = __ballot_sync(FULL, small);
-            if (m) {
-                if (ocnt + __popc(m) > OBW) {
-                    warp_flush(ws, p, set_out, qo, ocnt);
-                    ocnt = 0;
-                }
-                if (small) {
-                    const int pos = ocnt + __popc(m & lt);
-                    ws.ou[pos] = v[k];
-                    ws.ob[pos] = rb[k];
-                    ws.ol[pos] = len[k];
-                }
-                ocnt += __popc(m);
-            }
-            // hubs: slices of W edges, written by the whole warp
-            unsigned hm = __ballot_sync(FULL, win[k] && len[k] > W);
-            while (hm) {
-                const int src = __ffs(hm) - 1;
-                hm &= hm - 1;
-                const int hv = __shfl_sync(FULL, v[k], src);
-                const int hb = __shfl_sync(FULL, rb[k], src);
-                const int hl = __shfl_sync(FULL, len[k], src);
-                const int nseg = (hl + W - 1) / W;
-                unsigned gi = 0;
-                if (lane == 0) gi = atomicAdd(&p.ctrl->hub_count[set_out], (unsigned)nseg);
-                gi = __shfl_sync(FULL, gi, 0);
-                for (int s = lane; s < nseg; s += 32) {
-                    const unsigned g = gi + (unsigned)s;
-                    if (g < p.hcap) {
-                        p.hu[qo][g] = hv;
-                        p.hb[qo][g] = hb + s * W;
-                        p.hl[qo][g] = min(W, hl - s * W);
-                    } else {
-                        atomicOr(&p.ctrl->status, ST_OVERFLOW);
-                    }
-                }
-            }
+            ocnt += __popc(m);
         }
     }
     __syncwarp();
@@ -481,7 +567,7 @@ __global__ void __launch_bounds__(WPB * 32, (24 / WPB) > 0 ? (24 / WPB) : 1) td_
         }
         cp_async_wait_all();
         __syncwarp();
-        if (ocnt > 0) warp_flush(ws, p, set_out, qo, ocnt);
+        if (ocnt > 0) warp_flush(ws, p, set_out, qo, ocnt, next_level);
 
         if (p.stats && d < kMaxStatLayers) {
             unsigned long long a = my_vertices, e = my_edges, t = my_new;
