@@ -145,6 +145,35 @@ int64_t bfs_graph_get_option(const bfs_graph *g, int option);
 int bfs_run(bfs_graph *g, int32_t root, int32_t *level_out, int32_t *parent_out,
             void *stream);
 
+/*
+ * Single-source search that allocates nothing (the paper has no counterpart:
+ * this is a deployment variant of bfs_run).  For callers that cannot
+ * allocate GPU memory at the moment they search -- a process whose device
+ * memory is owned by another allocator or fixed budget, a latency-critical
+ * path that must not block in cudaMalloc/cudaFree, or code running where
+ * the CUDA runtime forbids allocation.  The search runs the same top-down
+ * kernel as bfs_run (BFS_OPT_MODE 2, BLOCK 512) directly on the caller's
+ * device CSR, with all scratch state in one fixed-size __device__ array
+ * built into the library (about 7 MB, held by every GPU that loads the
+ * library until the process exits).  No cudaMalloc, cudaFree or allocating
+ * library call is made.
+ *   row_offsets, col_idx : the caller's CSR in DEVICE memory (checked as in
+ *                          bfs_graph_create; no renumbering is done)
+ *   n, m                 : 1 <= n <= BFS_NOALLOC_MAX_VERTICES,
+ *                          0 <= m <= BFS_NOALLOC_MAX_EDGES, else
+ *                          BFS_ERR_INVALID_ARG
+ *   root, level_out, parent_out, stream : as bfs_run, outputs in DEVICE memory
+ * Blocks until the search has finished and returns its status (including
+ * BFS_ERR_TIMEOUT from the device).  The first call on a device also sets up
+ * the array on that device; make it before any stream capture.  Every call
+ * shares the one array: calls from several host threads are serialised, and
+ * searches that overlap on the GPU through other means would race on it.
+ */
+#define BFS_NOALLOC_MAX_VERTICES 131072
+#define BFS_NOALLOC_MAX_EDGES 4194304
+int bfs_run_noalloc(const int32_t *row_offsets, const int32_t *col_idx, int64_t n, int64_t m,
+                    int32_t root, int32_t *level_out, int32_t *parent_out, void *stream);
+
 /* Wait for the graph's last run and return its device-side status
  * (BFS_OK, BFS_ERR_TIMEOUT or BFS_ERR_CUDA); clears the status word. */
 int bfs_graph_status(bfs_graph *g);

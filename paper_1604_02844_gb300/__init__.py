@@ -69,6 +69,7 @@ SIGNATURES = {
     "bfs_graph_set_option": (_INT, [_P, _INT, _I64]),
     "bfs_graph_get_option": (_I64, [_P, _INT]),
     "bfs_run": (_INT, [_P, _I32, _P, _P, _P]),
+    "bfs_run_noalloc": (_INT, [_P, _P, _I64, _I64, _I32, _P, _P, _P]),
     "bfs_graph_status": (_INT, [_P]),
     "bfs_graph_layer_stats": (_INT, [_P, _P, _P, _P, _I32]),
     "bfs_graph_layer_times": (_INT, [_P, _P, _I32]),
@@ -164,6 +165,19 @@ def bfs_graph_destroy(g) -> None:
 
 def bfs_run(g, root: int, level_out, parent_out=None, stream=None) -> None:
     _check(load().bfs_run(g, int(root), _ptr(level_out), _ptr(parent_out), _stream_handle(stream)))
+
+
+NOALLOC_MAX_VERTICES = 131072
+NOALLOC_MAX_EDGES = 4194304
+
+
+def bfs_run_noalloc(row_offsets, col_idx, root: int, level_out, parent_out=None, stream=None,
+                    n: int | None = None, m: int | None = None) -> None:
+    """Search without any allocation (device CSR and outputs; blocks until done)."""
+    n = (len(row_offsets) - 1) if n is None else n
+    m = len(col_idx) if m is None else m
+    _check(load().bfs_run_noalloc(_ptr(row_offsets), _ptr(col_idx) if m > 0 else None, n, m, int(root),
+                                  _ptr(level_out), _ptr(parent_out), _stream_handle(stream)))
 
 
 def bfs_graph_status(g) -> int:

@@ -126,4 +126,8 @@ int bitmap_to_caller(Graph *g, uint32_t *d_out);
 
 bool is_device_pointer(const void *p);
 
+// implemented in graph.cu: CSR checks (flags: 1 offsets, 2 columns, 4 ends)
+__global__ void validate_csr_kernel(const int32_t *__restrict__ ro, const int32_t *__restrict__ col, int64_t n,
+                                    int64_t m, unsigned *flags);
+
 }  // namespace gbbfs
