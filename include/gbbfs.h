@@ -79,11 +79,11 @@ typedef enum {
     BFS_OPT_MAX_CTAS = 8,       /* cap on the persistent grid size (0 = no cap)        */
     BFS_OPT_BATCH_WIDTH = 9,    /* sources per bit-parallel batch: 8..64, multiple of 8 */
     BFS_OPT_BATCH_BLOCK = 10,   /* threads per CTA of the batched kernels: 256 or 512   */
-    BFS_OPT_MODE = 11           /* expansion of bfs_run: 0 = edge-balanced units run by
-                                   whole CTAs, 1 = one item per frontier vertex binned
-                                   by degree (thread / warp / CTA), 2 = edge-balanced
-                                   units run by independent warps.  Modes 0 and 2 take
-                                   BLOCK 256 or 512                                      */
+    BFS_OPT_MODE = 11           /* expansion of bfs_run: 0 = work items bounded in edges
+                                   (short lists packed into units, hubs cut into slices)
+                                   run by independent warps, BLOCK 256 or 512 (default);
+                                   1 = one item per frontier vertex, binned by degree
+                                   and expanded by a thread, a warp or a whole CTA      */
 } bfs_option;
 
 /* ---- library ------------------------------------------------------------ */
@@ -152,7 +152,7 @@ int bfs_run(bfs_graph *g, int32_t root, int32_t *level_out, int32_t *parent_out,
  * memory is owned by another allocator or fixed budget, a latency-critical
  * path that must not block in cudaMalloc/cudaFree, or code running where
  * the CUDA runtime forbids allocation.  The search runs the same top-down
- * kernel as bfs_run (BFS_OPT_MODE 2, BLOCK 512) directly on the caller's
+ * kernel as bfs_run (BFS_OPT_MODE 0, BLOCK 512) directly on the caller's
  * device CSR, with all scratch state in one fixed-size __device__ array
  * built into the library (about 7 MB, held by every GPU that loads the
  * library until the process exits).  No cudaMalloc, cudaFree or allocating

@@ -191,9 +191,9 @@ bfs_graph *bfs_graph_create(const int32_t *row_offsets, const int32_t *col_idx, 
         }
     }
 
-    // single-source workspace (units mode; the binned-mode queues are lazy)
+    // single-source workspace (warp mode; the binned-mode queues are lazy)
     g->bitmap_words = ((n + 31) / 32 + 3) / 4 * 4;
-    g->hcap = td_units_hub_capacity(m);
+    g->hcap = td_hub_capacity(m);
     if ((e = cudaMalloc(&g->d_bitmap, (size_t)g->bitmap_words * 4)) != cudaSuccess) return fail(e, "cudaMalloc(bitmap)");
     for (int b = 0; b < 2; ++b) {
         for (int j = 0; j < 3; ++j) {
@@ -276,8 +276,7 @@ int bfs_graph_set_option(bfs_graph *gh, int option, int64_t v)
         o.batch_block = (int)v;
         break;
     case BFS_OPT_MODE:
-        if (v != MODE_UNITS && v != MODE_BINNED && v != MODE_WARP)
-            return bad("MODE must be 0 (units), 1 (binned) or 2 (warp)");
+        if (v != MODE_WARP && v != MODE_BINNED) return bad("MODE must be 0 (warp units) or 1 (degree-binned)");
         o.mode = (int)v;
         break;
     default:
@@ -329,17 +328,15 @@ int bfs_run(bfs_graph *gh, int32_t root, int32_t *level_out, int32_t *parent_out
     }
     // one workspace: a run on another stream waits for the previous run
     if (g->ran && s != g->last_stream) GB_CUDA(cudaStreamWaitEvent(s, g->ws_event, 0));
-    if (g->opt.mode != MODE_BINNED && g->opt.block == 1024)
-        return set_error(BFS_ERR_INVALID_ARG, "bfs_run: the units and warp modes take BLOCK 256 or 512");
+    if (g->opt.mode == MODE_WARP && g->opt.block == 1024)
+        return set_error(BFS_ERR_INVALID_ARG, "bfs_run: mode 0 takes BLOCK 256 or 512");
     int rc;
     if (g->opt.mode == MODE_BINNED) {
         rc = alloc_binned(g);
         if (rc != BFS_OK) return rc;
         rc = td_launch(g, root, d_level, d_parent, s);
-    } else if (g->opt.mode == MODE_WARP) {
-        rc = td_warp_launch(g, root, d_level, d_parent, s);
     } else {
-        rc = td_units_launch(g, root, d_level, d_parent, s);
+        rc = td_warp_launch(g, root, d_level, d_parent, s);
     }
     if (rc != BFS_OK) return rc;
     if (!lvl_dev) GB_CUDA(cudaMemcpyAsync(level_out, d_level, (size_t)g->n * 4, cudaMemcpyDeviceToHost, s));

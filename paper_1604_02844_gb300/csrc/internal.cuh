@@ -34,8 +34,8 @@ enum : unsigned {
 // (d+1)%3 and clears set (d+2)%3, which nobody touches during layer d.
 // The last CTA to leave a search returns every counter to zero.
 struct Ctrl {
-    unsigned long long eu_count[3];  // units mode: (units << 32) | entries
-    unsigned hub_count[3];           // units mode: hub slices
+    unsigned long long eu_count[3];  // warp mode: (units << 32) | entries
+    unsigned hub_count[3];           // warp mode: hub slices
     unsigned work[3];                // work-item dispenser (both modes)
     unsigned count[3];               // binned mode: small-item queue size
     unsigned big_count[3];           // binned mode: large-item queue size
@@ -49,7 +49,7 @@ struct Ctrl {
 using TdCtrl = Ctrl;
 using UnitCtrl = Ctrl;
 
-enum { MODE_UNITS = 0, MODE_BINNED = 1, MODE_WARP = 2 };
+enum { MODE_WARP = 0, MODE_BINNED = 1 };
 
 struct Options {
     int block = 512;
@@ -62,7 +62,7 @@ struct Options {
     int max_ctas = 0;
     int batch_width = 64;
     int batch_block = 512;
-    int mode = MODE_UNITS;
+    int mode = MODE_WARP;
 };
 
 constexpr int kMaxStatLayers = 256;
@@ -80,9 +80,9 @@ struct Graph {
     // single-source workspace
     uint32_t *d_bitmap = nullptr;  // words rounded up to a multiple of 4
     int64_t bitmap_words = 0;
-    int32_t *d_eq[2][3] = {};      // units mode: [buffer][u, beg, len] entries
-    int32_t *d_uq[2][2] = {};      // units mode: [buffer][first entry, count]
-    int32_t *d_hq[2][3] = {};      // units mode: [buffer][u, beg, len] hub slices
+    int32_t *d_eq[2][3] = {};      // warp mode: [buffer][u, beg, len] entries
+    int32_t *d_uq[2][2] = {};      // warp mode: [buffer][first entry, count]
+    int32_t *d_hq[2][3] = {};      // warp mode: [buffer][u, beg, len] hub slices
     int64_t hcap = 0;
     int32_t *d_q[2][3] = {};       // binned mode (lazy): small-item queue
     int32_t *d_bq[2][3] = {};      // binned mode (lazy): large-item queue
@@ -108,13 +108,9 @@ struct Graph {
 // on first use by graph.cu)
 int td_launch(Graph *g, int32_t root, int32_t *level, int32_t *parent, cudaStream_t s);
 
-// implemented in topdown_units.cu (edge-balanced units mode)
-int td_units_launch(Graph *g, int32_t root, int32_t *level, int32_t *parent, cudaStream_t s);
-int64_t td_units_hub_capacity(int64_t m);
-
-// implemented in topdown_warp.cu (warp-private pipelines; shares the units
-// mode's queues)
+// implemented in topdown_warp.cu (warp-private pipelines, the default)
 int td_warp_launch(Graph *g, int32_t root, int32_t *level, int32_t *parent, cudaStream_t s);
+int64_t td_hub_capacity(int64_t m);
 
 // implemented in msbfs.cu
 int ms_run_batch(Graph *g, const int32_t *roots, int32_t k, uint8_t *level_out);

@@ -1,7 +1,7 @@
 // topdown_warp.cu -- single-source level-synchronous top-down BFS with
-// warp-private work pipelines (expansion mode 2).
+// warp-private work pipelines (the default expansion mode).
 //
-// Method as in topdown.cu / topdown_units.cu (Alg. 2 with an atomic
+// Method as in topdown.cu (Alg. 2 with an atomic
 // visited bitmap, word v>>5 bit v&31 as in Listing 1; P[s] = s; layer L_d
 // finished before L_{d+1}, Sec. 3); one persistent cooperative kernel per
 // search.  The difference is who works together: every warp runs its own
@@ -634,6 +634,10 @@ int launch(Graph *g, const WParams &prm, cudaStream_t s)
 }
 
 }  // namespace
+
+// Hub slices of one layer: a vertex of degree d > W gives ceil(d/W) <= 2d/W
+// slices, so a layer has at most 2m/W = m/128 of them (+2).
+int64_t td_hub_capacity(int64_t m) { return m / 128 + 2; }
 
 int td_warp_launch(Graph *g, int32_t root, int32_t *level, int32_t *parent, cudaStream_t s)
 {
