@@ -47,7 +47,7 @@ def parse_args(argv=None):
     ap.add_argument("--edgefactor", type=int, default=16)
     ap.add_argument("--roots", type=int, default=64)
     ap.add_argument("--seed", type=int, default=1)
-    ap.add_argument("--cpu-sample-roots", type=int, default=8)
+    ap.add_argument("--cpu-sample-roots", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--option", action="append", default=[],
@@ -137,6 +137,31 @@ class ClockSampler:
         loaded = [s for s in sm if s > 0.5 * max(sm)] or sm
         return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(smax),
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+KERNEL_SOURCES = ["paper_1604_02844_gb300/csrc/topdown_warp.cu",
+                  "paper_1604_02844_gb300/csrc/device_common.cuh",
+                  "paper_1604_02844_gb300/csrc/internal.cuh"]
+
+
+def profiled_traffic(args, options):
+    """DRAM bytes per launch from the committed ncu summary, or None when the
+    kernel sources or the configuration differ from what was profiled."""
+    import hashlib
+    prof = os.path.join(ROOT, "profiles", f"td_warp_kernel_kronecker_s{args.scale}.txt")
+    if not os.path.exists(prof) or options.get("mode") != 0 or options.get("block") != 512:
+        return None
+    kv = {}
+    for line in open(prof):
+        if ":" in line and not line.startswith(" "):
+            k, v = line.split(":", 1)
+            kv[k.strip()] = v.strip()
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    if kv.get("source_sha256_16") != h.hexdigest()[:16]:
+        return None
+    return float(kv["traffic_bytes_per_launch"])
 
 
 def measured_peaks():
@@ -333,6 +358,7 @@ def run_ours(args):
         value = sum(float(x[0]) for x in gathered)
         step_ms = 1e3 * max(float(x[1]) for x in gathered) / args.steps
 
+    options = {k: g.get_option(k) for k in gb.OPTION_NAMES}
     if rank == 0:
         cpu = None
         if not args.no_cpu_baseline:
@@ -345,12 +371,14 @@ def run_ours(args):
                        "scale": args.scale, "edgefactor": args.edgefactor, "roots": args.roots,
                        "n": n, "m_directed": m, "seed": args.seed, "parallelism": "replicas",
                        "l2": "flushed between searches (512 MiB write); col_idx also > L2",
-                       "options": {k: g.get_option(k) for k in gb.OPTION_NAMES}},
+                       "options": options},
             "teps_stats": {"min": min(teps) / 1e9, "median": statistics.median(teps) / 1e9,
                            "max": max(teps) / 1e9, "runs": len(teps)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
-                         "kernel": "td_kernel", "algorithmic_bytes_per_launch": mean_bytes,
+                         "frac": achieved / peak, "peak_kind": peak_kind,
+                         "traffic": profiled_traffic(args, options),
+                         "kernel": "td_warp_kernel" if options.get("mode") == 0 else "td_kernel",
+                         "algorithmic_bytes_per_launch": mean_bytes,
                          "mean_launch_s": mean_t},
             "cpu_baseline": cpu,
             "e2e": e2e,
