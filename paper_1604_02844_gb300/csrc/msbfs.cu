@@ -1,13 +1,569 @@
-// msbfs.cu -- bit-parallel batched BFS (filled in by the batched-kernel work).
+// msbfs.cu -- bit-parallel multi-source BFS (bfs_run_batch) and the lane
+// machinery the serving loop builds on.
+//
+// Not in the paper; it applies the paper's layer step (Alg. 2: expand the
+// frontier, test and set the visited state, queue new vertices) to up to 64
+// searches at once, one bit per search ("lane") in 64-bit words per vertex:
+//   seen[v]      lanes that have reached v
+//   front[p][v]  lanes whose frontier holds v in iteration parity p
+//   next[v]      lanes that reach v in the current iteration
+// One iteration (all lanes advance one layer):
+//   EXPAND: for every frontier entry (u, beg, len) and every v in its slice
+//           of Adj[u]: nb = front[u] & ~seen[v]; if nb, atomicOr(next[v], nb)
+//           (64-bit); the warp whose atomicOr found next[v] == 0 queues v in
+//           the touched list.
+//   UPDATE: for every touched v: nn = next[v] & ~seen[v]; next[v] = 0;
+//           seen[v] |= nn; front[v] = nn; lane i of nn gets level
+//           iter + 1 - start[i]; v is queued for the next EXPAND (vertices of
+//           degree > H as slices of H edges).  The old frontier words are
+//           cleared.
+// Lanes may join at different iterations (start[i] = the iteration they were
+// injected), which is what the serving loop uses: a lane whose frontier has
+// emptied is finished, its level column is read out and the lane reused.
+//
+// Levels are kept vertex-major, lvl[v][64] uint8 in the caller's numbering
+// (one 64-byte line per vertex), 0xFF = unreached, and transposed into the
+// caller's source-major [k][n] output when lanes finish.
+//
+// All iterations of a launch run in one persistent cooperative kernel with
+// two bounded grid barriers per iteration.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "device_common.cuh"
 #include "internal.cuh"
+#include "msbfs.cuh"
 
 namespace gbbfs {
+namespace {
 
-int ms_run_batch(Graph *, const int32_t *, int32_t, uint8_t *)
+using namespace dev;
+
+constexpr int H = 256;   // hub slice length
+constexpr int UX = 4;    // 32-edge batches per warp in flight
+constexpr int MS_WPB = 8;
+
+struct MsParams {
+    const int32_t *__restrict__ ro;
+    const int32_t *__restrict__ col;
+    const int32_t *__restrict__ orig;
+    unsigned long long *seen, *next, *front[2];
+    uint8_t *lvl;
+    int32_t *fu[2], *fb[2], *fl[2];
+    int32_t *touched;
+    const int32_t *start;  // [64] start iteration per lane
+    MsCtrl *ctrl;
+    int32_t n;
+    uint32_t fcap;
+    uint32_t max_iters;
+    uint64_t timeout_ns;
+};
+
+// Append the slices of vertex u (degree >= 1) to frontier buffer q.  Called
+// by all lanes of a warp; `want` marks the lanes with a vertex to append.
+__device__ __forceinline__ void append_frontier(const MsParams &p, int q, bool want, int u, int rb, int len)
 {
-    return set_error(BFS_ERR_INVALID_ARG, "bfs_run_batch: batched kernels are not in this build yet");
+    const int lane = threadIdx.x & 31;
+    const int ns = want ? (len + H - 1) / H : 0;
+    int inc = ns;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(FULL, inc, o);
+        if (lane >= o) inc += y;
+    }
+    const int total = __shfl_sync(FULL, inc, 31);
+    if (total == 0) return;
+    unsigned base = 0;
+    if (lane == 31) base = atomicAdd(&p.ctrl->fcount[q], (unsigned)total);
+    base = __shfl_sync(FULL, base, 31);
+    unsigned pos = base + (unsigned)(inc - ns);
+    for (int s = 0; s < ns; ++s, ++pos) {
+        if (pos < p.fcap) {
+            p.fu[q][pos] = u;
+            p.fb[q][pos] = rb + s * H;
+            p.fl[q][pos] = min(H, len - s * H);
+        } else {
+            atomicOr(&p.ctrl->status, ST_OVERFLOW);
+        }
+    }
 }
 
-void ms_free(Graph *) {}
+__device__ __forceinline__ void ms_expand(const MsParams &p, int par, unsigned nF)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = lanemask_lt();
+    MsCtrl *c = p.ctrl;
+    for (;;) {
+        unsigned base = 0;
+        if (lane == 0) base = atomicAdd(&c->work[par], 32u);
+        base = __shfl_sync(FULL, base, 0);
+        if (base >= nF) break;
+        const unsigned j = base + lane;
+        const bool real = j < nF;
+        int u = 0, b = 0, l = 0;
+        unsigned long long f = 0;
+        if (real) {
+            u = __ldcg(p.fu[par] + j);
+            b = __ldcg(p.fb[par] + j);
+            l = __ldcg(p.fl[par] + j);
+            f = __ldcg(p.front[par] + u);
+            if (l < 0 || l > H) l = 0;  // cannot happen: slices hold <= H edges
+        }
+        int inc = l;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(FULL, inc, o);
+            if (lane >= o) inc += y;
+        }
+        const int E = __shfl_sync(FULL, inc, 31);
+        const int off = inc - l;
+        for (int e0 = 0; e0 < E; e0 += 32 * UX) {
+            int v[UX];
+            unsigned long long nb[UX];
+#pragma unroll
+            for (int x = 0; x < UX; ++x) {
+                const int bb = e0 + x * 32;
+                unsigned starts = (real && off > bb && off < bb + 32) ? (1u << (off - bb)) : 0u;
+                starts = __reduce_or_sync(FULL, starts);
+                const int j0 = __popc(__ballot_sync(FULL, real && off <= bb)) - 1;
+                const int jj = (j0 + __popc(starts & ((2u << lane) - 1u))) & 31;
+                const int jb = __shfl_sync(FULL, b, jj);
+                const int jo = __shfl_sync(FULL, off, jj);
+                const unsigned long long jf = __shfl_sync(FULL, f, jj);
+                const int e = bb + lane;
+                v[x] = (e < E) ? __ldg(p.col + jb + (e - jo)) : -1;
+                nb[x] = jf;
+            }
+#pragma unroll
+            for (int x = 0; x < UX; ++x)
+                if (v[x] >= 0) nb[x] &= ~__ldcg(p.seen + v[x]);
+#pragma unroll
+            for (int x = 0; x < UX; ++x) {
+                bool first = false;
+                if (v[x] >= 0 && nb[x]) first = (atomicOr(p.next + v[x], nb[x]) == 0ull);
+                const unsigned m = __ballot_sync(FULL, first);
+                if (m) {
+                    unsigned tb = 0;
+                    if (lane == 0) tb = atomicAdd(&c->tcount[par], (unsigned)__popc(m));
+                    tb = __shfl_sync(FULL, tb, 0);
+                    if (first) {
+                        const unsigned at = tb + __popc(m & lt);
+                        if (at < (unsigned)p.n) p.touched[at] = v[x];
+                        else atomicOr(&c->status, ST_OVERFLOW);
+                    }
+                }
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void ms_update(const MsParams &p, int par, unsigned nF, unsigned iter, unsigned long long &alive)
+{
+    const int lane = threadIdx.x & 31;
+    const int q = par ^ 1;
+    MsCtrl *c = p.ctrl;
+    const unsigned nT = min(ld_relaxed(&c->tcount[par]), (unsigned)p.n);
+    const unsigned gtid = blockIdx.x * blockDim.x + threadIdx.x;
+    const unsigned gsz = gridDim.x * blockDim.x;
+    // the old frontier words
+    for (unsigned i = gtid; i < nF; i += gsz) p.front[par][__ldcg(p.fu[par] + i)] = 0ull;
+    // the touched vertices
+    for (unsigned i0 = gtid - lane; i0 < nT; i0 += gsz) {  // warp-uniform loop
+        const unsigned i = i0 + lane;
+        int v = 0, rb = 0, len = 0;
+        unsigned long long nn = 0;
+        if (i < nT) {
+            v = __ldcg(p.touched + i);
+            const unsigned long long x = __ldcg(p.next + v);
+            p.next[v] = 0ull;
+            const unsigned long long s = __ldcg(p.seen + v);
+            nn = x & ~s;
+            if (nn) {
+                p.seen[v] = s | nn;
+                p.front[q][v] = nn;
+                alive |= nn;
+                const int ov = __ldg(p.orig + v);
+                uint8_t *row = p.lvl + (size_t)ov * 64;
+                unsigned long long bits = nn;
+                while (bits) {
+                    const int ln = __ffsll((long long)bits) - 1;
+                    bits &= bits - 1;
+                    const int lvv = (int)iter + 1 - __ldg(p.start + ln);
+                    if (lvv > 254) atomicOr(&c->status, ST_DEPTH);
+                    row[ln] = (uint8_t)min(lvv, 254);
+                }
+                rb = __ldg(p.ro + v);
+                len = __ldg(p.ro + v + 1) - rb;
+            }
+        }
+        append_frontier(p, q, nn != 0ull && len > 0, v, rb, len);
+    }
+}
+
+__global__ void __launch_bounds__(MS_WPB * 32) ms_kernel(MsParams p)
+{
+    __shared__ int s_ok;
+    __shared__ unsigned s_nF, s_iter0;
+    __shared__ unsigned long long s_alive;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const unsigned G = gridDim.x;
+    MsCtrl *c = p.ctrl;
+    if (tid == 0) s_iter0 = ld_relaxed(&c->iter);  // only the last CTA out writes it
+    __syncthreads();
+    const unsigned iter0 = s_iter0;
+    unsigned done = 0;
+    bool ok = true;
+    for (unsigned it = 0; it < p.max_iters && ok; ++it) {
+        const unsigned iter = iter0 + it;
+        const int par = (int)(iter & 1);
+        if (tid == 0) {
+            s_nF = min(ld_relaxed(&c->fcount[par]), p.fcap);
+            s_alive = 0ull;
+        }
+        __syncthreads();
+        const unsigned nF = s_nF;
+        if (nF == 0) break;
+        if (blockIdx.x == 0 && tid == 0) {
+            // parity par^1: last read before the previous barrier, next used
+            // after the coming one
+            c->fcount[par ^ 1] = 0;
+            c->work[par ^ 1] = 0;
+            c->tcount[par ^ 1] = 0;
+            c->alive[par ^ 1] = 0ull;
+        }
+        ms_expand(p, par, nF);
+        ok = grid_sync(&c->bar_count, &c->bar_gen, &c->status, G, p.timeout_ns, &s_ok);
+        if (!ok) break;
+        unsigned long long alive = 0;
+        ms_update(p, par, nF, iter, alive);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) alive |= __shfl_xor_sync(FULL, alive, o);
+        if (lane == 0 && alive) atomicOr(&s_alive, alive);
+        __syncthreads();
+        if (tid == 0 && s_alive) atomicOr(&c->alive[par ^ 1], s_alive);
+        ok = grid_sync(&c->bar_count, &c->bar_gen, &c->status, G, p.timeout_ns, &s_ok);
+        if (ok) done = it + 1;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        __threadfence();
+        const unsigned old = atomicAdd(&c->exit_count, 1u);
+        if (old == G - 1) {
+            c->iter = iter0 + done;
+            c->bar_count = 0;
+            c->exit_count = 0;
+            __threadfence();
+        }
+    }
+}
+
+// Lanes in `mask`: set seen/front bits for their sources, level 0, start
+// iteration, and queue the sources.  One warp per lane.
+__global__ void ms_inject_kernel(MsParams p, const int32_t *__restrict__ lanes_src, unsigned long long mask,
+                                 int32_t *start)
+{
+    const int lane = threadIdx.x & 31;
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (w >= 64 || !((mask >> w) & 1ull)) return;
+    MsCtrl *c = p.ctrl;
+    const unsigned iter = c->iter;
+    const int par = (int)(iter & 1);
+    const int s = lanes_src[w];  // internal id
+    const unsigned long long bit = 1ull << w;
+    unsigned long long oldf = 0;
+    if (lane == 0) {
+        start[w] = (int32_t)iter;
+        atomicOr(p.seen + s, bit);
+        oldf = atomicOr(p.front[par] + s, bit);
+        p.lvl[(size_t)__ldg(p.orig + s) * 64 + w] = 0;
+        atomicOr(&c->alive[par], bit);
+    }
+    oldf = __shfl_sync(FULL, oldf, 0);
+    const int rb = __ldg(p.ro + s), len = __ldg(p.ro + s + 1) - rb;
+    append_frontier(p, par, lane == 0 && oldf == 0ull && len > 0, s, rb, len);
+}
+
+// Read the level columns of the lanes in `mask` into rows of `out`
+// (out[row_of_lane * n + v], caller numbering) and, with `recycle`, reset
+// them: level 0xFF, seen bit cleared.  Block: 128 vertices x 64 lanes.
+__global__ void ms_extract_kernel(uint8_t *lvl, unsigned long long *seen, const int32_t *__restrict__ perm, int64_t n,
+                                  unsigned long long mask, const int32_t *__restrict__ lane_row, uint8_t *out,
+                                  int64_t out_stride, int recycle)
+{
+    __shared__ uint8_t tile[128][65];
+    const int64_t v0 = (int64_t)blockIdx.x * 128;
+    // load 128 x 64 bytes (caller numbering), 16 B per thread per step
+    for (int t = threadIdx.x; t < 128 * 4; t += blockDim.x) {
+        const int r = t >> 2, q = t & 3;
+        const int64_t v = v0 + r;
+        uint4 x = make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu);
+        if (v < n) {
+            uint4 *src = reinterpret_cast<uint4 *>(lvl + (size_t)v * 64) + q;
+            x = *src;
+            if (recycle) {
+                // reset the recycled lanes' bytes, keep the others
+                uint4 y = x;
+                uint8_t *yb = reinterpret_cast<uint8_t *>(&y);
+                for (int k = 0; k < 16; ++k)
+                    if ((mask >> (q * 16 + k)) & 1ull) yb[k] = 0xFF;
+                *src = y;
+            }
+        }
+        const uint8_t *xb = reinterpret_cast<const uint8_t *>(&x);
+        for (int k = 0; k < 16; ++k) tile[r][q * 16 + k] = xb[k];
+    }
+    __syncthreads();
+    // write each requested lane's 128 bytes
+    unsigned long long mm = mask;
+    while (mm) {
+        const int ln = __ffsll((long long)mm) - 1;
+        mm &= mm - 1;
+        const int row = lane_row[ln];
+        if (row >= 0)
+            for (int r = threadIdx.x; r < 128; r += blockDim.x) {
+                const int64_t v = v0 + r;
+                if (v < n) out[(size_t)row * out_stride + v] = tile[r][ln];
+            }
+    }
+    if (recycle)
+        for (int r = threadIdx.x; r < 128; r += blockDim.x) {
+            const int64_t v = v0 + r;
+            if (v < n) {
+                const int w = __ldg(perm + v);  // seen is indexed by internal id
+                atomicAnd(seen + w, ~mask);
+            }
+        }
+}
+
+}  // namespace
+
+// ---- host side ---------------------------------------------------------------
+
+static MsWs *ws_of(Graph *g) { return reinterpret_cast<MsWs *>(g->batch_ws); }
+
+int ms_alloc(Graph *g, MsWs **out)
+{
+    if (g->batch_ws) {
+        *out = ws_of(g);
+        return BFS_OK;
+    }
+    MsWs *w = new (std::nothrow) MsWs();
+    if (!w) return set_error(BFS_ERR_OOM, "bfs_run_batch: host allocation");
+    const int64_t n = g->n;
+    w->fcap = n + 2 * (g->m / H) + 2;
+    auto bad = [&](cudaError_t e, const char *what) {
+        const int rc = cuda_error(e, what);
+        g->batch_ws = w;  // let ms_free release what exists
+        ms_free(g);
+        return rc;
+    };
+    cudaError_t e;
+    if ((e = cudaMalloc(&w->seen, (size_t)n * 8)) != cudaSuccess) return bad(e, "cudaMalloc(seen)");
+    if ((e = cudaMalloc(&w->next, (size_t)n * 8)) != cudaSuccess) return bad(e, "cudaMalloc(next)");
+    for (int b = 0; b < 2; ++b) {
+        if ((e = cudaMalloc(&w->front[b], (size_t)n * 8)) != cudaSuccess) return bad(e, "cudaMalloc(front)");
+        for (int j = 0; j < 3; ++j)
+            if ((e = cudaMalloc(&w->fq[b][j], (size_t)w->fcap * 4)) != cudaSuccess) return bad(e, "cudaMalloc(frontier)");
+    }
+    if ((e = cudaMalloc(&w->lvl, (size_t)n * 64)) != cudaSuccess) return bad(e, "cudaMalloc(levels)");
+    if ((e = cudaMalloc(&w->touched, (size_t)n * 4)) != cudaSuccess) return bad(e, "cudaMalloc(touched)");
+    if ((e = cudaMalloc(&w->ctrl, sizeof(MsCtrl))) != cudaSuccess) return bad(e, "cudaMalloc(ms ctrl)");
+    if ((e = cudaMalloc(&w->start, 64 * 4)) != cudaSuccess) return bad(e, "cudaMalloc(start)");
+    if ((e = cudaMalloc(&w->lane_src, 64 * 4)) != cudaSuccess) return bad(e, "cudaMalloc(lane sources)");
+    if ((e = cudaMalloc(&w->lane_row, 64 * 4)) != cudaSuccess) return bad(e, "cudaMalloc(lane rows)");
+    if ((e = cudaMallocHost(&w->h_ctrl, sizeof(MsCtrl))) != cudaSuccess) return bad(e, "cudaMallocHost(ms ctrl)");
+    if ((e = cudaMallocHost(&w->h_lanes, 2 * 64 * 4)) != cudaSuccess) return bad(e, "cudaMallocHost(lanes)");
+    if ((e = cudaStreamCreateWithFlags(&w->stream, cudaStreamNonBlocking)) != cudaSuccess) return bad(e, "cudaStreamCreate");
+    g->batch_ws = w;
+    const int rc = ms_reset(g);
+    if (rc != BFS_OK) return rc;
+    *out = w;
+    return BFS_OK;
+}
+
+void ms_free(Graph *g)
+{
+    MsWs *w = ws_of(g);
+    if (!w) return;
+    if (w->stream) cudaStreamSynchronize(w->stream);
+    cudaFree(w->seen);
+    cudaFree(w->next);
+    for (int b = 0; b < 2; ++b) {
+        cudaFree(w->front[b]);
+        for (int j = 0; j < 3; ++j) cudaFree(w->fq[b][j]);
+    }
+    cudaFree(w->lvl);
+    cudaFree(w->touched);
+    cudaFree(w->ctrl);
+    cudaFree(w->start);
+    cudaFree(w->lane_src);
+    cudaFree(w->lane_row);
+    if (w->h_ctrl) cudaFreeHost(w->h_ctrl);
+    if (w->h_lanes) cudaFreeHost(w->h_lanes);
+    if (w->stream) cudaStreamDestroy(w->stream);
+    delete w;
+    g->batch_ws = nullptr;
+}
+
+// All lanes free: clear the bit words, levels 0xFF, counters zero.
+int ms_reset(Graph *g)
+{
+    MsWs *w = ws_of(g);
+    const int64_t n = g->n;
+    cudaStream_t s = w->stream;
+    GB_CUDA(cudaMemsetAsync(w->seen, 0, (size_t)n * 8, s));
+    GB_CUDA(cudaMemsetAsync(w->next, 0, (size_t)n * 8, s));
+    GB_CUDA(cudaMemsetAsync(w->front[0], 0, (size_t)n * 8, s));
+    GB_CUDA(cudaMemsetAsync(w->front[1], 0, (size_t)n * 8, s));
+    GB_CUDA(cudaMemsetAsync(w->lvl, 0xFF, (size_t)n * 64, s));
+    GB_CUDA(cudaMemsetAsync(w->ctrl, 0, sizeof(MsCtrl), s));
+    GB_CUDA(cudaMemsetAsync(w->start, 0, 64 * 4, s));
+    return BFS_OK;
+}
+
+static MsParams make_params(Graph *g, MsWs *w, uint32_t max_iters)
+{
+    MsParams p;
+    p.ro = g->d_row_offsets;
+    p.col = g->d_col_idx;
+    p.orig = g->d_orig;
+    p.seen = w->seen;
+    p.next = w->next;
+    p.front[0] = w->front[0];
+    p.front[1] = w->front[1];
+    p.lvl = w->lvl;
+    for (int b = 0; b < 2; ++b) {
+        p.fu[b] = w->fq[b][0];
+        p.fb[b] = w->fq[b][1];
+        p.fl[b] = w->fq[b][2];
+    }
+    p.touched = w->touched;
+    p.start = w->start;
+    p.ctrl = w->ctrl;
+    p.n = (int32_t)g->n;
+    p.fcap = (uint32_t)std::min<int64_t>(w->fcap, 0x7FFFFFFFLL);
+    p.max_iters = max_iters;
+    p.timeout_ns = (uint64_t)g->opt.timeout_ns;
+    return p;
+}
+
+// Inject sources (caller numbering, validated) into the lanes of `mask`;
+// lane_src_host[lane] holds each source.  Asynchronous on the ws stream.
+int ms_inject(Graph *g, const int32_t *lane_src_caller, unsigned long long mask)
+{
+    MsWs *w = ws_of(g);
+    cudaStream_t s = w->stream;
+    // caller ids -> internal ids through perm on the device: copy the caller
+    // ids, then map them with a gather done by the inject kernel's inputs
+    int32_t *h = w->h_lanes;
+    for (int i = 0; i < 64; ++i) h[i] = ((mask >> i) & 1ull) ? lane_src_caller[i] : 0;
+    GB_CUDA(cudaMemcpyAsync(w->lane_src, h, 64 * 4, cudaMemcpyHostToDevice, s));
+    map_ids_kernel<<<1, 64, 0, s>>>(w->lane_src, g->d_perm, 64);
+    MsParams p = make_params(g, w, 0);
+    ms_inject_kernel<<<8, 256, 0, s>>>(p, w->lane_src, mask, w->start);
+    GB_CUDA(cudaGetLastError());
+    return BFS_OK;
+}
+
+// Run up to max_iters iterations (stops early when no lane has a frontier).
+int ms_step(Graph *g, uint32_t max_iters)
+{
+    MsWs *w = ws_of(g);
+    MsParams p = make_params(g, w, max_iters);
+    auto kern = ms_kernel;
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, MS_WPB * 32, 0);
+    if (e != cudaSuccess) return cuda_error(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor(ms_kernel)");
+    if (per_sm < 1) return set_error(BFS_ERR_CUDA, "ms_kernel: no CTA fits on an SM");
+    per_sm = std::min(per_sm, 4);
+    int grid = per_sm * g->num_sms;
+    if (g->opt.max_ctas > 0) grid = std::min(grid, g->opt.max_ctas);
+    void *args[] = {&p};
+    e = cudaLaunchCooperativeKernel((const void *)kern, dim3(grid), dim3(MS_WPB * 32), args, 0, w->stream);
+    if (e != cudaSuccess) return cuda_error(e, "cudaLaunchCooperativeKernel(ms_kernel)");
+    return BFS_OK;
+}
+
+// Copy the control block to pinned host memory and wait for it.
+int ms_read_ctrl(Graph *g, MsCtrl *out)
+{
+    MsWs *w = ws_of(g);
+    GB_CUDA(cudaMemcpyAsync(w->h_ctrl, w->ctrl, sizeof(MsCtrl), cudaMemcpyDeviceToHost, w->stream));
+    GB_CUDA(cudaStreamSynchronize(w->stream));
+    *out = *w->h_ctrl;
+    return BFS_OK;
+}
+
+// Level columns of the lanes in `mask` -> rows of `out` (device memory,
+// out_stride bytes apart; lane_row_host[lane] = row, -1 = skip); with
+// recycle the lanes are reset for reuse.  Asynchronous on the ws stream.
+int ms_extract(Graph *g, unsigned long long mask, const int32_t *lane_row_host, uint8_t *out, int64_t out_stride,
+               bool recycle)
+{
+    MsWs *w = ws_of(g);
+    cudaStream_t s = w->stream;
+    int32_t *h = w->h_lanes + 64;
+    for (int i = 0; i < 64; ++i) h[i] = lane_row_host ? lane_row_host[i] : -1;
+    GB_CUDA(cudaMemcpyAsync(w->lane_row, h, 64 * 4, cudaMemcpyHostToDevice, s));
+    const int64_t blocks = (g->n + 127) / 128;
+    ms_extract_kernel<<<(unsigned)blocks, 128, 0, s>>>(w->lvl, w->seen, g->d_perm, g->n, mask, w->lane_row, out,
+                                                      out_stride, recycle ? 1 : 0);
+    GB_CUDA(cudaGetLastError());
+    return BFS_OK;
+}
+
+__global__ void map_ids_kernel(int32_t *ids, const int32_t *__restrict__ perm, int k)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < k) ids[i] = perm[ids[i]];
+}
+
+// bfs_run_batch: batches of `batch_width` sources, each run to completion.
+int ms_run_batch(Graph *g, const int32_t *roots, int32_t k, uint8_t *level_out)
+{
+    MsWs *w = nullptr;
+    int rc = ms_alloc(g, &w);
+    if (rc != BFS_OK) return rc;
+    const int64_t n = g->n;
+    const bool out_dev = is_device_pointer(level_out);
+    uint8_t *d_out = level_out;
+    uint8_t *tmp = nullptr;
+    const int width = g->opt.batch_width;
+    if (!out_dev) {
+        GB_CUDA(cudaMalloc(&tmp, (size_t)width * n));
+        d_out = tmp;
+    }
+    bool depth = false;
+    for (int32_t b0 = 0; b0 < k && rc == BFS_OK; b0 += width) {
+        const int kb = std::min<int32_t>(width, k - b0);
+        unsigned long long mask = (kb == 64) ? ~0ull : ((1ull << kb) - 1ull);
+        int32_t src[64], rows[64];
+        for (int i = 0; i < 64; ++i) {
+            src[i] = i < kb ? roots[b0 + i] : 0;
+            rows[i] = i < kb ? (out_dev ? b0 + i : i) : -1;
+        }
+        if ((rc = ms_reset(g)) != BFS_OK) break;
+        if ((rc = ms_inject(g, src, mask)) != BFS_OK) break;
+        if ((rc = ms_step(g, 0x7FFFFFFFu)) != BFS_OK) break;
+        MsCtrl st;
+        if ((rc = ms_read_ctrl(g, &st)) != BFS_OK) break;
+        if (st.status & ST_TIMEOUT) rc = set_error(BFS_ERR_TIMEOUT, "bfs_run_batch: a device-side wait ran out");
+        else if (st.status & ST_OVERFLOW) rc = set_error(BFS_ERR_CUDA, "bfs_run_batch: a frontier append ran past its capacity");
+        if (st.status & ST_DEPTH) depth = true;
+        if (rc != BFS_OK) break;
+        if ((rc = ms_extract(g, mask, rows, d_out, n, false)) != BFS_OK) break;
+        if (!out_dev) {
+            cudaError_t e = cudaMemcpyAsync(level_out + (size_t)b0 * n, d_out, (size_t)kb * n, cudaMemcpyDeviceToHost, w->stream);
+            if (e != cudaSuccess) rc = cuda_error(e, "cudaMemcpy(batch levels)");
+        }
+    }
+    cudaError_t e = cudaStreamSynchronize(w->stream);
+    if (rc == BFS_OK && e != cudaSuccess) rc = cuda_error(e, "bfs_run_batch");
+    cudaFree(tmp);
+    if (rc == BFS_OK && depth) rc = set_error(BFS_ERR_DEPTH, "bfs_run_batch: a level exceeds 254");
+    return rc;
+}
 
 }  // namespace gbbfs

@@ -1,0 +1,51 @@
+// msbfs.cuh -- workspace and host entry points of the bit-parallel
+// multi-source search (msbfs.cu), shared with the serving loop (server.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "internal.cuh"
+
+namespace gbbfs {
+
+// Control block.  Counters of iteration parity p are used by iteration
+// iter (p = iter & 1) and cleared during the iteration of the other parity.
+struct MsCtrl {
+    unsigned fcount[2];           // frontier entries in buffer p
+    unsigned work[2];             // EXPAND dispenser
+    unsigned tcount[2];           // touched vertices
+    unsigned bar_count, bar_gen, exit_count;
+    unsigned status;              // ST_* bits
+    unsigned iter;                // global iteration number (persists across launches)
+    unsigned pad;
+    unsigned long long alive[2];  // lanes present in frontier buffer p
+};
+
+struct MsWs {
+    unsigned long long *seen = nullptr, *next = nullptr, *front[2] = {};
+    uint8_t *lvl = nullptr;       // [n][64] levels, caller numbering, 0xFF = unreached
+    int32_t *fq[2][3] = {};       // frontier entries (u, beg, len) per parity
+    int32_t *touched = nullptr;
+    MsCtrl *ctrl = nullptr;
+    int32_t *start = nullptr;     // [64] iteration each lane joined
+    int32_t *lane_src = nullptr;  // [64] staging for inject
+    int32_t *lane_row = nullptr;  // [64] staging for extract
+    MsCtrl *h_ctrl = nullptr;     // pinned
+    int32_t *h_lanes = nullptr;   // pinned, 128 entries
+    int64_t fcap = 0;
+    cudaStream_t stream = nullptr;
+};
+
+int ms_alloc(Graph *g, MsWs **out);
+int ms_reset(Graph *g);
+// sources in the caller's numbering, one per lane of `mask`
+int ms_inject(Graph *g, const int32_t *lane_src_caller, unsigned long long mask);
+// up to max_iters iterations, stopping when no lane has a frontier
+int ms_step(Graph *g, uint32_t max_iters);
+int ms_read_ctrl(Graph *g, MsCtrl *out);
+int ms_extract(Graph *g, unsigned long long mask, const int32_t *lane_row_host, uint8_t *out, int64_t out_stride,
+               bool recycle);
+__global__ void map_ids_kernel(int32_t *ids, const int32_t *__restrict__ perm, int k);
+
+}  // namespace gbbfs
