@@ -52,6 +52,10 @@ def parse_args(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--option", action="append", default=[],
                     help="name=value tunable passed to bfs_graph_set_option")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the batched (bit-parallel multi-source) measurement")
+    ap.add_argument("--batched-scale", type=int, default=20)
+    ap.add_argument("--batched-sources", type=int, default=1024)
     ap.add_argument("--profile-layers", action="store_true",
                     help="print the per-layer counters and device times of one search to stderr")
     return ap.parse_args(argv)
@@ -238,6 +242,49 @@ def run_reference(args):
     return 0
 
 
+def batched_measurement(args, gb, torch, dev):
+    """1,024 seeded sources on a Kronecker graph (scale 20, ef 16) through
+    bfs_run_batch (64 sources per bit-parallel batch), against the plain path
+    (bfs_run, one query at a time) on the same GPU and the same sources."""
+    import graphgen
+    ro, col = graphgen.kronecker(args.batched_scale, args.edgefactor, args.seed)
+    roots = graphgen.pick_roots(ro, args.batched_sources, args.seed + 7)
+    n = len(ro) - 1
+    g = gb.Graph(ro, col)
+    out = torch.empty((len(roots), n), dtype=torch.uint8, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    gb.bfs_run_batch(g.handle, roots, out)  # warm-up
+    times = []
+    for _ in range(3):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        gb.bfs_run_batch(g.handle, roots, out)
+        times.append(time.perf_counter() - t0)
+    t_batch = min(times)
+    level = torch.empty(n, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    for r in roots[:8]:
+        gb.bfs_run(g.handle, int(r), level, None, stream)
+    flush.fill_(1)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for r in roots:
+        gb.bfs_run(g.handle, int(r), level, None, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_plain = e0.elapsed_time(e1) * 1e-3
+    g.close()
+    return {"workload": f"kronecker_scale{args.batched_scale}_ef{args.edgefactor}_{len(roots)}sources",
+            "batch_width": 64, "queries_per_s": len(roots) / t_batch,
+            "plain_queries_per_s": len(roots) / t_plain, "speedup_vs_plain": t_plain / t_batch,
+            "s_per_1024_batched": t_batch, "s_per_1024_plain": t_plain,
+            "how": "host wall clock around the synchronous bfs_run_batch (device output, best of 3); "
+                   "plain = CUDA events around back-to-back bfs_run (levels only) on one stream"}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -359,6 +406,9 @@ def run_ours(args):
         step_ms = 1e3 * max(float(x[1]) for x in gathered) / args.steps
 
     options = {k: g.get_option(k) for k in gb.OPTION_NAMES}
+    batched = None
+    if not args.no_batched and rank == 0:
+        batched = batched_measurement(args, gb, torch, dev)
     if rank == 0:
         cpu = None
         if not args.no_cpu_baseline:
@@ -382,6 +432,7 @@ def run_ours(args):
                          "mean_launch_s": mean_t},
             "cpu_baseline": cpu,
             "e2e": e2e,
+            "batched": batched,
             "gpu_launches": len(runs),
             "clocks": clocks.summary(),
             "wall_s_timed": wall,

@@ -225,12 +225,15 @@ bfs_server *bfs_server_create(int64_t hbm_budget_bytes);
 int bfs_server_destroy(bfs_server *s);
 
 /* Register a graph (not owned: keep it alive until bfs_server_destroy).
+ * From then on the server owns the graph's batch workspace: do not call
+ * bfs_run_batch on it while it is registered (bfs_run stays available).
  * Returns a graph id >= 0 or a negative bfs_status. */
 int bfs_server_add_graph(bfs_server *s, bfs_graph *g);
 
 /* Queue one BFS query.  level_out: host uint8[n] of that graph, written as in
  * bfs_run_batch (0xFF = unreached); it must stay valid until bfs_poll
- * reports completion.  *ticket receives the query's id. */
+ * reports completion.  *ticket receives the query's id.  Returns
+ * BFS_ERR_BUSY if the graph's workspace can never fit the HBM budget. */
 int bfs_submit(bfs_server *s, int graph_id, int32_t root, uint8_t *level_out,
                uint64_t *ticket);
 

@@ -318,3 +318,48 @@ class Graph:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class Server:
+    """Continuous-batching request loop over resident graphs (C ABI
+    bfs_server_*).  ``submit`` returns a ticket; ``poll``/``wait`` report
+    completion; results land in the host uint8 buffer given at submit."""
+
+    def __init__(self, hbm_budget_bytes: int = 0):
+        self.handle = bfs_server_create(hbm_budget_bytes)
+        self._keep = {}
+
+    def add_graph(self, graph: "Graph") -> int:
+        return bfs_server_add_graph(self.handle, graph.handle)
+
+    def submit(self, graph_id: int, root: int, level_out: np.ndarray) -> int:
+        assert level_out.dtype == np.uint8 and level_out.flags["C_CONTIGUOUS"]
+        t = bfs_submit(self.handle, graph_id, root, level_out)
+        self._keep[t] = level_out
+        return t
+
+    def poll(self, ticket: int) -> bool:
+        return bfs_poll(self.handle, ticket) == BFS_OK
+
+    def wait(self, ticket: int, sleep_s: float = 0.0) -> None:
+        import time
+        while not self.poll(ticket):
+            if sleep_s:
+                time.sleep(sleep_s)
+
+    def drain(self) -> None:
+        bfs_server_drain(self.handle)
+
+    def times(self, ticket: int):
+        return bfs_ticket_times(self.handle, ticket)
+
+    def close(self):
+        if self.handle:
+            bfs_server_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

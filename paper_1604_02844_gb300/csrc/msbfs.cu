@@ -90,11 +90,30 @@ __device__ __forceinline__ void append_frontier(const MsParams &p, int q, bool w
     }
 }
 
-__device__ __forceinline__ void ms_expand(const MsParams &p, int par, unsigned nF)
+constexpr int TB = 128;  // touched-vertex buffer per warp (shared memory)
+
+// Move a warp's buffered touched vertices to the global list: one atomicAdd.
+__device__ __forceinline__ void flush_touched(const MsParams &p, int par, int32_t *tbuf, int cnt)
+{
+    const int lane = threadIdx.x & 31;
+    unsigned base = 0;
+    if (lane == 0) base = atomicAdd(&p.ctrl->tcount[par], (unsigned)cnt);
+    base = __shfl_sync(FULL, base, 0);
+    __syncwarp();
+    for (int i = lane; i < cnt; i += 32) {
+        const unsigned at = base + (unsigned)i;
+        if (at < (unsigned)p.n) p.touched[at] = tbuf[i];
+        else atomicOr(&p.ctrl->status, ST_OVERFLOW);
+    }
+    __syncwarp();
+}
+
+__device__ __forceinline__ void ms_expand(const MsParams &p, int par, unsigned nF, int32_t *tbuf)
 {
     const int lane = threadIdx.x & 31;
     const unsigned lt = lanemask_lt();
     MsCtrl *c = p.ctrl;
+    int tcnt = 0;  // warp-uniform fill of tbuf
     for (;;) {
         unsigned base = 0;
         if (lane == 0) base = atomicAdd(&c->work[par], 32u);
@@ -136,30 +155,58 @@ __device__ __forceinline__ void ms_expand(const MsParams &p, int par, unsigned n
                 v[x] = (e < E) ? __ldg(p.col + jb + (e - jo)) : -1;
                 nb[x] = jf;
             }
+            // lanes that neither reached v before nor already reach it now:
+            // most edges into hubs stop here, without an atomic
 #pragma unroll
             for (int x = 0; x < UX; ++x)
-                if (v[x] >= 0) nb[x] &= ~__ldcg(p.seen + v[x]);
+                if (v[x] >= 0) nb[x] &= ~(__ldcg(p.seen + v[x]) | __ldcg(p.next + v[x]));
 #pragma unroll
             for (int x = 0; x < UX; ++x) {
                 bool first = false;
                 if (v[x] >= 0 && nb[x]) first = (atomicOr(p.next + v[x], nb[x]) == 0ull);
                 const unsigned m = __ballot_sync(FULL, first);
                 if (m) {
-                    unsigned tb = 0;
-                    if (lane == 0) tb = atomicAdd(&c->tcount[par], (unsigned)__popc(m));
-                    tb = __shfl_sync(FULL, tb, 0);
-                    if (first) {
-                        const unsigned at = tb + __popc(m & lt);
-                        if (at < (unsigned)p.n) p.touched[at] = v[x];
-                        else atomicOr(&c->status, ST_OVERFLOW);
+                    if (tcnt + __popc(m) > TB) {
+                        flush_touched(p, par, tbuf, tcnt);
+                        tcnt = 0;
                     }
+                    if (first) tbuf[tcnt + __popc(m & lt)] = v[x];
+                    tcnt += __popc(m);
                 }
             }
         }
     }
+    __syncwarp();
+    if (tcnt) flush_touched(p, par, tbuf, tcnt);
 }
 
-__device__ __forceinline__ void ms_update(const MsParams &p, int par, unsigned nF, unsigned iter, unsigned long long &alive)
+// Write level bytes of the lanes in nn into a vertex's 64-byte level line:
+// byte i becomes lv[i] where bit i of nn is set.  Branch-free per 16-byte
+// chunk (bit masks widened to byte masks), so a vertex reached by many lanes
+// at once costs the same as one reached by a single lane.
+__device__ __forceinline__ void merge_levels(uint4 *row, unsigned long long nn, const uint32_t *lv)
+{
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const unsigned m16 = (unsigned)(nn >> (16 * q)) & 0xFFFFu;
+        if (!m16) continue;
+        uint4 x = row[q];
+        uint32_t *xw = reinterpret_cast<uint32_t *>(&x);
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            const unsigned m4 = (m16 >> (4 * w)) & 0xFu;
+            const uint32_t bm = ((m4 & 1u) ? 0x000000FFu : 0u) | ((m4 & 2u) ? 0x0000FF00u : 0u) |
+                                ((m4 & 4u) ? 0x00FF0000u : 0u) | ((m4 & 8u) ? 0xFF000000u : 0u);
+            xw[w] = (xw[w] & ~bm) | (lv[4 * q + w] & bm);
+        }
+        row[q] = x;
+    }
+}
+
+constexpr int UU = 4;  // touched vertices per lane per round
+
+__device__ __forceinline__ void ms_update(const MsParams &p, int par, unsigned nF, unsigned iter, unsigned long long &alive,
+                                          const uint32_t *s_lv, unsigned long long over)
 {
     const int lane = threadIdx.x & 31;
     const int q = par ^ 1;
@@ -169,36 +216,67 @@ __device__ __forceinline__ void ms_update(const MsParams &p, int par, unsigned n
     const unsigned gsz = gridDim.x * blockDim.x;
     // the old frontier words
     for (unsigned i = gtid; i < nF; i += gsz) p.front[par][__ldcg(p.fu[par] + i)] = 0ull;
-    // the touched vertices
-    for (unsigned i0 = gtid - lane; i0 < nT; i0 += gsz) {  // warp-uniform loop
-        const unsigned i = i0 + lane;
-        int v = 0, rb = 0, len = 0;
-        unsigned long long nn = 0;
-        if (i < nT) {
-            v = __ldcg(p.touched + i);
-            const unsigned long long x = __ldcg(p.next + v);
-            p.next[v] = 0ull;
-            const unsigned long long s = __ldcg(p.seen + v);
-            nn = x & ~s;
-            if (nn) {
-                p.seen[v] = s | nn;
-                p.front[q][v] = nn;
-                alive |= nn;
-                const int ov = __ldg(p.orig + v);
-                uint8_t *row = p.lvl + (size_t)ov * 64;
-                unsigned long long bits = nn;
-                while (bits) {
-                    const int ln = __ffsll((long long)bits) - 1;
-                    bits &= bits - 1;
-                    const int lvv = (int)iter + 1 - __ldg(p.start + ln);
-                    if (lvv > 254) atomicOr(&c->status, ST_DEPTH);
-                    row[ln] = (uint8_t)min(lvv, 254);
+    // the touched vertices, UU per lane per round (warp-uniform loop)
+    for (unsigned i0 = (gtid - lane) * UU; i0 < nT; i0 += gsz * UU) {
+        int v[UU], rb[UU], len[UU];
+        unsigned long long x[UU], sn[UU], nn[UU];
+#pragma unroll
+        for (int k = 0; k < UU; ++k) {
+            const unsigned i = i0 + k * 32 + lane;
+            v[k] = (i < nT) ? __ldcg(p.touched + i) : -1;
+        }
+#pragma unroll
+        for (int k = 0; k < UU; ++k) {
+            x[k] = v[k] >= 0 ? __ldcg(p.next + v[k]) : 0ull;
+            sn[k] = v[k] >= 0 ? __ldcg(p.seen + v[k]) : 0ull;
+        }
+        int ns = 0;
+#pragma unroll
+        for (int k = 0; k < UU; ++k) {
+            nn[k] = x[k] & ~sn[k];
+            rb[k] = 0;
+            len[k] = 0;
+            if (v[k] >= 0) {
+                p.next[v[k]] = 0ull;
+                if (nn[k]) {
+                    p.seen[v[k]] = sn[k] | nn[k];
+                    p.front[q][v[k]] = nn[k];
+                    alive |= nn[k];
+                    if (nn[k] & over) atomicOr(&c->status, ST_DEPTH);
+                    const int ov = __ldg(p.orig + v[k]);
+                    merge_levels(reinterpret_cast<uint4 *>(p.lvl + (size_t)ov * 64), nn[k], s_lv);
+                    rb[k] = __ldg(p.ro + v[k]);
+                    len[k] = __ldg(p.ro + v[k] + 1) - rb[k];
+                    ns += (len[k] + H - 1) / H;
                 }
-                rb = __ldg(p.ro + v);
-                len = __ldg(p.ro + v + 1) - rb;
             }
         }
-        append_frontier(p, q, nn != 0ull && len > 0, v, rb, len);
+        // one reservation for the whole warp's slices of this round
+        int inc = ns;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(FULL, inc, o);
+            if (lane >= o) inc += y;
+        }
+        const int total = __shfl_sync(FULL, inc, 31);
+        if (total == 0) continue;
+        unsigned base = 0;
+        if (lane == 31) base = atomicAdd(&c->fcount[q], (unsigned)total);
+        base = __shfl_sync(FULL, base, 31);
+        unsigned pos = base + (unsigned)(inc - ns);
+#pragma unroll
+        for (int k = 0; k < UU; ++k) {
+            if (!nn[k] || len[k] <= 0) continue;
+            for (int sg = 0; sg * H < len[k]; ++sg, ++pos) {
+                if (pos < p.fcap) {
+                    p.fu[q][pos] = v[k];
+                    p.fb[q][pos] = rb[k] + sg * H;
+                    p.fl[q][pos] = min(H, len[k] - sg * H);
+                } else {
+                    atomicOr(&c->status, ST_OVERFLOW);
+                }
+            }
+        }
     }
 }
 
@@ -207,6 +285,9 @@ __global__ void __launch_bounds__(MS_WPB * 32) ms_kernel(MsParams p)
     __shared__ int s_ok;
     __shared__ unsigned s_nF, s_iter0;
     __shared__ unsigned long long s_alive;
+    __shared__ uint32_t s_lv[16];
+    __shared__ int32_t s_tbuf[MS_WPB][TB];
+    __shared__ unsigned long long s_over;  // lanes whose level this iteration would exceed 254
     const int tid = threadIdx.x, lane = tid & 31;
     const unsigned G = gridDim.x;
     MsCtrl *c = p.ctrl;
@@ -233,11 +314,24 @@ __global__ void __launch_bounds__(MS_WPB * 32) ms_kernel(MsParams p)
             c->tcount[par ^ 1] = 0;
             c->alive[par ^ 1] = 0ull;
         }
-        ms_expand(p, par, nF);
+        ms_expand(p, par, nF, s_tbuf[threadIdx.x >> 5]);
         ok = grid_sync(&c->bar_count, &c->bar_gen, &c->status, G, p.timeout_ns, &s_ok);
         if (!ok) break;
+        // this iteration's level byte per lane, packed four to a word
+        if (tid < 16) {
+            uint32_t w = 0;
+            for (int k = 0; k < 4; ++k) {
+                const int lvv = (int)iter + 1 - __ldg(p.start + 4 * tid + k);
+                w |= (uint32_t)(min(max(lvv, 0), 254)) << (8 * k);
+            }
+            s_lv[tid] = w;
+        }
+        if (tid == 0) s_over = 0ull;
+        __syncthreads();
+        if (tid < 64 && (int)iter + 1 - __ldg(p.start + tid) > 254) atomicOr(&s_over, 1ull << tid);
+        __syncthreads();
         unsigned long long alive = 0;
-        ms_update(p, par, nF, iter, alive);
+        ms_update(p, par, nF, iter, alive, s_lv, s_over);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) alive |= __shfl_xor_sync(FULL, alive, o);
         if (lane == 0 && alive) atomicOr(&s_alive, alive);
@@ -467,8 +561,9 @@ int ms_inject(Graph *g, const int32_t *lane_src_caller, unsigned long long mask)
     return BFS_OK;
 }
 
-// Run up to max_iters iterations (stops early when no lane has a frontier).
-int ms_step(Graph *g, uint32_t max_iters)
+// Run up to max_iters iterations (stops early when no lane has a frontier),
+// with at most max_ctas CTAs (0 = as many as fit).
+int ms_step_capped(Graph *g, uint32_t max_iters, int max_ctas)
 {
     MsWs *w = ws_of(g);
     MsParams p = make_params(g, w, max_iters);
@@ -479,12 +574,14 @@ int ms_step(Graph *g, uint32_t max_iters)
     if (per_sm < 1) return set_error(BFS_ERR_CUDA, "ms_kernel: no CTA fits on an SM");
     per_sm = std::min(per_sm, 4);
     int grid = per_sm * g->num_sms;
-    if (g->opt.max_ctas > 0) grid = std::min(grid, g->opt.max_ctas);
+    if (max_ctas > 0) grid = std::min(grid, max_ctas);
     void *args[] = {&p};
     e = cudaLaunchCooperativeKernel((const void *)kern, dim3(grid), dim3(MS_WPB * 32), args, 0, w->stream);
     if (e != cudaSuccess) return cuda_error(e, "cudaLaunchCooperativeKernel(ms_kernel)");
     return BFS_OK;
 }
+
+int ms_step(Graph *g, uint32_t max_iters) { return ms_step_capped(g, max_iters, g->opt.max_ctas); }
 
 // Copy the control block to pinned host memory and wait for it.
 int ms_read_ctrl(Graph *g, MsCtrl *out)

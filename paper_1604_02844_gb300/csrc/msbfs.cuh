@@ -43,6 +43,7 @@ int ms_reset(Graph *g);
 int ms_inject(Graph *g, const int32_t *lane_src_caller, unsigned long long mask);
 // up to max_iters iterations, stopping when no lane has a frontier
 int ms_step(Graph *g, uint32_t max_iters);
+int ms_step_capped(Graph *g, uint32_t max_iters, int max_ctas);
 int ms_read_ctrl(Graph *g, MsCtrl *out);
 int ms_extract(Graph *g, unsigned long long mask, const int32_t *lane_row_host, uint8_t *out, int64_t out_stride,
                bool recycle);

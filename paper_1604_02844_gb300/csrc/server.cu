@@ -1,14 +1,371 @@
-// server.cu -- continuous-batching request loop (filled in by the serving work).
+// server.cu -- continuous-batching BFS request loop over resident graphs.
+//
+// Not in the paper.  Queries (graph, root) are served by the bit-parallel
+// search of msbfs.cu.  Each graph with work owns a 64-lane workspace; a
+// worker thread repeats, for every such graph:
+//   1. put waiting queries into free lanes of the running search (a lane
+//      that joins at iteration t reports levels iter + 1 - t);
+//   2. advance the search a few iterations (one cooperative launch on the
+//      graph's own stream, its grid capped to a share of the GPU so that
+//      several graphs' searches run on the device at the same time);
+//   3. read which lanes still have a frontier; the others are finished:
+//      their level columns are copied to the callers' buffers, the lanes
+//      are reset and become free for the next queries.
+// A workspace is created only while the device memory it needs fits the
+// server's budget; a graph with no running or waiting query gives its
+// workspace back when another graph needs the room.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <vector>
+
 #include "internal.cuh"
+#include "msbfs.cuh"
+
+namespace gbbfs {
+namespace {
+
+int64_t now_ns()
+{
+    return std::chrono::duration_cast<std::chrono::nanoseconds>(std::chrono::steady_clock::now().time_since_epoch())
+        .count();
+}
+
+struct Request {
+    int graph = 0;
+    int32_t root = 0;
+    uint8_t *out = nullptr;
+    int64_t t_submit = 0, t_done = 0;
+    std::atomic<int> status{BFS_NOT_READY};
+};
+
+struct GraphState {
+    Graph *g = nullptr;
+    std::deque<uint64_t> waiting;     // tickets
+    uint64_t lane_ticket[64] = {};
+    unsigned long long running = 0;   // occupied lanes
+    bool has_ws = false;
+    int64_t ws_bytes = 0;
+    uint8_t *d_stage = nullptr;       // [64][n] extraction rows
+    bool launched = false;
+};
+
+// Device bytes of one graph's serving workspace (msbfs workspace + rows).
+int64_t workspace_bytes(const Graph *g)
+{
+    const int64_t n = g->n, fcap = n + 2 * (g->m / 256) + 2;
+    return n * (8 * 4 + 64 + 4) + fcap * 4 * 6 + 64 * n + (1 << 20);
+}
+
+}  // namespace
+
+struct Server {
+    int64_t budget = 0, used = 0;
+    int device = 0;
+    int total_ctas = 0;
+    uint32_t iters_per_step = 2;
+    std::vector<std::unique_ptr<GraphState>> graphs;
+    std::vector<std::unique_ptr<Request>> reqs;  // ticket = index + 1
+    std::mutex mu;
+    std::condition_variable cv, done_cv;
+    bool stop = false;
+    int64_t outstanding = 0;
+    std::thread worker;
+    int error = BFS_OK;
+
+    void run();
+    int service(GraphState &gs);
+    int finish(GraphState &gs, unsigned long long mask);
+    bool ensure_ws(GraphState &gs);
+};
+
+bool Server::ensure_ws(GraphState &gs)
+{
+    if (gs.has_ws) return true;
+    const int64_t need = workspace_bytes(gs.g);
+    if (used + need > budget) {
+        // evict idle workspaces until it fits
+        for (auto &o : graphs) {
+            if (used + need <= budget) break;
+            if (o.get() != &gs && o->has_ws && o->running == 0 && o->waiting.empty()) {
+                ms_free(o->g);
+                cudaFree(o->d_stage);
+                o->d_stage = nullptr;
+                o->has_ws = false;
+                used -= o->ws_bytes;
+            }
+        }
+        if (used + need > budget) return false;
+    }
+    MsWs *w = nullptr;
+    if (ms_alloc(gs.g, &w) != BFS_OK) return false;
+    if (cudaMalloc(&gs.d_stage, (size_t)64 * gs.g->n) != cudaSuccess) {
+        ms_free(gs.g);
+        return false;
+    }
+    gs.has_ws = true;
+    gs.ws_bytes = need;
+    used += need;
+    gs.running = 0;
+    return true;
+}
+
+// Copy finished lanes to their callers and free the lanes.
+int Server::finish(GraphState &gs, unsigned long long mask)
+{
+    if (!mask) return BFS_OK;
+    int32_t rows[64];
+    for (int i = 0; i < 64; ++i) rows[i] = ((mask >> i) & 1ull) ? i : -1;
+    int rc = ms_extract(gs.g, mask, rows, gs.d_stage, gs.g->n, true);
+    if (rc != BFS_OK) return rc;
+    MsWs *w = reinterpret_cast<MsWs *>(gs.g->batch_ws);
+    for (int i = 0; i < 64; ++i) {
+        if (!((mask >> i) & 1ull)) continue;
+        Request &r = *reqs[gs.lane_ticket[i] - 1];
+        cudaError_t e = cudaMemcpyAsync(r.out, gs.d_stage + (size_t)i * gs.g->n, (size_t)gs.g->n,
+                                        cudaMemcpyDeviceToHost, w->stream);
+        if (e != cudaSuccess) return cuda_error(e, "server: result copy");
+    }
+    cudaError_t e = cudaStreamSynchronize(w->stream);
+    if (e != cudaSuccess) return cuda_error(e, "server: result copy");
+    const int64_t t = now_ns();
+    std::lock_guard<std::mutex> lk(mu);
+    for (int i = 0; i < 64; ++i) {
+        if (!((mask >> i) & 1ull)) continue;
+        Request &r = *reqs[gs.lane_ticket[i] - 1];
+        r.t_done = t;
+        r.status.store(BFS_OK);
+        gs.lane_ticket[i] = 0;
+        --outstanding;
+    }
+    gs.running &= ~mask;
+    done_cv.notify_all();
+    return BFS_OK;
+}
+
+// Inject waiting queries into free lanes and launch a few iterations.
+int Server::service(GraphState &gs)
+{
+    gs.launched = false;
+    unsigned long long add = 0;
+    int32_t src[64] = {0};
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (gs.waiting.empty() && gs.running == 0) return BFS_OK;
+        if (!ensure_ws(gs)) return BFS_OK;  // no room yet: the queries wait
+        while (!gs.waiting.empty() && (gs.running | add) != ~0ull) {
+            const int lane = __builtin_ctzll(~(gs.running | add));
+            const uint64_t t = gs.waiting.front();
+            gs.waiting.pop_front();
+            gs.lane_ticket[lane] = t;
+            src[lane] = reqs[t - 1]->root;
+            add |= 1ull << lane;
+        }
+    }
+    if (add) {
+        const int rc = ms_inject(gs.g, src, add);
+        if (rc != BFS_OK) return rc;
+        gs.running |= add;
+    }
+    if (gs.running == 0) return BFS_OK;
+    int active = 0;
+    for (auto &o : graphs)
+        if (o->running) ++active;
+    const int share = std::max(gs.g->num_sms, total_ctas / std::max(1, active));
+    const int rc = ms_step_capped(gs.g, iters_per_step, share);
+    if (rc != BFS_OK) return rc;
+    gs.launched = true;
+    return BFS_OK;
+}
+
+void Server::run()
+{
+    cudaSetDevice(device);
+    while (true) {
+        {
+            std::unique_lock<std::mutex> lk(mu);
+            cv.wait(lk, [&] {
+                if (stop) return true;
+                for (auto &gs : graphs)
+                    if (!gs->waiting.empty() || gs->running) return true;
+                return false;
+            });
+            if (stop) break;
+        }
+        int rc = BFS_OK;
+        for (auto &gs : graphs)
+            if (rc == BFS_OK) rc = service(*gs);
+        for (auto &gs : graphs) {
+            if (rc != BFS_OK || !gs->launched) continue;
+            MsCtrl st;
+            rc = ms_read_ctrl(gs->g, &st);
+            if (rc != BFS_OK) break;
+            if (st.status & (ST_TIMEOUT | ST_OVERFLOW | ST_DEPTH)) {
+                rc = set_error(st.status & ST_DEPTH ? BFS_ERR_DEPTH : (st.status & ST_TIMEOUT ? BFS_ERR_TIMEOUT : BFS_ERR_CUDA),
+                               "server: device-side error in a batched search");
+                break;
+            }
+            const unsigned long long alive = st.alive[st.iter & 1];
+            rc = finish(*gs, gs->running & ~alive);
+        }
+        if (rc != BFS_OK) {
+            // fail every outstanding query rather than hang the callers
+            std::lock_guard<std::mutex> lk(mu);
+            error = rc;
+            for (auto &r : reqs)
+                if (r->status.load() == BFS_NOT_READY) {
+                    r->status.store(rc);
+                    r->t_done = now_ns();
+                }
+            for (auto &gs : graphs) {
+                gs->waiting.clear();
+                gs->running = 0;
+            }
+            outstanding = 0;
+            done_cv.notify_all();
+            break;
+        }
+    }
+}
+
+}  // namespace gbbfs
 
 using namespace gbbfs;
 
 extern "C" {
-bfs_server *bfs_server_create(int64_t) { set_error(BFS_ERR_INVALID_ARG, "server not in this build yet"); return nullptr; }
-int bfs_server_destroy(bfs_server *) { return BFS_OK; }
-int bfs_server_add_graph(bfs_server *, bfs_graph *) { return set_error(BFS_ERR_INVALID_ARG, "server not in this build yet"); }
-int bfs_submit(bfs_server *, int, int32_t, uint8_t *, uint64_t *) { return set_error(BFS_ERR_INVALID_ARG, "server not in this build yet"); }
-int bfs_poll(bfs_server *, uint64_t) { return set_error(BFS_ERR_INVALID_ARG, "server not in this build yet"); }
-int bfs_server_drain(bfs_server *) { return BFS_OK; }
-int bfs_ticket_times(bfs_server *, uint64_t, int64_t *, int64_t *) { return set_error(BFS_ERR_INVALID_ARG, "server not in this build yet"); }
+
+bfs_server *bfs_server_create(int64_t hbm_budget_bytes)
+{
+    clear_error();
+    if (hbm_budget_bytes < 0) {
+        set_error(BFS_ERR_INVALID_ARG, "bfs_server_create: negative budget");
+        return nullptr;
+    }
+    Server *s = new (std::nothrow) Server();
+    if (!s) {
+        set_error(BFS_ERR_OOM, "bfs_server_create: host allocation");
+        return nullptr;
+    }
+    cudaGetDevice(&s->device);
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
+    s->total_ctas = 4 * sms;
+    size_t free_b = 0, total_b = 0;
+    cudaMemGetInfo(&free_b, &total_b);
+    s->budget = hbm_budget_bytes > 0 ? hbm_budget_bytes : (int64_t)(0.8 * (double)free_b);
+    s->worker = std::thread([s] { s->run(); });
+    return reinterpret_cast<bfs_server *>(s);
 }
+
+int bfs_server_destroy(bfs_server *sh)
+{
+    if (!sh) return BFS_OK;
+    Server *s = reinterpret_cast<Server *>(sh);
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop = true;
+    }
+    s->cv.notify_all();
+    if (s->worker.joinable()) s->worker.join();
+    for (auto &gs : s->graphs) {
+        if (gs->has_ws) {
+            ms_free(gs->g);
+            cudaFree(gs->d_stage);
+        }
+    }
+    delete s;
+    return BFS_OK;
+}
+
+int bfs_server_add_graph(bfs_server *sh, bfs_graph *gh)
+{
+    clear_error();
+    if (!sh || !gh) return set_error(BFS_ERR_INVALID_ARG, "bfs_server_add_graph: NULL argument");
+    Server *s = reinterpret_cast<Server *>(sh);
+    Graph *g = reinterpret_cast<Graph *>(gh);
+    std::lock_guard<std::mutex> lk(s->mu);
+    for (auto &gs : s->graphs)
+        if (gs->g == g) return set_error(BFS_ERR_INVALID_ARG, "bfs_server_add_graph: graph already added");
+    {
+        // the server manages the graph's batch workspace from now on
+        std::lock_guard<std::mutex> glk(g->mu);
+        ms_free(g);
+    }
+    auto gs = std::make_unique<GraphState>();
+    gs->g = g;
+    s->graphs.push_back(std::move(gs));
+    return (int)s->graphs.size() - 1;
+}
+
+int bfs_submit(bfs_server *sh, int graph_id, int32_t root, uint8_t *level_out, uint64_t *ticket)
+{
+    clear_error();
+    if (!sh || !level_out || !ticket) return set_error(BFS_ERR_INVALID_ARG, "bfs_submit: NULL argument");
+    Server *s = reinterpret_cast<Server *>(sh);
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->error != BFS_OK) return set_error(s->error, "bfs_submit: the server stopped after an error");
+    if (graph_id < 0 || graph_id >= (int)s->graphs.size()) return set_error(BFS_ERR_INVALID_ARG, "bfs_submit: unknown graph id");
+    GraphState &gs = *s->graphs[graph_id];
+    if (root < 0 || (int64_t)root >= gs.g->n) return set_error(BFS_ERR_INVALID_ARG, "bfs_submit: root outside [0, n)");
+    if (workspace_bytes(gs.g) > s->budget)
+        return set_error(BFS_ERR_BUSY, "bfs_submit: the graph's workspace exceeds the server's HBM budget");
+    auto r = std::make_unique<Request>();
+    r->graph = graph_id;
+    r->root = root;
+    r->out = level_out;
+    r->t_submit = now_ns();
+    s->reqs.push_back(std::move(r));
+    const uint64_t t = s->reqs.size();
+    gs.waiting.push_back(t);
+    ++s->outstanding;
+    *ticket = t;
+    s->cv.notify_one();
+    return BFS_OK;
+}
+
+int bfs_poll(bfs_server *sh, uint64_t ticket)
+{
+    if (!sh) return set_error(BFS_ERR_INVALID_ARG, "bfs_poll: NULL server");
+    Server *s = reinterpret_cast<Server *>(sh);
+    Request *r;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (ticket == 0 || ticket > s->reqs.size()) return set_error(BFS_ERR_INVALID_ARG, "bfs_poll: unknown ticket");
+        r = s->reqs[ticket - 1].get();
+    }
+    const int st = r->status.load();
+    if (st < 0) set_error(st, "bfs_poll: the query failed");
+    return st;
+}
+
+int bfs_server_drain(bfs_server *sh)
+{
+    if (!sh) return set_error(BFS_ERR_INVALID_ARG, "bfs_server_drain: NULL server");
+    Server *s = reinterpret_cast<Server *>(sh);
+    std::unique_lock<std::mutex> lk(s->mu);
+    s->done_cv.wait(lk, [&] { return s->outstanding == 0 || s->error != BFS_OK; });
+    return s->error;
+}
+
+int bfs_ticket_times(bfs_server *sh, uint64_t ticket, int64_t *t_submit_ns, int64_t *t_done_ns)
+{
+    if (!sh || !t_submit_ns || !t_done_ns) return set_error(BFS_ERR_INVALID_ARG, "bfs_ticket_times: NULL argument");
+    Server *s = reinterpret_cast<Server *>(sh);
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (ticket == 0 || ticket > s->reqs.size()) return set_error(BFS_ERR_INVALID_ARG, "bfs_ticket_times: unknown ticket");
+    Request &r = *s->reqs[ticket - 1];
+    *t_submit_ns = r.t_submit;
+    *t_done_ns = r.t_done;
+    return BFS_OK;
+}
+
+}  // extern "C"

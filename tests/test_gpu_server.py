@@ -1,0 +1,125 @@
+"""The serving loop (bfs_server_*): continuous batching over resident graphs.
+
+Each query's levels must be the same whether it ran alone or in a mixed
+stream that arrived while other queries were on the GPU (exact: the search
+is integer), and equal to the oracle's.
+"""
+import random
+import threading
+import time
+
+import numpy as np
+import pytest
+
+import graphgen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_1604_02844_gb300 as gb  # noqa: E402
+from paper_1604_02844_gb300 import build as lib_build  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    lib_build.build()
+    gb.load()
+
+
+@pytest.fixture(scope="module")
+def resident():
+    specs = [("kron", 12, 8), ("kron", 14, 16), ("kron", 16, 16), ("er", 13, 16)]
+    out = []
+    for kind, scale, ef in specs:
+        ro, col = (graphgen.kronecker if kind == "kron" else graphgen.erdos_renyi)(scale, ef, 50 + scale)
+        out.append((ro, col, gb.Graph(ro, col)))
+    yield out
+    for _, _, g in out:
+        g.close()
+
+
+def make_queries(resident, k, seed):
+    rng = random.Random(seed)
+    qs = []
+    for _ in range(k):
+        gi = rng.randrange(len(resident))
+        ro = resident[gi][0]
+        r = int(graphgen.pick_roots(ro, 1, rng.randrange(1 << 30))[0])
+        qs.append((gi, r))
+    return qs
+
+
+def run_alone(server, ids, resident, queries):
+    res = []
+    for gi, r in queries:
+        buf = np.empty(len(resident[gi][0]) - 1, np.uint8)
+        t = server.submit(ids[gi], r, buf)
+        server.wait(t)
+        res.append(buf)
+    return res
+
+
+def run_mixed(server, ids, resident, queries, seed):
+    bufs = [np.empty(len(resident[gi][0]) - 1, np.uint8) for gi, _ in queries]
+    tickets = [None] * len(queries)
+    rng = random.Random(seed)
+
+    def producer():
+        for i, (gi, r) in enumerate(queries):
+            tickets[i] = server.submit(ids[gi], r, bufs[i])
+            if rng.random() < 0.3:
+                time.sleep(rng.random() * 0.002)  # arrivals while others run
+
+    th = threading.Thread(target=producer)
+    th.start()
+    th.join()
+    server.drain()
+    for t in tickets:
+        assert server.poll(t)
+    return bufs, tickets
+
+
+def test_alone_and_mixed_results_are_identical(resident):
+    queries = make_queries(resident, 160, 1)
+    with gb.Server() as s:
+        ids = [s.add_graph(g) for _, _, g in resident]
+        alone = run_alone(s, ids, resident, queries[:40])
+        mixed, tickets = run_mixed(s, ids, resident, queries, 2)
+        for i in range(40):
+            np.testing.assert_array_equal(alone[i], mixed[i], err_msg=f"query {i}")
+        for i, (gi, r) in enumerate(queries):
+            ro, col, _ = resident[gi]
+            ref = oracle.bfs_batch(ro, col, np.array([r], np.int32))[0]
+            np.testing.assert_array_equal(mixed[i], ref, err_msg=f"query {i} graph {gi}")
+        for t in tickets:
+            t0, t1 = s.times(t)
+            assert t1 >= t0 > 0
+
+
+def test_tight_budget_admits_one_workspace_at_a_time(resident):
+    # room for the largest workspace only: graphs take turns
+    queries = make_queries(resident, 60, 3)
+    budget = 130 * (1 << 16) + 40 * (1 << 20)
+    with gb.Server(budget) as s:
+        ids = [s.add_graph(g) for _, _, g in resident]
+        mixed, _ = run_mixed(s, ids, resident, queries, 4)
+    for i, (gi, r) in enumerate(queries):
+        ro, col, _ = resident[gi]
+        np.testing.assert_array_equal(mixed[i], oracle.bfs_batch(ro, col, np.array([r], np.int32))[0])
+
+
+def test_submit_errors(resident):
+    with gb.Server(1 << 20) as s:  # 1 MiB: no workspace fits
+        gid = s.add_graph(resident[2][2])
+        buf = np.empty(len(resident[2][0]) - 1, np.uint8)
+        with pytest.raises(gb.BfsError) as ei:
+            s.submit(gid, 0, buf)
+        assert ei.value.status == gb.BFS_ERR_BUSY
+        with pytest.raises(gb.BfsError):
+            s.submit(gid + 5, 0, buf)
+        with pytest.raises(gb.BfsError):
+            gb.bfs_poll(s.handle, 12345)
