@@ -103,7 +103,7 @@ def test_alone_and_mixed_results_are_identical(resident):
 def test_tight_budget_admits_one_workspace_at_a_time(resident):
     # room for the largest workspace only: graphs take turns
     queries = make_queries(resident, 60, 3)
-    budget = 130 * (1 << 16) + 40 * (1 << 20)
+    budget = 14 << 20  # the scale-16 workspace (~13.7 MB) fits only alone
     with gb.Server(budget) as s:
         ids = [s.add_graph(g) for _, _, g in resident]
         mixed, _ = run_mixed(s, ids, resident, queries, 4)
