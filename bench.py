@@ -56,6 +56,10 @@ def parse_args(argv=None):
                     help="skip the batched (bit-parallel multi-source) measurement")
     ap.add_argument("--batched-scale", type=int, default=20)
     ap.add_argument("--batched-sources", type=int, default=1024)
+    ap.add_argument("--no-serving", action="store_true",
+                    help="skip the serving-loop measurement")
+    ap.add_argument("--serving-requests", type=int, default=100000)
+    ap.add_argument("--serving-scales", default="12,14,15,17,18,20,21,23")
     ap.add_argument("--profile-layers", action="store_true",
                     help="print the per-layer counters and device times of one search to stderr")
     return ap.parse_args(argv)
@@ -285,6 +289,115 @@ def batched_measurement(args, gb, torch, dev):
                    "plain = CUDA events around back-to-back bfs_run (levels only) on one stream"}
 
 
+def serving_measurement(args, gb, torch, dev):
+    """Eight resident Kronecker graphs (scales 12..23; edgefactor 16 from
+    scale 16, 8 below), requests choosing a graph with probability
+    proportional to 1/scale and a uniform source of degree >= 1, Poisson
+    arrivals.  Saturated throughput first (all requests at once), then rate
+    points at 0.5/0.7/0.9 of it; latency = completion - submission, from the
+    library's own ticket times.  Plain path: bfs_run one query at a time."""
+    import graphgen
+    scales = [int(x) for x in args.serving_scales.split(",")]
+    graphs, roots = [], []
+    for s_ in scales:
+        ro, col = graphgen.kronecker(s_, 16 if s_ >= 16 else 8, args.seed + s_)
+        graphs.append((len(ro) - 1, gb.Graph(ro, col)))
+        roots.append(graphgen.pick_roots(ro, 4096, args.seed + 100 + s_, distinct=False))
+    w = np.array([1.0 / s_ for s_ in scales])
+    w /= w.sum()
+    rng = np.random.default_rng(args.seed + 9)
+
+    def draw(k):
+        gi = rng.choice(len(scales), size=k, p=w)
+        return [(int(g_), int(roots[g_][rng.integers(0, len(roots[g_]))])) for g_ in gi]
+
+    pools = [[] for _ in scales]
+
+    def buf(gi):
+        if pools[gi]:
+            return pools[gi].pop()
+        return torch.empty(graphs[gi][0], dtype=torch.uint8).pin_memory().numpy()
+
+    server = gb.Server()
+    ids = [server.add_graph(g) for _, g in graphs]
+
+    def run(reqs, rate):
+        """Submit reqs at Poisson times (rate None = all at once); returns
+        (elapsed_s, latencies_s)."""
+        gaps = rng.exponential(1.0 / rate, size=len(reqs)) if rate else np.zeros(len(reqs))
+        inflight = []
+        tickets = []
+        t0 = time.perf_counter()
+        t_next = t0
+        for (gi, r), gap in zip(reqs, gaps):
+            t_next += gap
+            while True:
+                now = time.perf_counter()
+                if now >= t_next:
+                    break
+                # recycle finished buffers while waiting for the next arrival
+                keep = []
+                for t, g_, b in inflight:
+                    if server.poll(t):
+                        pools[g_].append(b)
+                    else:
+                        keep.append((t, g_, b))
+                inflight = keep
+            b = buf(gi)
+            t = server.submit(ids[gi], r, b)
+            tickets.append(t)
+            inflight.append((t, gi, b))
+        server.drain()
+        elapsed = time.perf_counter() - t0
+        for t, g_, b in inflight:
+            pools[g_].append(b)
+        server._keep.clear()
+        lat = []
+        for t in tickets:
+            a, b2 = server.times(t)
+            lat.append((b2 - a) * 1e-9)
+        return elapsed, np.array(lat)
+
+    run(draw(2000), None)  # warm-up: workspaces, kernels
+    n_sat = min(20000, args.serving_requests)
+    el, lat = run(draw(n_sat), None)
+    sat = n_sat / el
+    points = []
+    for frac in (0.5, 0.7, 0.9):
+        k = args.serving_requests if frac == 0.7 else max(1000, args.serving_requests // 5)
+        el, lat = run(draw(k), frac * sat)
+        points.append({"rate_fraction_of_saturation": frac, "offered_qps": frac * sat, "requests": k,
+                       "queries_per_s": k / el, "p50_ms": float(np.percentile(lat, 50) * 1e3),
+                       "p99_ms": float(np.percentile(lat, 99) * 1e3)})
+    server.close()
+    # plain path: bfs_run one query at a time (levels to pinned host memory)
+    plain_reqs = draw(2000)
+    outs = {}
+    for gi, (n_, g) in enumerate(graphs):
+        outs[gi] = torch.empty(n_, dtype=torch.int32).pin_memory()
+    stream = torch.cuda.current_stream(dev)
+    plat = []
+    t0 = time.perf_counter()
+    for gi, r in plain_reqs:
+        a = time.perf_counter()
+        gb.bfs_run(graphs[gi][1].handle, r, outs[gi], None, stream)
+        stream.synchronize()
+        plat.append(time.perf_counter() - a)
+    plain_el = time.perf_counter() - t0
+    for _, g in graphs:
+        g.close()
+    head = points[1]
+    return {"workload": "kronecker_scales_" + "_".join(map(str, scales)) + "_poisson",
+            "requests": head["requests"], "saturated_queries_per_s": sat,
+            "queries_per_s": head["queries_per_s"], "p50_ms": head["p50_ms"], "p99_ms": head["p99_ms"],
+            "offered_qps": head["offered_qps"], "sweep": points,
+            "plain_queries_per_s": len(plain_reqs) / plain_el,
+            "plain_p50_ms": float(np.percentile(plat, 50) * 1e3), "plain_p99_ms": float(np.percentile(plat, 99) * 1e3),
+            "how": "bfs_submit/bfs_poll (64-lane continuous batching, uint8 levels to pinned host buffers); "
+                   "latency from the library's ticket times; plain = bfs_run + sync per query, "
+                   "int32 levels to pinned host memory, back to back"}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -409,6 +522,9 @@ def run_ours(args):
     batched = None
     if not args.no_batched and rank == 0:
         batched = batched_measurement(args, gb, torch, dev)
+    serving = None
+    if not args.no_serving and rank == 0:
+        serving = serving_measurement(args, gb, torch, dev)
     if rank == 0:
         cpu = None
         if not args.no_cpu_baseline:
@@ -433,6 +549,7 @@ def run_ours(args):
             "cpu_baseline": cpu,
             "e2e": e2e,
             "batched": batched,
+            "serving": serving,
             "gpu_launches": len(runs),
             "clocks": clocks.summary(),
             "wall_s_timed": wall,
