@@ -324,25 +324,23 @@ def serving_measurement(args, gb, torch, dev):
     def run(reqs, rate):
         """Submit reqs at Poisson times (rate None = all at once); returns
         (elapsed_s, latencies_s)."""
+        import collections
         gaps = rng.exponential(1.0 / rate, size=len(reqs)) if rate else np.zeros(len(reqs))
-        inflight = []
+        inflight = collections.deque()
         tickets = []
         t0 = time.perf_counter()
         t_next = t0
         for (gi, r), gap in zip(reqs, gaps):
             t_next += gap
-            while True:
-                now = time.perf_counter()
-                if now >= t_next:
+            # recycle finished buffers (oldest first, a few per arrival)
+            for _ in range(4):
+                if inflight and server.poll(inflight[0][0]):
+                    t, g_, b = inflight.popleft()
+                    pools[g_].append(b)
+                else:
                     break
-                # recycle finished buffers while waiting for the next arrival
-                keep = []
-                for t, g_, b in inflight:
-                    if server.poll(t):
-                        pools[g_].append(b)
-                    else:
-                        keep.append((t, g_, b))
-                inflight = keep
+            while time.perf_counter() < t_next:
+                pass
             b = buf(gi)
             t = server.submit(ids[gi], r, b)
             tickets.append(t)
