@@ -1,8 +1,8 @@
 // server.cu -- continuous-batching BFS request loop over resident graphs.
 //
 // Not in the paper.  Queries (graph, root) are served by the bit-parallel
-// search of msbfs.cu.  Each graph with work owns a 64-lane workspace; a
-// worker thread repeats, for every such graph:
+// search of msbfs.cu.  Each graph with work owns a 64-lane workspace and a
+// worker thread with its own CUDA stream, which repeats:
 //   1. put waiting queries into free lanes of the running search (a lane
 //      that joins at iteration t reports levels iter + 1 - t);
 //   2. advance the search a few iterations (one cooperative launch on the
@@ -50,13 +50,14 @@ struct Request {
 
 struct GraphState {
     Graph *g = nullptr;
-    std::deque<uint64_t> waiting;     // tickets
+    std::deque<uint64_t> waiting;     // tickets (under Server::mu)
     uint64_t lane_ticket[64] = {};
-    unsigned long long running = 0;   // occupied lanes
-    bool has_ws = false;
+    unsigned long long running = 0;   // occupied lanes (under Server::mu)
+    bool has_ws = false;              // (under Server::mu)
     int64_t ws_bytes = 0;
     uint8_t *d_stage = nullptr;       // [64][n] extraction rows
-    bool launched = false;
+    std::thread worker;
+    std::condition_variable cv;
 };
 
 // Device bytes of one graph's serving workspace (msbfs workspace + rows).
@@ -76,24 +77,26 @@ struct Server {
     std::vector<std::unique_ptr<GraphState>> graphs;
     std::vector<std::unique_ptr<Request>> reqs;  // ticket = index + 1
     std::mutex mu;
-    std::condition_variable cv, done_cv;
+    std::condition_variable done_cv;
     bool stop = false;
     int64_t outstanding = 0;
-    std::thread worker;
     int error = BFS_OK;
 
-    void run();
-    int service(GraphState &gs);
+    void run(GraphState &gs);
+    int round(GraphState &gs);
     int finish(GraphState &gs, unsigned long long mask);
-    bool ensure_ws(GraphState &gs);
+    bool ensure_ws(GraphState &gs);  // with mu held
+    void fail_all(int rc);
 };
 
+// With mu held.  Makes room by dropping the workspaces of graphs that have
+// nothing running or waiting (their workers are idle and their streams are
+// drained).
 bool Server::ensure_ws(GraphState &gs)
 {
     if (gs.has_ws) return true;
     const int64_t need = workspace_bytes(gs.g);
     if (used + need > budget) {
-        // evict idle workspaces until it fits
         for (auto &o : graphs) {
             if (used + need <= budget) break;
             if (o.get() != &gs && o->has_ws && o->running == 0 && o->waiting.empty()) {
@@ -130,8 +133,12 @@ int Server::finish(GraphState &gs, unsigned long long mask)
     MsWs *w = reinterpret_cast<MsWs *>(gs.g->batch_ws);
     for (int i = 0; i < 64; ++i) {
         if (!((mask >> i) & 1ull)) continue;
-        Request &r = *reqs[gs.lane_ticket[i] - 1];
-        cudaError_t e = cudaMemcpyAsync(r.out, gs.d_stage + (size_t)i * gs.g->n, (size_t)gs.g->n,
+        uint8_t *out;
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            out = reqs[gs.lane_ticket[i] - 1]->out;
+        }
+        cudaError_t e = cudaMemcpyAsync(out, gs.d_stage + (size_t)i * gs.g->n, (size_t)gs.g->n,
                                         cudaMemcpyDeviceToHost, w->stream);
         if (e != cudaSuccess) return cuda_error(e, "server: result copy");
     }
@@ -152,16 +159,16 @@ int Server::finish(GraphState &gs, unsigned long long mask)
     return BFS_OK;
 }
 
-// Inject waiting queries into free lanes and launch a few iterations.
-int Server::service(GraphState &gs)
+// One round for one graph: waiting queries into free lanes, a few
+// iterations, finished lanes out.
+int Server::round(GraphState &gs)
 {
-    gs.launched = false;
-    unsigned long long add = 0;
+    unsigned long long add = 0, running;
     int32_t src[64] = {0};
+    int active = 1;
     {
         std::lock_guard<std::mutex> lk(mu);
-        if (gs.waiting.empty() && gs.running == 0) return BFS_OK;
-        if (!ensure_ws(gs)) return BFS_OK;  // no room yet: the queries wait
+        if (!ensure_ws(gs)) return BFS_NOT_READY;  // no room yet: the queries wait
         while (!gs.waiting.empty() && (gs.running | add) != ~0ull) {
             const int lane = __builtin_ctzll(~(gs.running | add));
             const uint64_t t = gs.waiting.front();
@@ -170,68 +177,63 @@ int Server::service(GraphState &gs)
             src[lane] = reqs[t - 1]->root;
             add |= 1ull << lane;
         }
+        gs.running |= add;
+        running = gs.running;
+        active = 0;
+        for (auto &o : graphs)
+            if (o->running) ++active;
     }
     if (add) {
         const int rc = ms_inject(gs.g, src, add);
         if (rc != BFS_OK) return rc;
-        gs.running |= add;
     }
-    if (gs.running == 0) return BFS_OK;
-    int active = 0;
-    for (auto &o : graphs)
-        if (o->running) ++active;
+    if (!running) return BFS_OK;
     const int share = std::max(gs.g->num_sms, total_ctas / std::max(1, active));
-    const int rc = ms_step_capped(gs.g, iters_per_step, share);
+    int rc = ms_step_capped(gs.g, iters_per_step, share);
     if (rc != BFS_OK) return rc;
-    gs.launched = true;
-    return BFS_OK;
+    MsCtrl st;
+    rc = ms_read_ctrl(gs.g, &st);
+    if (rc != BFS_OK) return rc;
+    if (st.status & (ST_TIMEOUT | ST_OVERFLOW | ST_DEPTH))
+        return set_error(st.status & ST_DEPTH ? BFS_ERR_DEPTH : (st.status & ST_TIMEOUT ? BFS_ERR_TIMEOUT : BFS_ERR_CUDA),
+                         "server: device-side error in a batched search");
+    return finish(gs, running & ~st.alive[st.iter & 1]);
 }
 
-void Server::run()
+void Server::fail_all(int rc)
+{
+    std::lock_guard<std::mutex> lk(mu);
+    if (error == BFS_OK) error = rc;
+    for (auto &r : reqs)
+        if (r->status.load() == BFS_NOT_READY) {
+            r->status.store(rc);
+            r->t_done = now_ns();
+        }
+    for (auto &gs : graphs) {
+        gs->waiting.clear();
+        gs->running = 0;
+    }
+    outstanding = 0;
+    done_cv.notify_all();
+    for (auto &gs : graphs) gs->cv.notify_all();
+}
+
+void Server::run(GraphState &gs)
 {
     cudaSetDevice(device);
     while (true) {
         {
             std::unique_lock<std::mutex> lk(mu);
-            cv.wait(lk, [&] {
-                if (stop) return true;
-                for (auto &gs : graphs)
-                    if (!gs->waiting.empty() || gs->running) return true;
-                return false;
-            });
-            if (stop) break;
+            gs.cv.wait(lk, [&] { return stop || error != BFS_OK || !gs.waiting.empty() || gs.running; });
+            if (stop || error != BFS_OK) break;
         }
-        int rc = BFS_OK;
-        for (auto &gs : graphs)
-            if (rc == BFS_OK) rc = service(*gs);
-        for (auto &gs : graphs) {
-            if (rc != BFS_OK || !gs->launched) continue;
-            MsCtrl st;
-            rc = ms_read_ctrl(gs->g, &st);
-            if (rc != BFS_OK) break;
-            if (st.status & (ST_TIMEOUT | ST_OVERFLOW | ST_DEPTH)) {
-                rc = set_error(st.status & ST_DEPTH ? BFS_ERR_DEPTH : (st.status & ST_TIMEOUT ? BFS_ERR_TIMEOUT : BFS_ERR_CUDA),
-                               "server: device-side error in a batched search");
-                break;
-            }
-            const unsigned long long alive = st.alive[st.iter & 1];
-            rc = finish(*gs, gs->running & ~alive);
+        const int rc = round(gs);
+        if (rc == BFS_NOT_READY) {  // waiting for HBM budget
+            std::this_thread::sleep_for(std::chrono::microseconds(200));
+            continue;
         }
         if (rc != BFS_OK) {
-            // fail every outstanding query rather than hang the callers
-            std::lock_guard<std::mutex> lk(mu);
-            error = rc;
-            for (auto &r : reqs)
-                if (r->status.load() == BFS_NOT_READY) {
-                    r->status.store(rc);
-                    r->t_done = now_ns();
-                }
-            for (auto &gs : graphs) {
-                gs->waiting.clear();
-                gs->running = 0;
-            }
-            outstanding = 0;
-            done_cv.notify_all();
+            fail_all(rc);
             break;
         }
     }
@@ -262,7 +264,6 @@ bfs_server *bfs_server_create(int64_t hbm_budget_bytes)
     size_t free_b = 0, total_b = 0;
     cudaMemGetInfo(&free_b, &total_b);
     s->budget = hbm_budget_bytes > 0 ? hbm_budget_bytes : (int64_t)(0.8 * (double)free_b);
-    s->worker = std::thread([s] { s->run(); });
     return reinterpret_cast<bfs_server *>(s);
 }
 
@@ -273,9 +274,10 @@ int bfs_server_destroy(bfs_server *sh)
     {
         std::lock_guard<std::mutex> lk(s->mu);
         s->stop = true;
+        for (auto &gs : s->graphs) gs->cv.notify_all();
     }
-    s->cv.notify_all();
-    if (s->worker.joinable()) s->worker.join();
+    for (auto &gs : s->graphs)
+        if (gs->worker.joinable()) gs->worker.join();
     for (auto &gs : s->graphs) {
         if (gs->has_ws) {
             ms_free(gs->g);
@@ -302,7 +304,9 @@ int bfs_server_add_graph(bfs_server *sh, bfs_graph *gh)
     }
     auto gs = std::make_unique<GraphState>();
     gs->g = g;
+    GraphState *raw = gs.get();
     s->graphs.push_back(std::move(gs));
+    raw->worker = std::thread([s, raw] { s->run(*raw); });
     return (int)s->graphs.size() - 1;
 }
 
@@ -328,7 +332,7 @@ int bfs_submit(bfs_server *sh, int graph_id, int32_t root, uint8_t *level_out, u
     gs.waiting.push_back(t);
     ++s->outstanding;
     *ticket = t;
-    s->cv.notify_one();
+    gs.cv.notify_one();
     return BFS_OK;
 }
 
