@@ -76,6 +76,8 @@ struct Graph {
     int32_t *d_col_idx = nullptr;  // padded: m rounded up to 4, plus 4 entries
     int32_t *d_perm = nullptr;     // caller id -> internal id
     int32_t *d_orig = nullptr;     // internal id -> caller id
+    int64_t split32 = 0;           // internal ids [0, split32) have degree >= 32
+    bool symmetric = false;        // every (u, v) has (v, u): in-edges = out-edges
 
     // single-source workspace
     uint32_t *d_bitmap = nullptr;  // words rounded up to a multiple of 4

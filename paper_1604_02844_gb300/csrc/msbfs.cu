@@ -25,6 +25,13 @@
 // (one 64-byte line per vertex), 0xFF = unreached, and transposed into the
 // caller's source-major [k][n] output when lanes finish.
 //
+// Heavy iterations run as pull steps on symmetric graphs (checked exactly at
+// graph creation): every vertex v with a lane still missing ORs the
+// frontier words of its neighbours (in-neighbours = out-neighbours), with an
+// early exit once every missing live lane is found; no atomics, no touched
+// list.  An iteration is a pull step when the frontier's adjacency exceeds
+// m/16 entries.
+//
 // All iterations of a launch run in one persistent cooperative kernel with
 // two bounded grid barriers per iteration.
 #include <cuda_runtime.h>
@@ -56,6 +63,9 @@ struct MsParams {
     const int32_t *start;  // [64] start iteration per lane
     MsCtrl *ctrl;
     int32_t n;
+    int32_t split32;    // internal ids below have degree >= 32
+    int symmetric;
+    int64_t m;
     uint32_t fcap;
     uint32_t max_iters;
     uint64_t timeout_ns;
@@ -75,8 +85,14 @@ __device__ __forceinline__ void append_frontier(const MsParams &p, int q, bool w
     }
     const int total = __shfl_sync(FULL, inc, 31);
     if (total == 0) return;
+    unsigned long long edges = want ? (unsigned long long)len : 0ull;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) edges += __shfl_xor_sync(FULL, edges, o);
     unsigned base = 0;
-    if (lane == 31) base = atomicAdd(&p.ctrl->fcount[q], (unsigned)total);
+    if (lane == 31) {
+        base = atomicAdd(&p.ctrl->fcount[q], (unsigned)total);
+        atomicAdd(&p.ctrl->fedges[q], edges);
+    }
     base = __shfl_sync(FULL, base, 31);
     unsigned pos = base + (unsigned)(inc - ns);
     for (int s = 0; s < ns; ++s, ++pos) {
@@ -260,8 +276,16 @@ __device__ __forceinline__ void ms_update(const MsParams &p, int par, unsigned n
         }
         const int total = __shfl_sync(FULL, inc, 31);
         if (total == 0) continue;
+        unsigned long long edges = 0;
+#pragma unroll
+        for (int k = 0; k < UU; ++k) edges += (nn[k] && len[k] > 0) ? (unsigned long long)len[k] : 0ull;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) edges += __shfl_xor_sync(FULL, edges, o);
         unsigned base = 0;
-        if (lane == 31) base = atomicAdd(&c->fcount[q], (unsigned)total);
+        if (lane == 31) {
+            base = atomicAdd(&c->fcount[q], (unsigned)total);
+            atomicAdd(&c->fedges[q], edges);
+        }
         base = __shfl_sync(FULL, base, 31);
         unsigned pos = base + (unsigned)(inc - ns);
 #pragma unroll
@@ -277,6 +301,76 @@ __device__ __forceinline__ void ms_update(const MsParams &p, int par, unsigned n
                 }
             }
         }
+    }
+}
+
+__device__ __forceinline__ unsigned long long warp_or64(unsigned long long x)
+{
+    const unsigned lo = __reduce_or_sync(FULL, (unsigned)(x & 0xffffffffull));
+    const unsigned hi = __reduce_or_sync(FULL, (unsigned)(x >> 32));
+    return ((unsigned long long)hi << 32) | lo;
+}
+
+// Pull step: vertices of degree >= 32 one per warp, the rest one per lane.
+// A vertex v is new for lanes (OR of front[par][u] over neighbours u) &
+// ~seen[v]; the scan of Adj[v] stops once every live lane missing at v is
+// found.  Writes seen, front[q], levels and the next frontier list.
+__device__ __forceinline__ void ms_pull(const MsParams &p, int par, unsigned long long live, unsigned long long &alive,
+                                        const uint32_t *s_lv, unsigned long long over)
+{
+    const int lane = threadIdx.x & 31;
+    const int q = par ^ 1;
+    MsCtrl *c = p.ctrl;
+    const unsigned gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const unsigned GW = (gridDim.x * blockDim.x) >> 5;
+    // high degree: a warp per vertex
+    for (int v = (int)gw; v < p.split32; v += (int)GW) {
+        const unsigned long long need = live & ~__ldcg(p.seen + v);
+        if (!need) continue;
+        const int b = __ldg(p.ro + v), e = __ldg(p.ro + v + 1);
+        unsigned long long acc = 0;
+        for (int k0 = b; k0 < e; k0 += 32) {
+            const int k = k0 + lane;
+            if (k < e) acc |= __ldcg(p.front[par] + __ldg(p.col + k));
+            if ((warp_or64(acc) & need) == need) break;
+        }
+        const unsigned long long nn = warp_or64(acc) & need;
+        if (nn && lane == 0) {
+            p.seen[v] = __ldcg(p.seen + v) | nn;
+            p.front[q][v] = nn;
+            alive |= nn;
+            if (nn & over) atomicOr(&c->status, ST_DEPTH);
+            merge_levels(reinterpret_cast<uint4 *>(p.lvl + (size_t)__ldg(p.orig + v) * 64), nn, s_lv);
+        }
+        append_frontier(p, q, nn != 0ull && lane == 0, v, b, e - b);
+    }
+    // low degree: a lane per vertex (warp-uniform loop)
+    for (int v0 = p.split32 + (int)gw * 32; v0 < p.n; v0 += (int)GW * 32) {
+        const int v = v0 + lane;
+        unsigned long long nn = 0;
+        int b = 0, e = 0;
+        if (v < p.n) {
+            const unsigned long long sn = __ldcg(p.seen + v);
+            const unsigned long long need = live & ~sn;
+            if (need) {
+                b = __ldg(p.ro + v);
+                e = __ldg(p.ro + v + 1);
+                unsigned long long acc = 0;
+                for (int k = b; k < e; ++k) {
+                    acc |= __ldcg(p.front[par] + __ldg(p.col + k));
+                    if ((acc & need) == need) break;
+                }
+                nn = acc & need;
+                if (nn) {
+                    p.seen[v] = sn | nn;
+                    p.front[q][v] = nn;
+                    alive |= nn;
+                    if (nn & over) atomicOr(&c->status, ST_DEPTH);
+                    merge_levels(reinterpret_cast<uint4 *>(p.lvl + (size_t)__ldg(p.orig + v) * 64), nn, s_lv);
+                }
+            }
+        }
+        append_frontier(p, q, nn != 0ull && e > b, v, b, e - b);
     }
 }
 
@@ -310,13 +404,17 @@ __global__ void __launch_bounds__(MS_WPB * 32) ms_kernel(MsParams p)
             // parity par^1: last read before the previous barrier, next used
             // after the coming one
             c->fcount[par ^ 1] = 0;
+            c->fedges[par ^ 1] = 0ull;
             c->work[par ^ 1] = 0;
             c->tcount[par ^ 1] = 0;
             c->alive[par ^ 1] = 0ull;
         }
-        ms_expand(p, par, nF, s_tbuf[threadIdx.x >> 5]);
-        ok = grid_sync(&c->bar_count, &c->bar_gen, &c->status, G, p.timeout_ns, &s_ok);
-        if (!ok) break;
+        const bool pull = p.symmetric && (long long)ld_relaxed64(&c->fedges[par]) * 16 > p.m;
+        if (!pull) {
+            ms_expand(p, par, nF, s_tbuf[threadIdx.x >> 5]);
+            ok = grid_sync(&c->bar_count, &c->bar_gen, &c->status, G, p.timeout_ns, &s_ok);
+            if (!ok) break;
+        }
         // this iteration's level byte per lane, packed four to a word
         if (tid < 16) {
             uint32_t w = 0;
@@ -331,7 +429,17 @@ __global__ void __launch_bounds__(MS_WPB * 32) ms_kernel(MsParams p)
         if (tid < 64 && (int)iter + 1 - __ldg(p.start + tid) > 254) atomicOr(&s_over, 1ull << tid);
         __syncthreads();
         unsigned long long alive = 0;
-        ms_update(p, par, nF, iter, alive, s_lv, s_over);
+        if (pull) {
+            ms_pull(p, par, ld_relaxed64(&c->alive[par]), alive, s_lv, s_over);
+            ok = grid_sync(&c->bar_count, &c->bar_gen, &c->status, G, p.timeout_ns, &s_ok);
+            if (!ok) break;
+            // the old frontier words, once every pull has read them
+            for (unsigned i = blockIdx.x * blockDim.x + tid; i < nF; i += G * blockDim.x)
+                p.front[par][__ldcg(p.fu[par] + i)] = 0ull;
+            if (blockIdx.x == 0 && tid == 0) c->pulls += 1;
+        } else {
+            ms_update(p, par, nF, iter, alive, s_lv, s_over);
+        }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) alive |= __shfl_xor_sync(FULL, alive, o);
         if (lane == 0 && alive) atomicOr(&s_alive, alive);
@@ -537,6 +645,9 @@ static MsParams make_params(Graph *g, MsWs *w, uint32_t max_iters)
     p.start = w->start;
     p.ctrl = w->ctrl;
     p.n = (int32_t)g->n;
+    p.split32 = (int32_t)g->split32;
+    p.symmetric = g->symmetric ? 1 : 0;
+    p.m = g->m;
     p.fcap = (uint32_t)std::min<int64_t>(w->fcap, 0x7FFFFFFFLL);
     p.max_iters = max_iters;
     p.timeout_ns = (uint64_t)g->opt.timeout_ns;

@@ -13,6 +13,8 @@ namespace gbbfs {
 // iter (p = iter & 1) and cleared during the iteration of the other parity.
 struct MsCtrl {
     unsigned fcount[2];           // frontier entries in buffer p
+    unsigned long long fedges[2]; // adjacency entries of frontier buffer p
+    unsigned pulls;               // iterations run as pull steps (diagnostic)
     unsigned work[2];             // EXPAND dispenser
     unsigned tcount[2];           // touched vertices
     unsigned bar_count, bar_gen, exit_count;

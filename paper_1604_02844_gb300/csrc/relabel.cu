@@ -172,6 +172,33 @@ __global__ void copy_rows_kernel(const int32_t *__restrict__ ro, const int32_t *
     }
 }
 
+// flags bit 0: some row is not sorted; bit 1: some edge (u, v) has no (v, u).
+// One warp per row u; the reverse edge is found by binary search in the
+// sorted row of v (only meaningful when no row is unsorted).
+__global__ void symmetry_kernel(const int32_t *__restrict__ ro, const int32_t *__restrict__ col, int64_t n,
+                                unsigned *flags)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x / 32);
+    unsigned f = 0;
+    for (int64_t u = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); u < n; u += nwarps) {
+        const int32_t b = ro[u], e = ro[u + 1];
+        for (int32_t k = b + lane; k < e; k += 32) {
+            const int32_t v = col[k];
+            if (k > b && col[k - 1] > v) f |= 1u;
+            int32_t lo = ro[v], hi = ro[v + 1];  // find u in Adj[v]
+            while (lo < hi) {
+                const int32_t mid = (lo + hi) >> 1;
+                if (col[mid] < u) lo = mid + 1;
+                else hi = mid;
+            }
+            if (lo >= ro[v + 1] || col[lo] != u) f |= 2u;
+        }
+    }
+    f = __reduce_or_sync(0xffffffffu, f);
+    if (f && lane == 0) atomicOr(flags, f);
+}
+
 __global__ void bitmap_to_caller_kernel(const uint32_t *__restrict__ bm, const int32_t *__restrict__ orig, int64_t n,
                                         uint32_t *out)
 {
@@ -213,6 +240,22 @@ int relabel_graph(Graph *g, const int32_t *d_ro, const int32_t *d_col)
     tile_add_kernel<<<(unsigned)ntile, 256>>>(g->d_row_offsets, n, tsum, m);
     copy_rows_kernel<<<g->num_sms * 16, 256>>>(d_ro, d_col, g->d_orig, g->d_perm, g->d_row_offsets, n, g->d_col_idx);
     if ((e = cudaMemset(g->d_col_idx + m, 0, (size_t)(col_alloc - m) * 4)) != cudaSuccess) { rc = cuda_error(e, "cudaMemset(col tail)"); goto done; }
+    // vertices of degree >= 32 (classes 0..26) come first: their count is
+    // the exclusive offset of class 27, block 0
+    {
+        int32_t split = 0;
+        if ((e = cudaMemcpy(&split, hist + (int64_t)27 * nblk, 4, cudaMemcpyDeviceToHost)) != cudaSuccess) { rc = cuda_error(e, "cudaMemcpy(split)"); goto done; }
+        g->split32 = split;
+    }
+    // exact symmetry test on the caller's CSR (sorted rows + reverse edges)
+    {
+        unsigned *d_flags = reinterpret_cast<unsigned *>(tsum);  // scratch: tile sums are consumed
+        if ((e = cudaMemset(d_flags, 0, 4)) != cudaSuccess) { rc = cuda_error(e, "cudaMemset(symmetry)"); goto done; }
+        symmetry_kernel<<<g->num_sms * 16, 256>>>(d_ro, d_col, n, d_flags);
+        unsigned flags = 0;
+        if ((e = cudaMemcpy(&flags, d_flags, 4, cudaMemcpyDeviceToHost)) != cudaSuccess) { rc = cuda_error(e, "symmetry_kernel"); goto done; }
+        g->symmetric = (flags == 0);
+    }
     if ((e = cudaDeviceSynchronize()) != cudaSuccess) { rc = cuda_error(e, "relabel kernels"); goto done; }
 done:
     cudaFree(cls);

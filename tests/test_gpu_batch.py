@@ -145,3 +145,20 @@ def test_uneven_mix_of_six_graphs():
     finally:
         for g in graphs:
             g.close()
+
+
+def test_pull_steps_and_push_steps_agree():
+    """A symmetric graph with sorted rows takes pull steps in its heavy
+    iterations; the same graph with every row reversed fails the exact
+    symmetry test at creation and stays with push steps.  Both must match
+    the oracle."""
+    ro, col = graphgen.kronecker(15, 16, 34)
+    col_rev = col.copy()
+    for u in range(len(ro) - 1):
+        col_rev[ro[u]:ro[u + 1]] = col[ro[u]:ro[u + 1]][::-1]
+    roots = graphgen.pick_roots(ro, 64, 34)
+    ref = oracle.bfs_batch(ro, col, roots)
+    with gb.Graph(ro, col) as g:
+        np.testing.assert_array_equal(batch_levels(g, roots), ref)
+    with gb.Graph(ro, col_rev) as g:
+        np.testing.assert_array_equal(batch_levels(g, roots), ref)
