@@ -77,6 +77,7 @@ struct Graph {
     int32_t *d_perm = nullptr;     // caller id -> internal id
     int32_t *d_orig = nullptr;     // internal id -> caller id
     int64_t split32 = 0;           // internal ids [0, split32) have degree >= 32
+    int64_t n_nonzero = 0;         // internal ids [0, n_nonzero) have degree >= 1
     bool symmetric = false;        // every (u, v) has (v, u): in-edges = out-edges
 
     // single-source workspace

@@ -30,7 +30,10 @@
 // frontier words of its neighbours (in-neighbours = out-neighbours), with an
 // early exit once every missing live lane is found; no atomics, no touched
 // list.  An iteration is a pull step when the frontier's adjacency exceeds
-// m/16 entries.
+// m/16 entries and at least 30% of the live lanes' (vertex, lane) pairs over
+// vertices of degree >= 1 are already reached -- before that, most vertices
+// miss lanes whose frontier is still far away and would scan their whole
+// adjacency (the multi-lane form of the direction-optimising switch).
 //
 // All iterations of a launch run in one persistent cooperative kernel with
 // two bounded grid barriers per iteration.
@@ -66,6 +69,7 @@ struct MsParams {
     int32_t split32;    // internal ids below have degree >= 32
     int symmetric;
     int64_t m;
+    int64_t n_nonzero;
     uint32_t fcap;
     uint32_t max_iters;
     uint64_t timeout_ns;
@@ -267,6 +271,14 @@ __device__ __forceinline__ void ms_update(const MsParams &p, int par, unsigned n
                 }
             }
         }
+        {
+            unsigned long long pairs = 0;
+#pragma unroll
+            for (int k = 0; k < UU; ++k) pairs += (unsigned long long)__popcll(nn[k]);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) pairs += __shfl_xor_sync(FULL, pairs, o);
+            if (lane == 0 && pairs) atomicAdd(&c->seen_pairs, pairs);
+        }
         // one reservation for the whole warp's slices of this round
         int inc = ns;
 #pragma unroll
@@ -336,6 +348,7 @@ __device__ __forceinline__ void ms_pull(const MsParams &p, int par, unsigned lon
         }
         const unsigned long long nn = warp_or64(acc) & need;
         if (nn && lane == 0) {
+            atomicAdd(&c->seen_pairs, (unsigned long long)__popcll(nn));
             p.seen[v] = __ldcg(p.seen + v) | nn;
             p.front[q][v] = nn;
             alive |= nn;
@@ -370,6 +383,10 @@ __device__ __forceinline__ void ms_pull(const MsParams &p, int par, unsigned lon
                 }
             }
         }
+        unsigned long long pairs = (unsigned long long)__popcll(nn);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) pairs += __shfl_xor_sync(FULL, pairs, o);
+        if (lane == 0 && pairs) atomicAdd(&c->seen_pairs, pairs);
         append_frontier(p, q, nn != 0ull && e > b, v, b, e - b);
     }
 }
@@ -409,7 +426,9 @@ __global__ void __launch_bounds__(MS_WPB * 32) ms_kernel(MsParams p)
             c->tcount[par ^ 1] = 0;
             c->alive[par ^ 1] = 0ull;
         }
-        const bool pull = p.symmetric && (long long)ld_relaxed64(&c->fedges[par]) * 16 > p.m;
+        const unsigned long long live = ld_relaxed64(&c->alive[par]);
+        const bool pull = p.symmetric && (long long)ld_relaxed64(&c->fedges[par]) * 16 > p.m &&
+                          (double)ld_relaxed64(&c->seen_pairs) >= 0.3 * (double)__popcll(live) * (double)p.n_nonzero;
         if (!pull) {
             ms_expand(p, par, nF, s_tbuf[threadIdx.x >> 5]);
             ok = grid_sync(&c->bar_count, &c->bar_gen, &c->status, G, p.timeout_ns, &s_ok);
@@ -477,7 +496,7 @@ __global__ void ms_inject_kernel(MsParams p, const int32_t *__restrict__ lanes_s
     unsigned long long oldf = 0;
     if (lane == 0) {
         start[w] = (int32_t)iter;
-        atomicOr(p.seen + s, bit);
+        if (!(atomicOr(p.seen + s, bit) & bit)) atomicAdd(&c->seen_pairs, 1ull);
         oldf = atomicOr(p.front[par] + s, bit);
         p.lvl[(size_t)__ldg(p.orig + s) * 64 + w] = 0;
         atomicOr(&c->alive[par], bit);
@@ -492,7 +511,7 @@ __global__ void ms_inject_kernel(MsParams p, const int32_t *__restrict__ lanes_s
 // them: level 0xFF, seen bit cleared.  Block: 128 vertices x 64 lanes.
 __global__ void ms_extract_kernel(uint8_t *lvl, unsigned long long *seen, const int32_t *__restrict__ perm, int64_t n,
                                   unsigned long long mask, const int32_t *__restrict__ lane_row, uint8_t *out,
-                                  int64_t out_stride, int recycle)
+                                  int64_t out_stride, int recycle, MsCtrl *ctrl)
 {
     __shared__ uint8_t tile[128][65];
     const int64_t v0 = (int64_t)blockIdx.x * 128;
@@ -529,14 +548,19 @@ __global__ void ms_extract_kernel(uint8_t *lvl, unsigned long long *seen, const 
                 if (v < n) out[(size_t)row * out_stride + v] = tile[r][ln];
             }
     }
-    if (recycle)
+    if (recycle) {
+        unsigned long long cleared = 0;
         for (int r = threadIdx.x; r < 128; r += blockDim.x) {
             const int64_t v = v0 + r;
             if (v < n) {
                 const int w = __ldg(perm + v);  // seen is indexed by internal id
-                atomicAnd(seen + w, ~mask);
+                cleared += (unsigned long long)__popcll(atomicAnd(seen + w, ~mask) & mask);
             }
         }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) cleared += __shfl_xor_sync(0xffffffffu, cleared, o);
+        if ((threadIdx.x & 31) == 0 && cleared) atomicAdd(&ctrl->seen_pairs, 0ull - cleared);
+    }
 }
 
 }  // namespace
@@ -648,6 +672,7 @@ static MsParams make_params(Graph *g, MsWs *w, uint32_t max_iters)
     p.split32 = (int32_t)g->split32;
     p.symmetric = g->symmetric ? 1 : 0;
     p.m = g->m;
+    p.n_nonzero = g->n_nonzero;
     p.fcap = (uint32_t)std::min<int64_t>(w->fcap, 0x7FFFFFFFLL);
     p.max_iters = max_iters;
     p.timeout_ns = (uint64_t)g->opt.timeout_ns;
@@ -717,7 +742,7 @@ int ms_extract(Graph *g, unsigned long long mask, const int32_t *lane_row_host, 
     GB_CUDA(cudaMemcpyAsync(w->lane_row, h, 64 * 4, cudaMemcpyHostToDevice, s));
     const int64_t blocks = (g->n + 127) / 128;
     ms_extract_kernel<<<(unsigned)blocks, 128, 0, s>>>(w->lvl, w->seen, g->d_perm, g->n, mask, w->lane_row, out,
-                                                      out_stride, recycle ? 1 : 0);
+                                                      out_stride, recycle ? 1 : 0, w->ctrl);
     GB_CUDA(cudaGetLastError());
     return BFS_OK;
 }

@@ -15,6 +15,7 @@ struct MsCtrl {
     unsigned fcount[2];           // frontier entries in buffer p
     unsigned long long fedges[2]; // adjacency entries of frontier buffer p
     unsigned pulls;               // iterations run as pull steps (diagnostic)
+    unsigned long long seen_pairs;  // (vertex, lane) pairs set in seen
     unsigned work[2];             // EXPAND dispenser
     unsigned tcount[2];           // touched vertices
     unsigned bar_count, bar_gen, exit_count;

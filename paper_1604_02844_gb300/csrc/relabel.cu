@@ -246,6 +246,9 @@ int relabel_graph(Graph *g, const int32_t *d_ro, const int32_t *d_col)
         int32_t split = 0;
         if ((e = cudaMemcpy(&split, hist + (int64_t)27 * nblk, 4, cudaMemcpyDeviceToHost)) != cudaSuccess) { rc = cuda_error(e, "cudaMemcpy(split)"); goto done; }
         g->split32 = split;
+        int32_t nz = 0;  // vertices of degree >= 1: exclusive offset of class 32
+        if ((e = cudaMemcpy(&nz, hist + (int64_t)32 * nblk, 4, cudaMemcpyDeviceToHost)) != cudaSuccess) { rc = cuda_error(e, "cudaMemcpy(nonzero)"); goto done; }
+        g->n_nonzero = nz;
     }
     // exact symmetry test on the caller's CSR (sorted rows + reverse edges)
     {
