@@ -369,13 +369,8 @@ __device__ __forceinline__ void ms_pull(const MsParams &p, int par, unsigned lon
                 b = __ldg(p.ro + v);
                 e = __ldg(p.ro + v + 1);
                 unsigned long long acc = 0;
-                for (int k = b; k < e; k += 4) {  // four neighbours in flight
-                    int u[4];
-#pragma unroll
-                    for (int x = 0; x < 4; ++x) u[x] = (k + x < e) ? __ldg(p.col + k + x) : -1;
-#pragma unroll
-                    for (int x = 0; x < 4; ++x)
-                        if (u[x] >= 0) acc |= __ldcg(p.front[par] + u[x]);
+                for (int k = b; k < e; ++k) {
+                    acc |= __ldcg(p.front[par] + __ldg(p.col + k));
                     if ((acc & need) == need) break;
                 }
                 nn = acc & need;
