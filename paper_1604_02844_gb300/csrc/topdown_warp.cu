@@ -400,14 +400,11 @@ __device__ __forceinline__ void process_item(WarpSmem &ws, const WParams &p, int
         }
 #pragma unroll
         // Bits are only ever set during a search, so a stale word can only
-        // send an already visited vertex on to the atomicOr.  A hub whose bit
-        // is set in the CTA's snapshot (taken at the layer start) is settled
-        // in shared memory; every other test reads the word through L1, which
-        // also sees the bits set earlier in this layer.
+        // send an already visited vertex on to the atomicOr: hub words come
+        // from the CTA's shared snapshot, the rest through L1.
         for (int k = 0; k < UA; ++k) {
             const int wd = (int)((unsigned)v[k] >> 5);
-            const unsigned bit = 1u << (v[k] & 31);
-            w[k] = (v[k] < 0 || (wd < hot_words && (hot[wd] & bit))) ? 0xffffffffu : __ldca(p.bitmap + wd);
+            w[k] = v[k] < 0 ? 0xffffffffu : (wd < hot_words ? hot[wd] : __ldca(p.bitmap + wd));
         }
         __syncwarp();
 #pragma unroll
