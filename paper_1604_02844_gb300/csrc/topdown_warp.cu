@@ -74,17 +74,8 @@ struct WarpSmem {
     int32_t ust[OBW];                   // flush: unit starts
 };
 
-// Words of the visited bitmap kept in shared memory per CTA: the first
-// HOT_WORDS words cover the highest-degree vertices (internal ids are sorted
-// by degree class), the targets of most adjacency entries.
-template <int WPB>
-struct Hot {
-    static constexpr int WORDS = (WPB >= 16) ? 16384 : 1024;
-};
-
 template <int WPB>
 struct CtaSmem {
-    uint32_t hot[Hot<WPB>::WORDS];  // snapshot of bitmap words [0, hot_words) at the layer start
     WarpSmem w[WPB];
     int ok;
     unsigned nU, nH;
@@ -382,8 +373,7 @@ __device__ __forceinline__ void warp_flush(WarpSmem &ws, const WParams &p, int s
 
 // Passes A and B over the staged item in stage[buf] with `et` edges.
 __device__ __forceinline__ void process_item(WarpSmem &ws, const WParams &p, int buf, int et, int cnt,
-                                             int next_level, int set_out, int qo, int &ocnt, unsigned &my_new,
-                                             const uint32_t *hot, int hot_words)
+                                             int next_level, int set_out, int qo, int &ocnt, unsigned &my_new)
 {
     const int lane = threadIdx.x & 31;
     const unsigned lt = lanemask_lt();
@@ -399,13 +389,9 @@ __device__ __forceinline__ void process_item(WarpSmem &ws, const WParams &p, int
             v[k] = e < et ? stg[e] : -1;
         }
 #pragma unroll
-        // Bits are only ever set during a search, so a stale word can only
-        // send an already visited vertex on to the atomicOr: hub words come
-        // from the CTA's shared snapshot, the rest through L1.
-        for (int k = 0; k < UA; ++k) {
-            const int wd = (int)((unsigned)v[k] >> 5);
-            w[k] = v[k] < 0 ? 0xffffffffu : (wd < hot_words ? hot[wd] : __ldca(p.bitmap + wd));
-        }
+        // L1-cached read: bits are only ever set during a search, so a stale
+        // word can only send an already visited vertex on to the atomicOr
+        for (int k = 0; k < UA; ++k) w[k] = v[k] >= 0 ? __ldca(p.bitmap + ((unsigned)v[k] >> 5)) : 0xffffffffu;
         __syncwarp();
 #pragma unroll
         for (int k = 0; k < UA; ++k) {
@@ -518,12 +504,8 @@ __global__ void __launch_bounds__(WPB * 32, (24 / WPB) > 0 ? (24 / WPB) : 1) td_
     }
     bool ok = grid_sync(&c->bar_count, &c->bar_gen, &c->status, G, p.timeout_ns, &cs.ok);
 
-    const int hot_words = min(Hot<WPB>::WORDS, p.bitmap_words);
     for (int d = 0; ok; ++d) {
         const int set_in = d % 3, set_out = (d + 1) % 3, set_rst = (d + 2) % 3;
-        // snapshot of the hub words as they stand after the last barrier
-        for (int i = tid * 4; i < hot_words; i += WPB * 32 * 4)
-            *reinterpret_cast<uint4 *>(&cs.hot[i]) = __ldcg(reinterpret_cast<const uint4 *>(p.bitmap + i));
         if (tid == 0) {
             const unsigned long long eu = ld_relaxed64(&c->eu_count[set_in]);
             cs.nU = min((unsigned)(eu >> 32), p.ucap);
@@ -574,7 +556,7 @@ __global__ void __launch_bounds__(WPB * 32, (24 / WPB) > 0 ? (24 / WPB) : 1) td_
             asm volatile("cp.async.wait_group 1;" ::: "memory");
             __syncwarp();
             if (lane == 0) my_edges += (unsigned long long)et_cur;
-            process_item(ws, p, buf, et_cur, cnt_cur, next_level, set_out, qo, ocnt, my_new, cs.hot, hot_words);
+            process_item(ws, p, buf, et_cur, cnt_cur, next_level, set_out, qo, ocnt, my_new);
             buf ^= 1;
             id = id1;
             et_cur = et_nxt;
