@@ -158,8 +158,7 @@ int bfs_run(bfs_graph *g, int32_t root, int32_t *level_out, int32_t *parent_out,
  * library until the process exits).  No cudaMalloc, cudaFree or allocating
  * library call is made.
  *   row_offsets, col_idx : the caller's CSR in DEVICE memory (checked as in
- *                          bfs_graph_create; no renumbering is done);
- *                          col_idx must be 16-byte aligned
+ *                          bfs_graph_create; no renumbering is done)
  *   n, m                 : 1 <= n <= BFS_NOALLOC_MAX_VERTICES,
  *                          0 <= m <= BFS_NOALLOC_MAX_EDGES, else
  *                          BFS_ERR_INVALID_ARG

@@ -109,8 +109,6 @@ extern "C" int bfs_run_noalloc(const int32_t *row_offsets, const int32_t *col_id
         (parent_out && !is_device_pointer(parent_out)))
         return set_error(BFS_ERR_INVALID_ARG,
                          "bfs_run_noalloc: row_offsets, col_idx, level_out and parent_out must be device memory");
-    if ((reinterpret_cast<uintptr_t>(col_idx) & 15u) != 0)
-        return set_error(BFS_ERR_INVALID_ARG, "bfs_run_noalloc: col_idx must be 16-byte aligned (adjacency is staged by bulk copies)");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     std::lock_guard<std::mutex> lk(g_mu);
     int dev = 0;

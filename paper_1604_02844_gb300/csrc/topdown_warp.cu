@@ -29,7 +29,6 @@
 #include <stdint.h>
 
 #include <algorithm>
-#include <cstddef>
 
 #include "device_common.cuh"
 #include "internal.cuh"
@@ -41,10 +40,6 @@ using namespace dev;
 
 constexpr int W = 256;       // unit edge target and hub slice length
 constexpr int MAXI = 2 * W;  // edges of one work item are < MAXI
-// A staged item: each entry's slice is copied as its 16-byte-aligned
-// superset (at most 3 extra words before and after), so an item of < MAXI
-// edges and <= 32 entries needs < MAXI + 6*32 words.
-constexpr int MAXP = MAXI + 6 * 32;
 constexpr int OBW = 128;     // out-buffer entries per warp
 constexpr int UA = 8;        // pass A: visited-word loads per lane in flight
 constexpr int UB = 2;        // pass B: claims per lane in flight
@@ -70,23 +65,14 @@ struct WParams {
 };
 
 struct WarpSmem {
-    unsigned long long mbar[2];             // bulk-copy completion, one per staging buffer
-    alignas(16) int32_t stage[2][MAXP];     // staged adjacency (padded slices); pass A compacts in place
-    uint16_t ce[MAXP];                      // candidate -> staged position inside the item
-    int32_t off[2][33];                     // item entries: prefix of padded slice lengths
-    int32_t iu[2][32];                      // item entries: vertex
-    int32_t hd[2][32];                      // item entries: words of padding before the slice
-    int32_t ln[2][32];                      // item entries: slice length
+    int32_t stage[2][MAXI];  // staged adjacency; pass A compacts candidates in place
+    uint16_t ce[MAXI];       // candidate -> edge index inside the item
+    int32_t off[2][33];      // item entries: prefix of lengths
+    int32_t iu[2][32];       // item entries: vertex
     int32_t wv[OBW], wu[OBW];           // claimed vertices and their sources (internal ids)
     int32_t ou[OBW], ob[OBW], ol[OBW];  // flush: the new frontier entries
     int32_t ust[OBW];                   // flush: unit starts
 };
-
-// bulk copies need 16-byte aligned destinations: every staging buffer of
-// every warp (padded slice offsets are multiples of 4 words)
-static_assert(offsetof(WarpSmem, stage) % 16 == 0, "staging buffer alignment");
-static_assert((MAXP * 4) % 16 == 0, "staging buffer stride");
-static_assert(sizeof(WarpSmem) % 16 == 0, "per-warp shared block stride");
 
 template <int WPB>
 struct CtaSmem {
@@ -146,12 +132,14 @@ __device__ __forceinline__ Item load_item(const WParams &p, int qi, const Desc &
     return it;  // lengths are checked in stage_item, so the loads stay in flight
 }
 
-// Issue the bulk copies of an item's adjacency into stage[buf]: entry j's
-// slice col[b, b+len) is copied as the 16-byte-aligned superset
-// [b & ~3, (b+len+3) & ~3) at the padded offset off[j] (prefix of padded
-// lengths), all completing on mbar[buf].  The bulk copies bypass L1, which
-// stays with the visited-word reads.  Returns the padded word count (uniform).
-__device__ __forceinline__ int stage_item(WarpSmem &ws, const WParams &p, const Item &it_in, int buf, int &edges)
+// Prefix-sum the item's lengths into off[buf], record vertices, and issue the
+// cp.async copies of its adjacency into stage[buf].  Consecutive lanes copy
+// consecutive edges of the concatenated lists (coalesced); the entry of each
+// edge comes from a warp-level search: the entries starting inside a batch
+// of 32 edges form a bit mask (redux.or), and a popc over it counts the
+// entry boundaries before each lane.  Commits one group per lane.  Returns
+// the item's edge count (uniform).
+__device__ __forceinline__ int stage_item(WarpSmem &ws, const WParams &p, const Item &it_in, int buf)
 {
     const int lane = threadIdx.x & 31;
     Item it = it_in;
@@ -159,52 +147,37 @@ __device__ __forceinline__ int stage_item(WarpSmem &ws, const WParams &p, const 
         atomicOr(&p.ctrl->status, ST_OVERFLOW);
         it.l = 0;
     }
-    const bool real = lane < it.cnt;
-    const int len = real ? it.l : 0;
-    const int head = it.b & 3;
-    const int plen = len > 0 ? (((it.b + len + 3) & ~3) - (it.b & ~3)) : 0;
-    int inc = plen;
+    int inc = it.l;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
         const int y = __shfl_up_sync(FULL, inc, o);
         if (lane >= o) inc += y;
     }
-    int ptot = __shfl_sync(FULL, inc, 31);
-    const bool fits = ptot <= MAXP;  // cannot fail: < MAXI edges and <= 32 entries
-    if (!fits) {
+    int et = __shfl_sync(FULL, inc, 31);
+    if (et >= MAXI) {  // cannot happen: units < 2W edges, slices <= W
         if (lane == 0) atomicOr(&p.ctrl->status, ST_OVERFLOW);
-        ptot = 0;
+        et = 0;
     }
-    const int off = inc - plen;
-    edges = __reduce_add_sync(FULL, fits ? (unsigned)len : 0u);
+    const int off = inc - it.l;
+    const bool real = lane < it.cnt;
     if (real) {
         ws.off[buf][lane] = off;
         ws.iu[buf][lane] = it.u;
-        ws.hd[buf][lane] = head;
-        ws.ln[buf][lane] = fits ? len : 0;
     }
-    if (lane == 0) {
-        ws.off[buf][it.cnt] = ptot;
-        if (ptot > 0) mbar_arrive_expect_tx(&ws.mbar[buf], (unsigned)ptot * 4u);
-        else mbar_arrive(&ws.mbar[buf]);
+    if (lane == 0) ws.off[buf][it.cnt] = et;
+#pragma unroll 4
+    for (int base = 0; base < et; base += 32) {
+        unsigned starts = (real && off > base && off < base + 32) ? (1u << (off - base)) : 0u;
+        starts = __reduce_or_sync(FULL, starts);
+        const int j0 = __popc(__ballot_sync(FULL, real && off <= base)) - 1;
+        const int j = j0 + __popc(starts & ((2u << lane) - 1u));
+        const int jb = __shfl_sync(FULL, it.b, j & 31);
+        const int jo = __shfl_sync(FULL, off, j & 31);
+        const int e = base + lane;
+        if (e < et) cp_async4(&ws.stage[buf][e], p.col + jb + (e - jo));
     }
-    __syncwarp();
-    if (fits && len > 0)
-        tma_load_1d(&ws.stage[buf][off], p.col + (it.b & ~3), (unsigned)plen * 4u, &ws.mbar[buf]);
-    return ptot;
-}
-
-// After the copies of stage[buf] have landed: mark the padding words -1.
-__device__ __forceinline__ void clear_padding(WarpSmem &ws, int buf, int cnt)
-{
-    const int lane = threadIdx.x & 31;
-    if (lane < cnt) {
-        const int off = ws.off[buf][lane], end = ws.off[buf][lane + 1];
-        const int hd = ws.hd[buf][lane], ln = ws.ln[buf][lane];
-        for (int k = off; k < off + hd; ++k) ws.stage[buf][k] = -1;
-        for (int k = off + hd + ln; k < end; ++k) ws.stage[buf][k] = -1;
-    }
-    __syncwarp();
+    cp_async_commit();
+    return et;
 }
 
 // Finish the vertices this warp claimed: write level and parent (in the
@@ -413,7 +386,7 @@ __device__ __forceinline__ void process_item(WarpSmem &ws, const WParams &p, int
 #pragma unroll
         for (int k = 0; k < UA; ++k) {
             const int e = base + k * 32 + lane;
-            v[k] = e < et ? stg[e] : -1;  // -1: outside the range or padding
+            v[k] = e < et ? stg[e] : -1;
         }
 #pragma unroll
         // L1-cached read: bits are only ever set during a search, so a stale
@@ -475,7 +448,6 @@ __device__ __forceinline__ void process_item(WarpSmem &ws, const WParams &p, int
             ocnt += __popc(m);
         }
     }
-    fence_proxy_async_smem();  // stage[buf] is written by bulk copies next
     __syncwarp();
 }
 
@@ -530,13 +502,6 @@ __global__ void __launch_bounds__(WPB * 32, (24 / WPB) > 0 ? (24 / WPB) : 1) td_
             }
         }
     }
-    if (lane == 0) {
-        mbar_init(&ws.mbar[0], 1);
-        mbar_init(&ws.mbar[1], 1);
-        mbar_init_fence();
-    }
-    __syncwarp();
-    unsigned phases = 0u;  // bit b: parity of the next phase to wait for on mbar[b]
     bool ok = grid_sync(&c->bar_count, &c->bar_gen, &c->status, G, p.timeout_ns, &cs.ok);
 
     for (int d = 0; ok; ++d) {
@@ -568,50 +533,39 @@ __global__ void __launch_bounds__(WPB * 32, (24 / WPB) > 0 ? (24 / WPB) : 1) td_
         Desc d0 = load_desc(p, qi, nH, n_items, id);
         Item cur = load_item(p, qi, d0, id < n_items);
         int buf = 0;
-        int real_cur = 0;
-        int et_cur = (id < n_items) ? stage_item(ws, p, cur, buf, real_cur) : 0;
+        int et_cur = (id < n_items) ? stage_item(ws, p, cur, buf) : 0;
         int cnt_cur = cur.cnt;
         if (p.stats && id < n_items && lane == 0)
             my_vertices += (d0.c < 0) ? (cur.b == __ldg(p.ro + cur.u) ? 1 : 0) : (unsigned)cur.cnt;
         Desc d1 = load_desc(p, qi, nH, n_items, id + GW);
         Item nxt = load_item(p, qi, d1, id + GW < n_items);
         Desc d2 = load_desc(p, qi, nH, n_items, id + 2 * GW);
-        bool staged_other = false;
         while (id < n_items) {
             const unsigned id1 = id + GW, id2 = id + 2 * GW;
-            int et_nxt = 0, real_nxt = 0;
-            staged_other = false;
+            int et_nxt = 0;
             if (id1 < n_items) {
-                et_nxt = stage_item(ws, p, nxt, buf ^ 1, real_nxt);
-                staged_other = true;
+                et_nxt = stage_item(ws, p, nxt, buf ^ 1);
                 if (p.stats && lane == 0)
                     my_vertices += (d1.c < 0) ? (nxt.b == __ldg(p.ro + nxt.u) ? 1 : 0) : (unsigned)nxt.cnt;
+            } else {
+                cp_async_commit();  // keep one group per item on every lane
             }
             const int cnt_nxt = nxt.cnt;
             const Item nn = load_item(p, qi, d2, id2 < n_items);
             const Desc d3 = load_desc(p, qi, nH, n_items, id2 + GW);
-            if (!mbar_wait(&ws.mbar[buf], (phases >> buf) & 1u, &c->status, p.timeout_ns)) break;
-            phases ^= 1u << buf;
-            clear_padding(ws, buf, cnt_cur);
-            if (lane == 0) my_edges += (unsigned long long)real_cur;
+            asm volatile("cp.async.wait_group 1;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) my_edges += (unsigned long long)et_cur;
             process_item(ws, p, buf, et_cur, cnt_cur, next_level, set_out, qo, ocnt, my_new);
             buf ^= 1;
             id = id1;
             et_cur = et_nxt;
-            real_cur = real_nxt;
             cnt_cur = cnt_nxt;
             d1 = d2;
             nxt = nn;
             d2 = d3;
-            staged_other = false;
         }
-        if (id < n_items) {
-            // a wait ran out: give the copies still in flight one more
-            // bounded wait before this warp leaves through the barrier
-            if (mbar_wait(&ws.mbar[buf], (phases >> buf) & 1u, &c->status, p.timeout_ns)) phases ^= 1u << buf;
-            if (staged_other && mbar_wait(&ws.mbar[buf ^ 1], (phases >> (buf ^ 1)) & 1u, &c->status, p.timeout_ns))
-                phases ^= 1u << (buf ^ 1);
-        }
+        cp_async_wait_all();
         __syncwarp();
         if (ocnt > 0) warp_flush(ws, p, set_out, qo, ocnt, next_level);
 

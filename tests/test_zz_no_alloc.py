@@ -88,14 +88,3 @@ def test_noalloc_rejects_out_of_limit_and_host_arguments():
         gb.bfs_run_noalloc(small, np.array([1, 0], np.int32), 0,
                            torch.empty(2, dtype=torch.int32, device="cuda"))
     assert ei.value.status == gb.BFS_ERR_INVALID_ARG
-
-
-def test_noalloc_rejects_misaligned_adjacency():
-    ro, col = graphgen.kronecker(10, 16, 23)
-    n, m = len(ro) - 1, len(col)
-    d_ro = torch.from_numpy(ro).cuda()
-    d_col = torch.zeros(m + 4, dtype=torch.int32, device="cuda")
-    lv = torch.empty(n, dtype=torch.int32, device="cuda")
-    with pytest.raises(gb.BfsError) as ei:  # 4 bytes past a 16-byte boundary
-        gb.bfs_run_noalloc(d_ro, d_col.data_ptr() + 4, 0, lv, m=m, n=n)
-    assert ei.value.status == gb.BFS_ERR_INVALID_ARG
