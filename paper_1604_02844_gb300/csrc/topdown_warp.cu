@@ -133,12 +133,13 @@ __device__ __forceinline__ Item load_item(const WParams &p, int qi, const Desc &
 }
 
 // Prefix-sum the item's lengths into off[buf], record vertices, and issue the
-// cp.async copies of its adjacency into stage[buf].  Consecutive lanes copy
-// consecutive edges of the concatenated lists (coalesced); the entry of each
-// edge comes from a warp-level search: the entries starting inside a batch
-// of 32 edges form a bit mask (redux.or), and a popc over it counts the
-// entry boundaries before each lane.  Commits one group per lane.  Returns
-// the item's edge count (uniform).
+// cp.async copies of its adjacency into stage[buf].  Lists of >= 32 edges
+// are copied by the whole warp striding over each (coalesced, no search);
+// the short lists are flattened: consecutive lanes copy consecutive edges of
+// the concatenated short lists, each lane finding its list with a warp-level
+// search (the short lists starting inside a batch of 32 edges form a bit
+// mask, redux.or; a popc counts the boundaries before the lane).  Commits
+// one group per lane.  Returns the item's edge count (uniform).
 __device__ __forceinline__ int stage_item(WarpSmem &ws, const WParams &p, const Item &it_in, int buf)
 {
     const int lane = threadIdx.x & 31;
@@ -147,34 +148,72 @@ __device__ __forceinline__ int stage_item(WarpSmem &ws, const WParams &p, const 
         atomicOr(&p.ctrl->status, ST_OVERFLOW);
         it.l = 0;
     }
-    int inc = it.l;
+    const bool real = lane < it.cnt;
+    const bool shortl = real && it.l < 32;
+    const int sl = shortl ? it.l : 0;
+    int inc = it.l, sinc = sl;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
         const int y = __shfl_up_sync(FULL, inc, o);
-        if (lane >= o) inc += y;
+        const int z = __shfl_up_sync(FULL, sinc, o);
+        if (lane >= o) {
+            inc += y;
+            sinc += z;
+        }
     }
     int et = __shfl_sync(FULL, inc, 31);
-    if (et >= MAXI) {  // cannot happen: units < 2W edges, slices <= W
+    const int st = __shfl_sync(FULL, sinc, 31);
+    const bool fits = et < MAXI;  // cannot fail: units < 2W edges, slices <= W
+    if (!fits) {
         if (lane == 0) atomicOr(&p.ctrl->status, ST_OVERFLOW);
         et = 0;
     }
     const int off = inc - it.l;
-    const bool real = lane < it.cnt;
+    const int soff = sinc - sl;
     if (real) {
         ws.off[buf][lane] = off;
         ws.iu[buf][lane] = it.u;
     }
     if (lane == 0) ws.off[buf][it.cnt] = et;
-#pragma unroll 4
-    for (int base = 0; base < et; base += 32) {
-        unsigned starts = (real && off > base && off < base + 32) ? (1u << (off - base)) : 0u;
-        starts = __reduce_or_sync(FULL, starts);
-        const int j0 = __popc(__ballot_sync(FULL, real && off <= base)) - 1;
-        const int j = j0 + __popc(starts & ((2u << lane) - 1u));
-        const int jb = __shfl_sync(FULL, it.b, j & 31);
-        const int jo = __shfl_sync(FULL, off, j & 31);
-        const int e = base + lane;
-        if (e < et) cp_async4(&ws.stage[buf][e], p.col + jb + (e - jo));
+    if (fits) {
+        // long lists
+        unsigned big = __ballot_sync(FULL, real && it.l >= 32);
+        while (big) {
+            const int src = __ffs(big) - 1;
+            big &= big - 1;
+            const int bo = __shfl_sync(FULL, off, src);
+            const int bb = __shfl_sync(FULL, it.b, src);
+            const int bl = __shfl_sync(FULL, it.l, src);
+            for (int k = lane; k < bl; k += 32) cp_async4(&ws.stage[buf][bo + k], p.col + bb + k);
+        }
+        // short lists, flattened
+        const unsigned sm = __ballot_sync(FULL, shortl);
+#pragma unroll 2
+        for (int base = 0; base < st; base += 32) {
+            unsigned starts = (shortl && soff > base && soff < base + 32) ? (1u << (soff - base)) : 0u;
+            starts = __reduce_or_sync(FULL, starts);
+            const unsigned below = __ballot_sync(FULL, shortl && soff <= base);
+            // the short list holding edge base + lane: the (rank)-th short list
+            const int rank = __popc(below) - 1 + __popc(starts & ((2u << lane) - 1u));
+            // lane of the rank-th (0-based) short list: the smallest j with
+            // more than `rank` short lists among lanes 0..j (5 fixed steps)
+            int j = 0;
+            {
+                int lo = 0, hi = 31;
+#pragma unroll
+                for (int step = 0; step < 5; ++step) {
+                    const int mid = (lo + hi) >> 1;
+                    if (__popc(sm & ((2u << mid) - 1u)) > rank) hi = mid;
+                    else lo = mid + 1;
+                }
+                j = lo & 31;
+            }
+            const int jb = __shfl_sync(FULL, it.b, j);
+            const int jo = __shfl_sync(FULL, off, j);
+            const int js = __shfl_sync(FULL, soff, j);
+            const int e = base + lane;
+            if (e < st) cp_async4(&ws.stage[buf][jo + (e - js)], p.col + jb + (e - js));
+        }
     }
     cp_async_commit();
     return et;
