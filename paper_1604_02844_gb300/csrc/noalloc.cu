@@ -37,7 +37,7 @@ namespace {
 constexpr int64_t kMaxN = BFS_NOALLOC_MAX_VERTICES;
 constexpr int64_t kMaxM = BFS_NOALLOC_MAX_EDGES;
 constexpr int64_t kBitmapWords = ((kMaxN + 31) / 32 + 3) / 4 * 4;
-constexpr int64_t kHubCap = kMaxM / 128 + 2;  // as td_hub_capacity(kMaxM)
+constexpr int64_t kHubCap = kMaxM / 128 + 2;  // >= td_hub_capacity(kMaxM) = 2 m / W + 2
 
 // byte offsets inside the scratch array (each a multiple of 256)
 constexpr int64_t align256(int64_t x) { return (x + 255) / 256 * 256; }

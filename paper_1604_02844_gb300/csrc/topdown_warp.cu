@@ -38,7 +38,7 @@ namespace {
 
 using namespace dev;
 
-constexpr int W = 256;       // unit edge target and hub slice length
+constexpr int W = 384;       // unit edge target and hub slice length
 constexpr int MAXI = 2 * W;  // edges of one work item are < MAXI
 constexpr int OBW = 128;     // out-buffer entries per warp
 constexpr int UA = 8;        // pass A: visited-word loads per lane in flight
@@ -675,8 +675,8 @@ int launch(Graph *g, const WParams &prm, cudaStream_t s)
 }  // namespace
 
 // Hub slices of one layer: a vertex of degree d > W gives ceil(d/W) <= 2d/W
-// slices, so a layer has at most 2m/W = m/128 of them (+2).
-int64_t td_hub_capacity(int64_t m) { return m / 128 + 2; }
+// slices, so a layer has at most 2m/W of them (+2).
+int64_t td_hub_capacity(int64_t m) { return 2 * (m / W) + 2; }
 
 int td_warp_launch(Graph *g, int32_t root, int32_t *level, int32_t *parent, cudaStream_t s)
 {
