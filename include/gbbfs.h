@@ -154,7 +154,7 @@ int bfs_run(bfs_graph *g, int32_t root, int32_t *level_out, int32_t *parent_out,
  * the CUDA runtime forbids allocation.  The search runs the same top-down
  * kernel as bfs_run (BFS_OPT_MODE 0, BLOCK 512) directly on the caller's
  * device CSR, with all scratch state in one fixed-size __device__ array
- * built into the library (about 9 MB, held by every GPU that loads the
+ * built into the library (about 7 MB, held by every GPU that loads the
  * library until the process exits).  No cudaMalloc, cudaFree or allocating
  * library call is made.
  *   row_offsets, col_idx : the caller's CSR in DEVICE memory (checked as in

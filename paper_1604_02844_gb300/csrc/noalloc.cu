@@ -14,7 +14,7 @@
 // routine.
 //
 // Limits: n <= BFS_NOALLOC_MAX_VERTICES, m <= BFS_NOALLOC_MAX_EDGES (the
-// array is sized for them, about 9 MB, and every GPU that loads the library
+// array is sized for them, about 7 MB, and every GPU that loads the library
 // holds it until the process exits).  The first call on a device sets the
 // array up (its device address, the identity maps); make that first call
 // before any stream capture.  All calls share the one array, which keeps
@@ -37,7 +37,7 @@ namespace {
 constexpr int64_t kMaxN = BFS_NOALLOC_MAX_VERTICES;
 constexpr int64_t kMaxM = BFS_NOALLOC_MAX_EDGES;
 constexpr int64_t kBitmapWords = ((kMaxN + 31) / 32 + 3) / 4 * 4;
-constexpr int64_t kHubCap = 2 * (kMaxM / 64) + 2;  // = td_hub_capacity(kMaxM)
+constexpr int64_t kHubCap = kMaxM / 128 + 2;  // >= td_hub_capacity(kMaxM) = 2 m / W + 2
 
 // byte offsets inside the scratch array (each a multiple of 256)
 constexpr int64_t align256(int64_t x) { return (x + 255) / 256 * 256; }

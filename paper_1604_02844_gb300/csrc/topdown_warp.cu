@@ -39,8 +39,6 @@ namespace {
 using namespace dev;
 
 constexpr int W = 384;       // unit edge target and hub slice length
-constexpr int SL_SMALL = 64; // hub slice length for vertices found by a layer
-                             // with fewer work items than the grid has warps
 constexpr int MAXI = 2 * W;  // edges of one work item are < MAXI
 constexpr int OBW = 128;     // out-buffer entries per warp
 constexpr int UA = 8;        // pass A: visited-word loads per lane in flight
@@ -226,7 +224,7 @@ __device__ __forceinline__ int stage_item(WarpSmem &ws, const WParams &p, const 
 // ones as frontier entries cut into units and the hubs as slices.  All loads
 // of a lane are issued together, so one flush costs about one round trip.
 __device__ __forceinline__ void warp_flush(WarpSmem &ws, const WParams &p, int set_out, int qo, int c,
-                                        int next_level, int sl)
+                                        int next_level)
 {
     constexpr int PER = OBW / 32;
     const int lane = threadIdx.x & 31;
@@ -252,8 +250,8 @@ __device__ __forceinline__ void warp_flush(WarpSmem &ws, const WParams &p, int s
             p.level[ov[k]] = next_level;
             if (p.parent) p.parent[ov[k]] = ou[k];
             const int len = re[k] - rb[k];
-            nsmall += (len >= 1 && len <= sl);
-            nslice += (len > sl) ? (len + sl - 1) / sl : 0;
+            nsmall += (len >= 1 && len <= W);
+            nslice += (len > W) ? (len + W - 1) / W : 0;
         }
     }
     // positions of the short entries (in claim order) and the hub slices
@@ -280,19 +278,19 @@ __device__ __forceinline__ void warp_flush(WarpSmem &ws, const WParams &p, int s
             const int i = i0 + k;
             if (i < i1) {
                 const int len = re[k] - rb[k];
-                if (len >= 1 && len <= sl) {
+                if (len >= 1 && len <= W) {
                     ws.ou[spos] = ws.wv[i];
                     ws.ob[spos] = rb[k];
                     ws.ol[spos] = len;
                     ++spos;
-                } else if (len > sl) {
-                    const int nseg = (len + sl - 1) / sl;
+                } else if (len > W) {
+                    const int nseg = (len + W - 1) / W;
                     if (nseg <= 8) {  // a few slices: this lane writes them
                         for (int sg = 0; sg < nseg; ++sg, ++hpos) {
                             if (hpos < p.hcap) {
                                 p.hu[qo][hpos] = ws.wv[i];
-                                p.hb[qo][hpos] = rb[k] + sg * sl;
-                                p.hl[qo][hpos] = min(sl, len - sg * sl);
+                                p.hb[qo][hpos] = rb[k] + sg * W;
+                                p.hl[qo][hpos] = min(W, len - sg * W);
                             } else {
                                 atomicOr(&p.ctrl->status, ST_OVERFLOW);
                             }
@@ -313,11 +311,11 @@ __device__ __forceinline__ void warp_flush(WarpSmem &ws, const WParams &p, int s
         for (int k = 0; k < PER; ++k) {
             const int i = i0 + k;
             const int len = (i < i1) ? re[k] - rb[k] : 0;
-            big_l[k] = (len > sl && (len + sl - 1) / sl > 8) ? len : 0;
+            big_l[k] = (len > W && (len + W - 1) / W > 8) ? len : 0;
             big_v[k] = (i < i1) ? ws.wv[i] : 0;
             big_b[k] = (i < i1) ? rb[k] : 0;
             big_at[k] = hpos;
-            if (len > sl) hpos += (unsigned)((len + sl - 1) / sl);
+            if (len > W) hpos += (unsigned)((len + W - 1) / W);
         }
 #pragma unroll
         for (int k = 0; k < PER; ++k) {
@@ -329,13 +327,13 @@ __device__ __forceinline__ void warp_flush(WarpSmem &ws, const WParams &p, int s
                 const int hb = __shfl_sync(FULL, big_b[k], src);
                 const int hl = __shfl_sync(FULL, big_l[k], src);
                 const unsigned at = __shfl_sync(FULL, big_at[k], src);
-                const int nseg = (hl + sl - 1) / sl;
+                const int nseg = (hl + W - 1) / W;
                 for (int sg = lane; sg < nseg; sg += 32) {
                     const unsigned g = at + (unsigned)sg;
                     if (g < p.hcap) {
                         p.hu[qo][g] = hv;
-                        p.hb[qo][g] = hb + sg * sl;
-                        p.hl[qo][g] = min(sl, hl - sg * sl);
+                        p.hb[qo][g] = hb + sg * W;
+                        p.hl[qo][g] = min(W, hl - sg * W);
                     } else {
                         atomicOr(&p.ctrl->status, ST_OVERFLOW);
                     }
@@ -414,8 +412,7 @@ __device__ __forceinline__ void warp_flush(WarpSmem &ws, const WParams &p, int s
 
 // Passes A and B over the staged item in stage[buf] with `et` edges.
 __device__ __forceinline__ void process_item(WarpSmem &ws, const WParams &p, int buf, int et, int cnt,
-                                             int next_level, int set_out, int qo, int &ocnt, unsigned &my_new,
-                                             int sl)
+                                             int next_level, int set_out, int qo, int &ocnt, unsigned &my_new)
 {
     const int lane = threadIdx.x & 31;
     const unsigned lt = lanemask_lt();
@@ -452,7 +449,7 @@ __device__ __forceinline__ void process_item(WarpSmem &ws, const WParams &p, int
     for (int c0 = 0; c0 < nc; c0 += 32 * UB) {
         // room for a whole batch of winners, flushed outside the claim loop
         if (ocnt > OBW - 32 * UB) {
-            warp_flush(ws, p, set_out, qo, ocnt, next_level, sl);
+            warp_flush(ws, p, set_out, qo, ocnt, next_level);
             ocnt = 0;
         }
         int v[UB], e[UB];
@@ -502,6 +499,7 @@ __global__ void __launch_bounds__(WPB * 32, (24 / WPB) > 0 ? (24 / WPB) : 1) td_
     WarpSmem &ws = cs.w[warp];
     const unsigned G = gridDim.x;
     const unsigned GW = G * WPB;
+    const unsigned gw = blockIdx.x * WPB + warp;
     Ctrl *c = p.ctrl;
     const uint64_t t_start = globaltimer();
 
@@ -524,19 +522,19 @@ __global__ void __launch_bounds__(WPB * 32, (24 / WPB) > 0 ? (24 / WPB) : 1) td_
                 const int rb = p.ro[rint], len = p.ro[rint + 1] - rb;
                 c->eu_count[0] = 0;
                 c->hub_count[0] = 0;
-                if (len >= 1 && len <= SL_SMALL) {
+                if (len >= 1 && len <= W) {
                     p.eu[0][0] = rint;
                     p.eb[0][0] = rb;
                     p.el[0][0] = len;
                     p.us[0][0] = 0;
                     p.uc[0][0] = 1;
                     c->eu_count[0] = (1ull << 32) | 1ull;
-                } else if (len > SL_SMALL) {
-                    const int nseg = (len + SL_SMALL - 1) / SL_SMALL;
+                } else if (len > W) {
+                    const int nseg = (len + W - 1) / W;
                     for (int s = 0; s < nseg && (unsigned)s < p.hcap; ++s) {
                         p.hu[0][s] = rint;
-                        p.hb[0][s] = rb + s * SL_SMALL;
-                        p.hl[0][s] = min(SL_SMALL, len - s * SL_SMALL);
+                        p.hb[0][s] = rb + s * W;
+                        p.hl[0][s] = min(W, len - s * W);
                     }
                     c->hub_count[0] = (unsigned)nseg;
                 }
@@ -562,7 +560,6 @@ __global__ void __launch_bounds__(WPB * 32, (24 / WPB) > 0 ? (24 / WPB) : 1) td_
         if (blockIdx.x == 0 && tid == 0) {
             c->eu_count[set_rst] = 0;
             c->hub_count[set_rst] = 0;
-            c->work[set_rst] = 0;
         }
         const int qi = d & 1, qo = qi ^ 1;
         const int next_level = d + 1;
@@ -570,17 +567,8 @@ __global__ void __launch_bounds__(WPB * 32, (24 / WPB) > 0 ? (24 / WPB) : 1) td_
         unsigned long long my_vertices = 0, my_edges = 0;
         int ocnt = 0;
 
-        // small layers cut the hubs they find into short slices, so that the
-        // next layer spreads over many warps
-        const int sl = (n_items < GW) ? SL_SMALL : W;
-        // software pipeline over items handed out by an atomic counter; the
-        // id three items ahead is requested one iteration before it is used
-        unsigned first = 0;
-        if (lane == 0) first = atomicAdd(&c->work[set_in], 3u);
-        first = __shfl_sync(FULL, first, 0);
-        unsigned id = first, id1 = first + 1, id2 = first + 2;
-        unsigned pend = 0;
-        if (lane == 0) pend = atomicAdd(&c->work[set_in], 1u);
+        // software pipeline over this warp's items gw, gw+GW, ...
+        unsigned id = gw;
         Desc d0 = load_desc(p, qi, nH, n_items, id);
         Item cur = load_item(p, qi, d0, id < n_items);
         int buf = 0;
@@ -588,10 +576,11 @@ __global__ void __launch_bounds__(WPB * 32, (24 / WPB) > 0 ? (24 / WPB) : 1) td_
         int cnt_cur = cur.cnt;
         if (p.stats && id < n_items && lane == 0)
             my_vertices += (d0.c < 0) ? (cur.b == __ldg(p.ro + cur.u) ? 1 : 0) : (unsigned)cur.cnt;
-        Desc d1 = load_desc(p, qi, nH, n_items, id1);
-        Item nxt = load_item(p, qi, d1, id1 < n_items);
-        Desc d2 = load_desc(p, qi, nH, n_items, id2);
+        Desc d1 = load_desc(p, qi, nH, n_items, id + GW);
+        Item nxt = load_item(p, qi, d1, id + GW < n_items);
+        Desc d2 = load_desc(p, qi, nH, n_items, id + 2 * GW);
         while (id < n_items) {
+            const unsigned id1 = id + GW, id2 = id + 2 * GW;
             int et_nxt = 0;
             if (id1 < n_items) {
                 et_nxt = stage_item(ws, p, nxt, buf ^ 1);
@@ -602,18 +591,13 @@ __global__ void __launch_bounds__(WPB * 32, (24 / WPB) > 0 ? (24 / WPB) : 1) td_
             }
             const int cnt_nxt = nxt.cnt;
             const Item nn = load_item(p, qi, d2, id2 < n_items);
-            const unsigned id3 = __shfl_sync(FULL, pend, 0);
-            const Desc d3 = load_desc(p, qi, nH, n_items, id3);
-            if (lane == 0 && id3 < n_items) pend = atomicAdd(&c->work[set_in], 1u);
-            else if (lane == 0) pend = id3;  // past the end: stop asking
+            const Desc d3 = load_desc(p, qi, nH, n_items, id2 + GW);
             asm volatile("cp.async.wait_group 1;" ::: "memory");
             __syncwarp();
             if (lane == 0) my_edges += (unsigned long long)et_cur;
-            process_item(ws, p, buf, et_cur, cnt_cur, next_level, set_out, qo, ocnt, my_new, sl);
+            process_item(ws, p, buf, et_cur, cnt_cur, next_level, set_out, qo, ocnt, my_new);
             buf ^= 1;
             id = id1;
-            id1 = id2;
-            id2 = id3;
             et_cur = et_nxt;
             cnt_cur = cnt_nxt;
             d1 = d2;
@@ -622,7 +606,7 @@ __global__ void __launch_bounds__(WPB * 32, (24 / WPB) > 0 ? (24 / WPB) : 1) td_
         }
         cp_async_wait_all();
         __syncwarp();
-        if (ocnt > 0) warp_flush(ws, p, set_out, qo, ocnt, next_level, sl);
+        if (ocnt > 0) warp_flush(ws, p, set_out, qo, ocnt, next_level);
 
         if (p.stats && d < kMaxStatLayers) {
             unsigned long long a = my_vertices, e = my_edges, t = my_new;
@@ -690,9 +674,9 @@ int launch(Graph *g, const WParams &prm, cudaStream_t s)
 
 }  // namespace
 
-// Hub slices of one layer: a vertex of degree d > s gives ceil(d/s) <= 2d/s
-// slices of length s >= SL_SMALL, so a layer has at most 2m/SL_SMALL of them.
-int64_t td_hub_capacity(int64_t m) { return 2 * (m / SL_SMALL) + 2; }
+// Hub slices of one layer: a vertex of degree d > W gives ceil(d/W) <= 2d/W
+// slices, so a layer has at most 2m/W of them (+2).
+int64_t td_hub_capacity(int64_t m) { return 2 * (m / W) + 2; }
 
 int td_warp_launch(Graph *g, int32_t root, int32_t *level, int32_t *parent, cudaStream_t s)
 {
