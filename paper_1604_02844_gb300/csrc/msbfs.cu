@@ -30,10 +30,11 @@
 // frontier words of its neighbours (in-neighbours = out-neighbours), with an
 // early exit once every missing live lane is found; no atomics, no touched
 // list.  An iteration is a pull step when the frontier's adjacency exceeds
-// m/16 entries and at least 30% of the live lanes' (vertex, lane) pairs over
-// vertices of degree >= 1 are already reached -- before that, most vertices
-// miss lanes whose frontier is still far away and would scan their whole
-// adjacency (the multi-lane form of the direction-optimising switch).
+// m/16 entries, every live lane is at least two iterations old, and at least
+// 30% of the live lanes' (vertex, lane) pairs over vertices of degree >= 1
+// are already reached -- otherwise most vertices miss lanes whose frontier is
+// still far away and would scan their whole adjacency without an early exit
+// (the multi-lane form of the direction-optimising switch).
 //
 // All iterations of a launch run in one persistent cooperative kernel with
 // two bounded grid barriers per iteration.
@@ -397,6 +398,7 @@ __global__ void __launch_bounds__(MS_WPB * 32) ms_kernel(MsParams p)
     __shared__ unsigned s_nF, s_iter0;
     __shared__ unsigned long long s_alive;
     __shared__ uint32_t s_lv[16];
+    __shared__ int s_minage;
     __shared__ int32_t s_tbuf[MS_WPB][TB];
     __shared__ unsigned long long s_over;  // lanes whose level this iteration would exceed 254
     const int tid = threadIdx.x, lane = tid & 31;
@@ -427,7 +429,14 @@ __global__ void __launch_bounds__(MS_WPB * 32) ms_kernel(MsParams p)
             c->alive[par ^ 1] = 0ull;
         }
         const unsigned long long live = ld_relaxed64(&c->alive[par]);
-        const bool pull = p.symmetric && (long long)ld_relaxed64(&c->fedges[par]) * 16 > p.m &&
+        // youngest live lane: a lane injected less than two iterations ago has
+        // explored almost nothing, and a pull step would scan every adjacency
+        // list for it without an early exit
+        if (tid == 0) s_minage = 0x7fffffff;
+        __syncthreads();
+        if (tid < 64 && ((live >> tid) & 1ull)) atomicMin(&s_minage, (int)iter - __ldg(p.start + tid));
+        __syncthreads();
+        const bool pull = p.symmetric && s_minage >= 2 && (long long)ld_relaxed64(&c->fedges[par]) * 16 > p.m &&
                           (double)ld_relaxed64(&c->seen_pairs) >= 0.3 * (double)__popcll(live) * (double)p.n_nonzero;
         if (!pull) {
             ms_expand(p, par, nF, s_tbuf[threadIdx.x >> 5]);
