@@ -65,6 +65,20 @@ def parse_args(argv=None):
     return ap.parse_args(argv)
 
 
+def combine_replicas(dist, world, hm_gteps, timed_device_s, steps):
+    """Replicas only: each rank searched its own roots on its own GPU.  The
+    job's value is the sum of the ranks' harmonic-mean GTEPS (they ran at the
+    same time); the step time is the slowest rank's.  Works on any backend
+    (gathered as Python objects)."""
+    if world == 1:
+        return hm_gteps, 1e3 * timed_device_s / steps
+    got = [None] * world
+    dist.all_gather_object(got, (float(hm_gteps), float(timed_device_s)))
+    value = sum(x[0] for x in got)
+    step_ms = 1e3 * max(x[1] for x in got) / steps
+    return value, step_ms
+
+
 def harmonic_mean(xs):
     xs = [x for x in xs]
     return len(xs) / sum(1.0 / x for x in xs)
@@ -508,13 +522,7 @@ def run_ours(args):
                "how": "host wall clock around bfs_run with pinned host level/parent outputs + stream sync, per root"}
 
     # combine ranks: max timed region, sum of per-rank throughput
-    value = hm
-    if world > 1:
-        t = torch.tensor([hm, total_dev], dtype=torch.float64, device=dev)
-        gathered = [torch.zeros_like(t) for _ in range(world)]
-        dist.all_gather(gathered, t)
-        value = sum(float(x[0]) for x in gathered)
-        step_ms = 1e3 * max(float(x[1]) for x in gathered) / args.steps
+    value, step_ms = combine_replicas(dist, world, hm, total_dev, args.steps)
 
     options = {k: g.get_option(k) for k in gb.OPTION_NAMES}
     batched = None
