@@ -56,6 +56,8 @@ def parse_args(argv=None):
                     help="skip the batched (bit-parallel multi-source) measurement")
     ap.add_argument("--batched-scale", type=int, default=20)
     ap.add_argument("--batched-sources", type=int, default=1024)
+    ap.add_argument("--no-ablation", action="store_true",
+                    help="skip the atomic-free (Alg. 3 restoration) and degree-binned runs")
     ap.add_argument("--no-serving", action="store_true",
                     help="skip the serving-loop measurement")
     ap.add_argument("--serving-requests", type=int, default=100000)
@@ -260,6 +262,44 @@ def run_reference(args):
     return 0
 
 
+def ablation_measurement(g, gb, torch, roots, mcc, checks, level, parent, flush, stream):
+    """The same searches through the other two expansion modes of bfs_run:
+    mode 2, the atomic-free variant of Alg. 3 (racy output bitmap, restoration
+    pass per layer), and mode 1, one item per frontier vertex binned by degree.
+    CUDA events around each search, L2 flushed in between; every search's
+    levels are checked against the atomic path's (count reached, sum)."""
+    base_mode = g.get_option("mode")
+    out = {}
+    for mode, name in ((2, "restoration_alg3"), (1, "degree_binned")):
+        g.set_option("mode", mode)
+        for r in roots[:4]:
+            gb.bfs_run(g.handle, int(r), level, parent, stream)
+        torch.cuda.synchronize()
+        evs = []
+        for r in roots:
+            flush.fill_(1)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            gb.bfs_run(g.handle, int(r), level, parent, stream)
+            e1.record(stream)
+            reached = level >= 0
+            evs.append((int(r), e0, e1, torch.stack([reached.sum(), level[reached].sum()])))
+        torch.cuda.synchronize()
+        assert g.status() == gb.BFS_OK, gb.last_error()
+        times, same = [], True
+        for r, e0, e1, ck in evs:
+            times.append((r, e0.elapsed_time(e1) * 1e-3))
+            same &= tuple(int(x) for x in ck.tolist()) == checks[r]
+        teps = [mcc[r] / t for r, t in times]
+        out[f"mode{mode}_{name}"] = {
+            "hm_gteps": harmonic_mean(teps) / 1e9,
+            "mean_launch_us": 1e6 * statistics.mean(t for _, t in times),
+            "levels_match_atomic_path": bool(same)}
+    g.set_option("mode", base_mode)
+    return out
+
+
 def batched_measurement(args, gb, torch, dev):
     """1,024 seeded sources on a Kronecker graph (scale 20, ef 16) through
     bfs_run_batch (64 sources per bit-parallel batch), against the plain path
@@ -436,7 +476,7 @@ def run_ours(args):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
 
     # per-root edge counts (bookkeeping for TEPS, outside any timed region)
-    mcc, bmin = {}, {}
+    mcc, bmin, checks = {}, {}, {}
     for r in roots:
         g.run(int(r), level, parent)
         reached = level >= 0
@@ -444,6 +484,7 @@ def run_ours(args):
         nr = int(reached.sum().item())
         mcc[int(r)] = dsum / 2.0
         bmin[int(r)] = algorithmic_bytes(dsum, nr, n)
+        checks[int(r)] = (nr, int(level[reached].sum().item()))
     torch.cuda.synchronize()
     assert g.status() == gb.BFS_OK, gb.last_error()
 
@@ -525,6 +566,11 @@ def run_ours(args):
     value, step_ms = combine_replicas(dist, world, hm, total_dev, args.steps)
 
     options = {k: g.get_option(k) for k in gb.OPTION_NAMES}
+    ablation = None
+    if not args.no_ablation and rank == 0:
+        ablation = ablation_measurement(g, gb, torch, roots, mcc, checks, level, parent, flush, stream)
+        for v in ablation.values():
+            v["vs_mode0_atomic"] = v["hm_gteps"] / hm
     batched = None
     if not args.no_batched and rank == 0:
         batched = batched_measurement(args, gb, torch, dev)
@@ -554,6 +600,7 @@ def run_ours(args):
                          "mean_launch_s": mean_t},
             "cpu_baseline": cpu,
             "e2e": e2e,
+            "ablation": ablation,
             "batched": batched,
             "serving": serving,
             "gpu_launches": len(runs),

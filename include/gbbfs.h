@@ -83,7 +83,13 @@ typedef enum {
                                    (short lists packed into units, hubs cut into slices)
                                    run by independent warps, BLOCK 256 or 512 (default);
                                    1 = one item per frontier vertex, binned by degree
-                                   and expanded by a thread, a warp or a whole CTA      */
+                                   and expanded by a thread, a warp or a whole CTA;
+                                   2 = as 0 without atomics: the output bitmap is set
+                                   by plain read-modify-writes and P[v] = u - n, then
+                                   a restoration pass per layer repairs both bitmaps
+                                   and P (Sec. 3.3.2, Alg. 3); BLOCK 256 or 512.  Its
+                                   workspace (4n bytes + one bitmap) is allocated on
+                                   the first run in this mode                          */
 } bfs_option;
 
 /* ---- library ------------------------------------------------------------ */

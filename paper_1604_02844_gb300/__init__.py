@@ -44,7 +44,7 @@ BFS_OPT_MAX_CTAS = 8
 BFS_OPT_BATCH_WIDTH = 9
 BFS_OPT_BATCH_BLOCK = 10
 BFS_OPT_MODE = 11
-MODE_WARP, MODE_BINNED = 0, 1
+MODE_WARP, MODE_BINNED, MODE_RESTORE = 0, 1, 2
 
 OPTION_NAMES = {
     "block": BFS_OPT_BLOCK, "ctas_per_sm": BFS_OPT_CTAS_PER_SM,

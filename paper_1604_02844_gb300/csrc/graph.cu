@@ -84,6 +84,8 @@ static void free_graph(Graph *g)
         }
         for (int j = 0; j < 2; ++j) cudaFree(g->d_uq[b][j]);
     }
+    cudaFree(g->d_vo);
+    cudaFree(g->d_pint);
     cudaFree(g->d_ctrl);
     cudaFree(g->d_stats);
     cudaFree(g->d_level_tmp);
@@ -109,6 +111,17 @@ static int alloc_binned(Graph *g)
             GB_CUDA(cudaMalloc(&g->d_q[b][j], (size_t)g->qcap * 4));
             GB_CUDA(cudaMalloc(&g->d_bq[b][j], (size_t)g->bqcap * 4));
         }
+    return BFS_OK;
+}
+
+// Restoration-mode workspace (Alg. 3 visited and output bitmaps as word
+// pairs, and `P` in the internal numbering), allocated the first time that
+// mode runs.
+static int alloc_restore(Graph *g)
+{
+    if (g->d_vo) return BFS_OK;
+    GB_CUDA(cudaMalloc(&g->d_pint, (size_t)g->n * 4));
+    GB_CUDA(cudaMalloc(&g->d_vo, (size_t)g->bitmap_words * 8));
     return BFS_OK;
 }
 
@@ -276,7 +289,8 @@ int bfs_graph_set_option(bfs_graph *gh, int option, int64_t v)
         o.batch_block = (int)v;
         break;
     case BFS_OPT_MODE:
-        if (v != MODE_WARP && v != MODE_BINNED) return bad("MODE must be 0 (warp units) or 1 (degree-binned)");
+        if (v != MODE_WARP && v != MODE_BINNED && v != MODE_RESTORE)
+            return bad("MODE must be 0 (warp units), 1 (degree-binned) or 2 (restoration, no atomics)");
         o.mode = (int)v;
         break;
     default:
@@ -328,13 +342,17 @@ int bfs_run(bfs_graph *gh, int32_t root, int32_t *level_out, int32_t *parent_out
     }
     // one workspace: a run on another stream waits for the previous run
     if (g->ran && s != g->last_stream) GB_CUDA(cudaStreamWaitEvent(s, g->ws_event, 0));
-    if (g->opt.mode == MODE_WARP && g->opt.block == 1024)
-        return set_error(BFS_ERR_INVALID_ARG, "bfs_run: mode 0 takes BLOCK 256 or 512");
+    if (g->opt.mode != MODE_BINNED && g->opt.block == 1024)
+        return set_error(BFS_ERR_INVALID_ARG, "bfs_run: modes 0 and 2 take BLOCK 256 or 512");
     int rc;
     if (g->opt.mode == MODE_BINNED) {
         rc = alloc_binned(g);
         if (rc != BFS_OK) return rc;
         rc = td_launch(g, root, d_level, d_parent, s);
+    } else if (g->opt.mode == MODE_RESTORE) {
+        rc = alloc_restore(g);
+        if (rc != BFS_OK) return rc;
+        rc = td_warp_launch(g, root, d_level, d_parent, s, true);
     } else {
         rc = td_warp_launch(g, root, d_level, d_parent, s);
     }

@@ -49,7 +49,7 @@ struct Ctrl {
 using TdCtrl = Ctrl;
 using UnitCtrl = Ctrl;
 
-enum { MODE_WARP = 0, MODE_BINNED = 1 };
+enum { MODE_WARP = 0, MODE_BINNED = 1, MODE_RESTORE = 2 };
 
 struct Options {
     int block = 512;
@@ -90,6 +90,8 @@ struct Graph {
     int32_t *d_q[2][3] = {};       // binned mode (lazy): small-item queue
     int32_t *d_bq[2][3] = {};      // binned mode (lazy): large-item queue
     int64_t qcap = 0, bqcap = 0;
+    uint2 *d_vo = nullptr;         // restoration mode (lazy): (visited, output) word pairs
+    int32_t *d_pint = nullptr;     // restoration mode (lazy): internal predecessors
     Ctrl *d_ctrl = nullptr;
     int64_t *d_stats = nullptr;    // [kMaxStatLayers][4]: vertices, edges, new, t_end_ns
     int last_grid = 0;
@@ -111,8 +113,11 @@ struct Graph {
 // on first use by graph.cu)
 int td_launch(Graph *g, int32_t root, int32_t *level, int32_t *parent, cudaStream_t s);
 
-// implemented in topdown_warp.cu (warp-private pipelines, the default)
-int td_warp_launch(Graph *g, int32_t root, int32_t *level, int32_t *parent, cudaStream_t s);
+// implemented in topdown_warp.cu (warp-private pipelines, the default; with
+// restore = true the atomic-free variant of Alg. 3, whose workspace graph.cu
+// allocates on first use)
+int td_warp_launch(Graph *g, int32_t root, int32_t *level, int32_t *parent, cudaStream_t s,
+                   bool restore = false);
 int64_t td_hub_capacity(int64_t m);
 
 // implemented in msbfs.cu

@@ -24,7 +24,17 @@
 // queues the winners (pass B).  Descriptors and entries of the next items
 // are prefetched into registers while the current item is processed.
 //
+// Mode 2 (RST) is the atomic-free variant of Alg. 3: pass B sets the bit of
+// the output bitmap with a plain read-modify-write (bits of other vertices in
+// the same word may be lost in a race) and records P[v] = u - n; after the
+// layer's expansion a restoration pass takes every non-zero output word,
+// finds the vertices of its 32 bits with a negative P, restores P[v] += n,
+// sets their visited bits and queues them through the same warp flush.  A
+// race can only drop a bit from a word that the last writer left non-zero,
+// so the pass sees every vertex discovered in the layer (Sec. 3.3.2).
+//
 // All waits are bounded (grid barrier timeout -> ST_TIMEOUT, clean exit).
+#include <climits>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -52,6 +62,8 @@ struct WParams {
     const int32_t *__restrict__ perm;  // caller id -> internal id
     const int32_t *__restrict__ orig;  // internal id -> caller id
     uint32_t *bitmap;
+    uint2 *vo;       // mode 2: (visited, output) bitmap words of Alg. 3, interleaved
+    int32_t *pint;   // mode 2: predecessors in internal numbering (Alg. 3 `P`)
     int32_t *eu[2], *eb[2], *el[2];  // entries [buffer]
     int32_t *us[2], *uc[2];          // units [buffer]
     int32_t *hu[2], *hb[2], *hl[2];  // hub slices [buffer]
@@ -81,6 +93,16 @@ struct CtaSmem {
     unsigned nU, nH;
     unsigned long long st[3];
 };
+
+__device__ __forceinline__ void st_relaxed_u32(uint32_t *p, uint32_t v)
+{
+    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ void st_relaxed_s32(int32_t *p, int32_t v)
+{
+    asm volatile("st.relaxed.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
 
 // A work item as seen by one lane: the lane's entry (if any) and the item's
 // entry count.
@@ -229,6 +251,7 @@ __device__ __forceinline__ void warp_flush(WarpSmem &ws, const WParams &p, int s
     constexpr int PER = OBW / 32;
     const int lane = threadIdx.x & 31;
     const unsigned lt = lanemask_lt();
+    __syncwarp();  // winners were written to ws.wv / ws.wu by other lanes
     const int i0 = min(lane * PER, c), i1 = min(i0 + PER, c);
     int rb[PER], re[PER], ov[PER], ou[PER];
 #pragma unroll
@@ -411,6 +434,7 @@ __device__ __forceinline__ void warp_flush(WarpSmem &ws, const WParams &p, int s
 }
 
 // Passes A and B over the staged item in stage[buf] with `et` edges.
+template <bool RST>
 __device__ __forceinline__ void process_item(WarpSmem &ws, const WParams &p, int buf, int et, int cnt,
                                              int next_level, int set_out, int qo, int &ocnt, unsigned &my_new)
 {
@@ -427,10 +451,23 @@ __device__ __forceinline__ void process_item(WarpSmem &ws, const WParams &p, int
             const int e = base + k * 32 + lane;
             v[k] = e < et ? stg[e] : -1;
         }
+        if (RST) {  // Alg. 3: not in vis and not in out; both words share one 8-byte load
+            // (a stale out word only sends v on to pass B)
 #pragma unroll
-        // L1-cached read: bits are only ever set during a search, so a stale
-        // word can only send an already visited vertex on to the atomicOr
-        for (int k = 0; k < UA; ++k) w[k] = v[k] >= 0 ? __ldca(p.bitmap + ((unsigned)v[k] >> 5)) : 0xffffffffu;
+            for (int k = 0; k < UA; ++k) {
+                if (v[k] >= 0) {
+                    const uint2 x = __ldca(p.vo + ((unsigned)v[k] >> 5));
+                    w[k] = x.x | x.y;
+                } else {
+                    w[k] = 0xffffffffu;
+                }
+            }
+        } else {
+            // L1-cached read: bits are only ever set during a search, so a
+            // stale word can only send an already visited vertex on to the atomicOr
+#pragma unroll
+            for (int k = 0; k < UA; ++k) w[k] = v[k] >= 0 ? __ldca(p.bitmap + ((unsigned)v[k] >> 5)) : 0xffffffffu;
+        }
         __syncwarp();
 #pragma unroll
         for (int k = 0; k < UA; ++k) {
@@ -445,6 +482,49 @@ __device__ __forceinline__ void process_item(WarpSmem &ws, const WParams &p, int
         }
     }
     __syncwarp();
+    if constexpr (RST) {
+        // pass B of Alg. 3: plain read-modify-write of the out word, then
+        // P[v] = u - n.  Lanes whose vertices share a word combine their bits
+        // and the lowest of them writes the word once (rows are sorted, so
+        // neighbouring candidates often share one); races between warps
+        // still lose bits, which the restoration pass repairs.  The (vis, out)
+        // pair is read from L2: vis changes only in the restoration pass, but
+        // an L1 copy may predate the last one.
+        for (int c0 = 0; c0 < nc; c0 += 32 * UB) {
+            int v[UB], e[UB];
+#pragma unroll
+            for (int k = 0; k < UB; ++k) {
+                const int i = c0 + k * 32 + lane;
+                v[k] = i < nc ? stg[i] : -1;
+                e[k] = i < nc ? (int)ws.ce[i] : 0;
+            }
+#pragma unroll
+            for (int k = 0; k < UB; ++k) {
+                const unsigned word = v[k] >= 0 ? ((unsigned)v[k] >> 5) : 0xffffffffu;
+                const unsigned grp = __match_any_sync(FULL, word);
+                const int leader = __ffs(grp) - 1;
+                unsigned long long o = ~0ull;
+                if (v[k] >= 0 && lane == leader)
+                    o = ld_relaxed64(reinterpret_cast<const unsigned long long *>(p.vo + word));
+                o = __shfl_sync(FULL, o, leader);
+                const unsigned bit = v[k] >= 0 ? 1u << (v[k] & 31) : 0u;
+                const unsigned vis_w = (unsigned)o, out_w = (unsigned)(o >> 32);
+                const bool need = v[k] >= 0 && !((vis_w | out_w) & bit);
+                const unsigned bits = __reduce_or_sync(grp, need ? bit : 0u);
+                if (lane == leader && bits) st_relaxed_u32(&p.vo[word].y, out_w | bits);
+                if (need) {
+                    int lo = 0, hi = cnt;  // source entry: largest j with off[j] <= e
+                    while (hi - lo > 1) {
+                        const int mid = (lo + hi) >> 1;
+                        if (ws.off[buf][mid] <= e[k]) lo = mid;
+                        else hi = mid;
+                    }
+                    st_relaxed_s32(p.pint + v[k], ws.iu[buf][lo] - p.n);
+                }
+            }
+        }
+        __syncwarp();
+    } else {
     // pass B: claim with atomicOr; each winner is queued with its source
     for (int c0 = 0; c0 < nc; c0 += 32 * UB) {
         // room for a whole batch of winners, flushed outside the claim loop
@@ -488,9 +568,10 @@ __device__ __forceinline__ void process_item(WarpSmem &ws, const WParams &p, int
         }
     }
     __syncwarp();
+    }
 }
 
-template <int WPB>
+template <int WPB, bool RST>
 __global__ void __launch_bounds__(WPB * 32, (24 / WPB) > 0 ? (24 / WPB) : 1) td_warp_kernel(WParams p)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -506,15 +587,19 @@ __global__ void __launch_bounds__(WPB * 32, (24 / WPB) > 0 ? (24 / WPB) : 1) td_
     // ---- initialisation (Alg. 1: P = infinity except P[s] = s; vis = {s}) --
     {
         const int64_t stride = (int64_t)G * WPB * 32;
+        const int rint = __ldg(p.perm + p.root);  // the root in internal numbering
         for (int64_t i = (int64_t)blockIdx.x * WPB * 32 + tid; i < p.n; i += stride) {
             const bool is_root = (i == p.root);
             p.level[i] = is_root ? 0 : -1;
             if (p.parent) p.parent[i] = is_root ? p.root : -1;
+            if (RST) p.pint[i] = (i == rint) ? rint : INT_MAX;  // Alg. 3: P = infinity, P[s] = s
         }
-        const int rint = __ldg(p.perm + p.root);  // the root in internal numbering
         const int rw = rint >> 5;
-        for (int64_t w = (int64_t)blockIdx.x * WPB * 32 + tid; w < p.bitmap_words; w += stride)
-            p.bitmap[w] = (w == rw) ? (1u << (rint & 31)) : 0u;
+        for (int64_t w = (int64_t)blockIdx.x * WPB * 32 + tid; w < p.bitmap_words; w += stride) {
+            const uint32_t b0 = (w == rw) ? (1u << (rint & 31)) : 0u;
+            p.bitmap[w] = b0;
+            if (RST) p.vo[w] = make_uint2(b0, 0u);
+        }
         if (blockIdx.x == 0) {
             if (p.stats)
                 for (int i = tid; i < 4 * kMaxStatLayers; i += WPB * 32) p.stats[i] = 0;
@@ -595,7 +680,7 @@ __global__ void __launch_bounds__(WPB * 32, (24 / WPB) > 0 ? (24 / WPB) : 1) td_
             asm volatile("cp.async.wait_group 1;" ::: "memory");
             __syncwarp();
             if (lane == 0) my_edges += (unsigned long long)et_cur;
-            process_item(ws, p, buf, et_cur, cnt_cur, next_level, set_out, qo, ocnt, my_new);
+            process_item<RST>(ws, p, buf, et_cur, cnt_cur, next_level, set_out, qo, ocnt, my_new);
             buf ^= 1;
             id = id1;
             et_cur = et_nxt;
@@ -607,6 +692,52 @@ __global__ void __launch_bounds__(WPB * 32, (24 / WPB) > 0 ? (24 / WPB) : 1) td_
         cp_async_wait_all();
         __syncwarp();
         if (ocnt > 0) warp_flush(ws, p, set_out, qo, ocnt, next_level);
+
+        if (RST) {
+            // restoration (Alg. 3), once every racy set of the layer is done:
+            // each non-zero out word is owned by one warp, which restores the
+            // vertices of its bits with P < 0, sets their visited bits, clears
+            // the word and queues them as the next frontier
+            ok = grid_sync(&c->bar_count, &c->bar_gen, &c->status, G, p.timeout_ns, &cs.ok);
+            if (!ok) break;
+            const unsigned lt = lanemask_lt();
+            const int64_t nwords = p.bitmap_words;
+            // words are dealt round-robin to the warps (word gw + GW * j), so
+            // the dense low words of the degree order are spread over all of them
+            for (int64_t j0 = 0; (int64_t)gw + GW * j0 < nwords; j0 += 32) {
+                const int64_t wi = (int64_t)gw + GW * (j0 + lane);
+                const uint2 x = wi < nwords ? __ldcg(p.vo + wi) : make_uint2(0u, 0u);
+                unsigned nz = __ballot_sync(FULL, x.y != 0u);
+                while (nz) {
+                    const int src = __ffs(nz) - 1;
+                    nz &= nz - 1;
+                    if (ocnt > OBW - 32) {
+                        warp_flush(ws, p, set_out, qo, ocnt, next_level);
+                        ocnt = 0;
+                    }
+                    const int64_t word = (int64_t)gw + GW * (j0 + src);
+                    const int64_t v = word * 32 + lane;
+                    const int pv = v < p.n ? __ldcg(p.pint + v) : 0;
+                    const bool neg = pv < 0;
+                    const unsigned m = __ballot_sync(FULL, neg);
+                    if (neg) {
+                        const int u = pv + p.n;
+                        p.pint[v] = u;
+                        const int pos = ocnt + __popc(m & lt);
+                        ws.wv[pos] = (int)v;
+                        ws.wu[pos] = u;
+                    }
+                    if (lane == src) {  // the lane that read the pair owns the word
+                        p.vo[word] = make_uint2(x.x | m, 0u);
+                        p.bitmap[word] = x.x | m;  // the plain visited bitmap, for export
+                    }
+                    ocnt += __popc(m);
+                    if (lane == 0) my_new += (unsigned)__popc(m);
+                }
+            }
+            if (ocnt > 0) warp_flush(ws, p, set_out, qo, ocnt, next_level);
+            ocnt = 0;
+        }
 
         if (p.stats && d < kMaxStatLayers) {
             unsigned long long a = my_vertices, e = my_edges, t = my_new;
@@ -650,10 +781,10 @@ __global__ void __launch_bounds__(WPB * 32, (24 / WPB) > 0 ? (24 / WPB) : 1) td_
     }
 }
 
-template <int WPB>
+template <int WPB, bool RST>
 int launch(Graph *g, const WParams &prm, cudaStream_t s)
 {
-    auto kern = td_warp_kernel<WPB>;
+    auto kern = td_warp_kernel<WPB, RST>;
     const int smem = (int)sizeof(CtaSmem<WPB>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute(td_warp_kernel)");
@@ -678,8 +809,10 @@ int launch(Graph *g, const WParams &prm, cudaStream_t s)
 // slices, so a layer has at most 2m/W of them (+2).
 int64_t td_hub_capacity(int64_t m) { return 2 * (m / W) + 2; }
 
-int td_warp_launch(Graph *g, int32_t root, int32_t *level, int32_t *parent, cudaStream_t s)
+int td_warp_launch(Graph *g, int32_t root, int32_t *level, int32_t *parent, cudaStream_t s, bool restore)
 {
+    if (restore && (!g->d_vo || !g->d_pint))
+        return set_error(BFS_ERR_INVALID_ARG, "mode 2: restoration workspace not allocated");
     WParams p;
     p.ro = g->d_row_offsets;
     p.col = g->d_col_idx;
@@ -688,6 +821,8 @@ int td_warp_launch(Graph *g, int32_t root, int32_t *level, int32_t *parent, cuda
     p.perm = g->d_perm;
     p.orig = g->d_orig;
     p.bitmap = g->d_bitmap;
+    p.vo = restore ? g->d_vo : nullptr;
+    p.pint = restore ? g->d_pint : nullptr;
     for (int b = 0; b < 2; ++b) {
         p.eu[b] = g->d_eq[b][0];
         p.eb[b] = g->d_eq[b][1];
@@ -708,8 +843,8 @@ int td_warp_launch(Graph *g, int32_t root, int32_t *level, int32_t *parent, cuda
     p.bitmap_words = (int32_t)g->bitmap_words;
     p.timeout_ns = (uint64_t)g->opt.timeout_ns;
     switch (g->opt.block) {
-    case 256: return launch<8>(g, p, s);
-    case 512: return launch<16>(g, p, s);
+    case 256: return restore ? launch<8, true>(g, p, s) : launch<8, false>(g, p, s);
+    case 512: return restore ? launch<16, true>(g, p, s) : launch<16, false>(g, p, s);
     default: return set_error(BFS_ERR_INVALID_ARG, "warp mode supports BLOCK 256 or 512");
     }
 }
