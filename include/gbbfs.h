@@ -79,7 +79,7 @@ typedef enum {
     BFS_OPT_MAX_CTAS = 8,       /* cap on the persistent grid size (0 = no cap)        */
     BFS_OPT_BATCH_WIDTH = 9,    /* sources per bit-parallel batch: 8..64, multiple of 8 */
     BFS_OPT_BATCH_BLOCK = 10,   /* threads per CTA of the batched kernels: 256 or 512   */
-    BFS_OPT_MODE = 11           /* expansion of bfs_run: 0 = work items bounded in edges
+    BFS_OPT_MODE = 11,          /* expansion of bfs_run: 0 = work items bounded in edges
                                    (short lists packed into units, hubs cut into slices)
                                    run by independent warps, BLOCK 256 or 512 (default);
                                    1 = one item per frontier vertex, binned by degree
@@ -88,8 +88,20 @@ typedef enum {
                                    by plain read-modify-writes and P[v] = u - n, then
                                    a restoration pass per layer repairs both bitmaps
                                    and P (Sec. 3.3.2, Alg. 3); BLOCK 256 or 512.  Its
-                                   workspace (4n bytes + one bitmap) is allocated on
-                                   the first run in this mode                          */
+                                   workspace (4n bytes + two bitmaps) is allocated on
+                                   the first run in this mode;
+                                   3 = direction-optimising: layers run as in mode 0
+                                   or bottom-up (every unvisited vertex looks for a
+                                   parent in the frontier bitmap), chosen per layer by
+                                   ALPHA and BETA; bottom-up only on graphs where every
+                                   edge (u, v) has its reverse (checked at creation),
+                                   else every layer is top-down; BLOCK 256 or 512;
+                                   2 bitmaps of workspace, allocated on first use      */
+    BFS_OPT_ALPHA = 12,         /* mode 3: a layer runs bottom-up once the frontier's
+                                   summed degree exceeds (edges of unreached vertices)
+                                   / ALPHA (0 .. 2^30, default 14; 0 = never)          */
+    BFS_OPT_BETA = 13           /* mode 3: back to top-down once the frontier has fewer
+                                   than n / BETA vertices (1 .. 2^30, default 24)       */
 } bfs_option;
 
 /* ---- library ------------------------------------------------------------ */

@@ -44,7 +44,9 @@ BFS_OPT_MAX_CTAS = 8
 BFS_OPT_BATCH_WIDTH = 9
 BFS_OPT_BATCH_BLOCK = 10
 BFS_OPT_MODE = 11
-MODE_WARP, MODE_BINNED, MODE_RESTORE = 0, 1, 2
+BFS_OPT_ALPHA = 12
+BFS_OPT_BETA = 13
+MODE_WARP, MODE_BINNED, MODE_RESTORE, MODE_HYBRID = 0, 1, 2, 3
 
 OPTION_NAMES = {
     "block": BFS_OPT_BLOCK, "ctas_per_sm": BFS_OPT_CTAS_PER_SM,
@@ -53,6 +55,8 @@ OPTION_NAMES = {
     "layer_stats": BFS_OPT_LAYER_STATS, "max_ctas": BFS_OPT_MAX_CTAS,
     "batch_width": BFS_OPT_BATCH_WIDTH, "batch_block": BFS_OPT_BATCH_BLOCK,
     "mode": BFS_OPT_MODE,
+    "alpha": BFS_OPT_ALPHA,
+    "beta": BFS_OPT_BETA,
 }
 
 # every symbol include/gbbfs.h declares, with (restype, argtypes)

@@ -85,6 +85,8 @@ static void free_graph(Graph *g)
         for (int j = 0; j < 2; ++j) cudaFree(g->d_uq[b][j]);
     }
     cudaFree(g->d_vo);
+    cudaFree(g->d_front[0]);
+    cudaFree(g->d_front[1]);
     cudaFree(g->d_pint);
     cudaFree(g->d_ctrl);
     cudaFree(g->d_stats);
@@ -122,6 +124,15 @@ static int alloc_restore(Graph *g)
     if (g->d_vo) return BFS_OK;
     GB_CUDA(cudaMalloc(&g->d_pint, (size_t)g->n * 4));
     GB_CUDA(cudaMalloc(&g->d_vo, (size_t)g->bitmap_words * 8));
+    return BFS_OK;
+}
+
+// Hybrid-mode frontier bitmaps (bottom-up layers), allocated the first time
+// that mode runs.
+static int alloc_hybrid(Graph *g)
+{
+    if (g->d_front[0]) return BFS_OK;
+    for (int b = 0; b < 2; ++b) GB_CUDA(cudaMalloc(&g->d_front[b], (size_t)g->bitmap_words * 4));
     return BFS_OK;
 }
 
@@ -289,9 +300,18 @@ int bfs_graph_set_option(bfs_graph *gh, int option, int64_t v)
         o.batch_block = (int)v;
         break;
     case BFS_OPT_MODE:
-        if (v != MODE_WARP && v != MODE_BINNED && v != MODE_RESTORE)
-            return bad("MODE must be 0 (warp units), 1 (degree-binned) or 2 (restoration, no atomics)");
+        if (v != MODE_WARP && v != MODE_BINNED && v != MODE_RESTORE && v != MODE_HYBRID)
+            return bad("MODE must be 0 (warp units), 1 (degree-binned), 2 (restoration, no atomics) "
+                       "or 3 (direction-optimising)");
         o.mode = (int)v;
+        break;
+    case BFS_OPT_ALPHA:
+        if (v < 0 || v > (1 << 30)) return bad("ALPHA must be in [0, 2^30] (0: top-down only)");
+        o.alpha = (int)v;
+        break;
+    case BFS_OPT_BETA:
+        if (v < 1 || v > (1 << 30)) return bad("BETA must be in [1, 2^30]");
+        o.beta = (int)v;
         break;
     default:
         return bad("unknown option");
@@ -315,6 +335,8 @@ int64_t bfs_graph_get_option(const bfs_graph *gh, int option)
     case BFS_OPT_BATCH_WIDTH: return o.batch_width;
     case BFS_OPT_BATCH_BLOCK: return o.batch_block;
     case BFS_OPT_MODE: return o.mode;
+    case BFS_OPT_ALPHA: return o.alpha;
+    case BFS_OPT_BETA: return o.beta;
     default: return set_error(BFS_ERR_INVALID_ARG, "bfs_graph_get_option: unknown option");
     }
 }
@@ -343,7 +365,7 @@ int bfs_run(bfs_graph *gh, int32_t root, int32_t *level_out, int32_t *parent_out
     // one workspace: a run on another stream waits for the previous run
     if (g->ran && s != g->last_stream) GB_CUDA(cudaStreamWaitEvent(s, g->ws_event, 0));
     if (g->opt.mode != MODE_BINNED && g->opt.block == 1024)
-        return set_error(BFS_ERR_INVALID_ARG, "bfs_run: modes 0 and 2 take BLOCK 256 or 512");
+        return set_error(BFS_ERR_INVALID_ARG, "bfs_run: modes 0, 2 and 3 take BLOCK 256 or 512");
     int rc;
     if (g->opt.mode == MODE_BINNED) {
         rc = alloc_binned(g);
@@ -352,7 +374,11 @@ int bfs_run(bfs_graph *gh, int32_t root, int32_t *level_out, int32_t *parent_out
     } else if (g->opt.mode == MODE_RESTORE) {
         rc = alloc_restore(g);
         if (rc != BFS_OK) return rc;
-        rc = td_warp_launch(g, root, d_level, d_parent, s, true);
+        rc = td_warp_launch(g, root, d_level, d_parent, s, MODE_RESTORE);
+    } else if (g->opt.mode == MODE_HYBRID) {
+        rc = alloc_hybrid(g);
+        if (rc != BFS_OK) return rc;
+        rc = td_warp_launch(g, root, d_level, d_parent, s, MODE_HYBRID);
     } else {
         rc = td_warp_launch(g, root, d_level, d_parent, s);
     }

@@ -35,6 +35,8 @@ enum : unsigned {
 // The last CTA to leave a search returns every counter to zero.
 struct Ctrl {
     unsigned long long eu_count[3];  // warp mode: (units << 32) | entries
+    unsigned long long nf[3];        // hybrid mode: frontier vertices of a layer
+    unsigned long long mf[3];        // hybrid mode: their summed degrees
     unsigned hub_count[3];           // warp mode: hub slices
     unsigned work[3];                // work-item dispenser (both modes)
     unsigned count[3];               // binned mode: small-item queue size
@@ -49,7 +51,7 @@ struct Ctrl {
 using TdCtrl = Ctrl;
 using UnitCtrl = Ctrl;
 
-enum { MODE_WARP = 0, MODE_BINNED = 1, MODE_RESTORE = 2 };
+enum { MODE_WARP = 0, MODE_BINNED = 1, MODE_RESTORE = 2, MODE_HYBRID = 3 };
 
 struct Options {
     int block = 512;
@@ -63,6 +65,8 @@ struct Options {
     int batch_width = 64;
     int batch_block = 512;
     int mode = MODE_WARP;
+    int alpha = 14;  // hybrid: go bottom-up when frontier edges > unexplored edges / alpha
+    int beta = 24;   // hybrid: back to top-down when frontier vertices < n / beta
 };
 
 constexpr int kMaxStatLayers = 256;
@@ -91,6 +95,7 @@ struct Graph {
     int32_t *d_bq[2][3] = {};      // binned mode (lazy): large-item queue
     int64_t qcap = 0, bqcap = 0;
     uint2 *d_vo = nullptr;         // restoration mode (lazy): (visited, output) word pairs
+    uint32_t *d_front[2] = {};     // hybrid mode (lazy): frontier bitmaps of bottom-up layers
     int32_t *d_pint = nullptr;     // restoration mode (lazy): internal predecessors
     Ctrl *d_ctrl = nullptr;
     int64_t *d_stats = nullptr;    // [kMaxStatLayers][4]: vertices, edges, new, t_end_ns
@@ -113,11 +118,11 @@ struct Graph {
 // on first use by graph.cu)
 int td_launch(Graph *g, int32_t root, int32_t *level, int32_t *parent, cudaStream_t s);
 
-// implemented in topdown_warp.cu (warp-private pipelines, the default; with
-// restore = true the atomic-free variant of Alg. 3, whose workspace graph.cu
-// allocates on first use)
+// implemented in topdown_warp.cu (warp-private pipelines, the default;
+// MODE_RESTORE is the atomic-free variant of Alg. 3 and MODE_HYBRID the
+// direction-optimising search, whose workspaces graph.cu allocates on first use)
 int td_warp_launch(Graph *g, int32_t root, int32_t *level, int32_t *parent, cudaStream_t s,
-                   bool restore = false);
+                   int mode = MODE_WARP);
 int64_t td_hub_capacity(int64_t m);
 
 // implemented in msbfs.cu

@@ -33,6 +33,15 @@
 // race can only drop a bit from a word that the last writer left non-zero,
 // so the pass sees every vertex discovered in the layer (Sec. 3.3.2).
 //
+// Mode 3 (HYB) is the direction-optimising search (bottom-up steps of the
+// related work named in Sec. 2; future work in Sec. 8) on graphs whose every
+// edge has its reverse: a layer runs bottom-up once the frontier's edges
+// exceed the unexplored edges / alpha, and top-down again once the frontier
+// has fewer than n / beta vertices.  In a bottom-up layer each warp owns
+// whole visited words (dealt round-robin); every unvisited vertex scans its
+// row (sorted, so hubs come first) until it meets a vertex of the frontier
+// bitmap, whose low (hub) words sit in the CTA's shared memory.
+//
 // All waits are bounded (grid barrier timeout -> ST_TIMEOUT, clean exit).
 #include <climits>
 #include <cuda_runtime.h>
@@ -53,6 +62,10 @@ constexpr int MAXI = 2 * W;  // edges of one work item are < MAXI
 constexpr int OBW = 128;     // out-buffer entries per warp
 constexpr int UA = 8;        // pass A: visited-word loads per lane in flight
 constexpr int UB = 2;        // pass B: claims per lane in flight
+constexpr int VW = 4;        // bottom-up: visited words per warp in flight
+
+enum { KM_ATOMIC = 0, KM_RESTORE = 1, KM_HYBRID = 2 };  // kernel variants
+enum { FL_LP = 1, FL_CNT = 2 };  // warp_flush: write level/parent; count frontier size and edges
 
 struct WParams {
     const int32_t *__restrict__ ro;
@@ -63,6 +76,7 @@ struct WParams {
     const int32_t *__restrict__ orig;  // internal id -> caller id
     uint32_t *bitmap;
     uint2 *vo;       // mode 2: (visited, output) bitmap words of Alg. 3, interleaved
+    uint32_t *front[2];  // mode 3: frontier bitmaps of bottom-up layers [layer parity]
     int32_t *pint;   // mode 2: predecessors in internal numbering (Alg. 3 `P`)
     int32_t *eu[2], *eb[2], *el[2];  // entries [buffer]
     int32_t *us[2], *uc[2];          // units [buffer]
@@ -71,6 +85,11 @@ struct WParams {
     int64_t *stats;  // [kMaxStatLayers][4] or null
     int32_t n;
     int32_t root;
+    int64_t m;            // directed entries (sum of degrees)
+    int32_t split32;      // internal ids below have degree >= 32
+    int32_t n_nonzero;    // internal ids below have degree >= 1
+    int32_t alpha, beta;  // mode 3 switching parameters
+    int32_t symmetric;    // mode 3 goes bottom-up only if every edge has its reverse
     uint32_t ecap, ucap, hcap;
     int32_t bitmap_words;
     uint64_t timeout_ns;
@@ -90,8 +109,9 @@ template <int WPB>
 struct CtaSmem {
     WarpSmem w[WPB];
     int ok;
-    unsigned nU, nH;
+    unsigned nU, nH, nE;
     unsigned long long st[3];
+    unsigned long long hnf, hmf;  // mode 3: size and edges of this layer's frontier
 };
 
 __device__ __forceinline__ void st_relaxed_u32(uint32_t *p, uint32_t v)
@@ -245,6 +265,7 @@ __device__ __forceinline__ int stage_item(WarpSmem &ws, const WParams &p, const 
 // caller's numbering), read each one's adjacency range, queue the short
 // ones as frontier entries cut into units and the hubs as slices.  All loads
 // of a lane are issued together, so one flush costs about one round trip.
+template <int FL>
 __device__ __forceinline__ void warp_flush(WarpSmem &ws, const WParams &p, int set_out, int qo, int c,
                                         int next_level)
 {
@@ -261,18 +282,22 @@ __device__ __forceinline__ void warp_flush(WarpSmem &ws, const WParams &p, int s
             const int v = ws.wv[i];
             rb[k] = __ldg(p.ro + v);
             re[k] = __ldg(p.ro + v + 1);
-            ov[k] = __ldg(p.orig + v);
-            ou[k] = p.parent ? __ldg(p.orig + ws.wu[i]) : 0;
+            ov[k] = (FL & FL_LP) ? __ldg(p.orig + v) : 0;
+            ou[k] = ((FL & FL_LP) && p.parent) ? __ldg(p.orig + ws.wu[i]) : 0;
         }
     }
     int nsmall = 0, nslice = 0;
+    long long esum = 0;
 #pragma unroll
     for (int k = 0; k < PER; ++k) {
         const int i = i0 + k;
         if (i < i1) {
-            p.level[ov[k]] = next_level;
-            if (p.parent) p.parent[ov[k]] = ou[k];
+            if (FL & FL_LP) {
+                p.level[ov[k]] = next_level;
+                if (p.parent) p.parent[ov[k]] = ou[k];
+            }
             const int len = re[k] - rb[k];
+            esum += len;
             nsmall += (len >= 1 && len <= W);
             nslice += (len > W) ? (len + W - 1) / W : 0;
         }
@@ -290,6 +315,14 @@ __device__ __forceinline__ void warp_flush(WarpSmem &ws, const WParams &p, int s
     }
     const int cs = __shfl_sync(FULL, sinc, 31);
     const int total_slices = __shfl_sync(FULL, hinc, 31);
+    if (FL & FL_CNT) {  // the next frontier's size and summed degrees
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) esum += __shfl_down_sync(FULL, esum, o);
+        if (lane == 0) {
+            atomicAdd(&p.ctrl->nf[set_out], (unsigned long long)c);
+            atomicAdd(&p.ctrl->mf[set_out], (unsigned long long)esum);
+        }
+    }
     unsigned hbase = 0;
     if (lane == 0 && total_slices > 0) hbase = atomicAdd(&p.ctrl->hub_count[set_out], (unsigned)total_slices);
     hbase = __shfl_sync(FULL, hbase, 0);
@@ -434,7 +467,7 @@ __device__ __forceinline__ void warp_flush(WarpSmem &ws, const WParams &p, int s
 }
 
 // Passes A and B over the staged item in stage[buf] with `et` edges.
-template <bool RST>
+template <int KM>
 __device__ __forceinline__ void process_item(WarpSmem &ws, const WParams &p, int buf, int et, int cnt,
                                              int next_level, int set_out, int qo, int &ocnt, unsigned &my_new)
 {
@@ -451,7 +484,7 @@ __device__ __forceinline__ void process_item(WarpSmem &ws, const WParams &p, int
             const int e = base + k * 32 + lane;
             v[k] = e < et ? stg[e] : -1;
         }
-        if (RST) {  // Alg. 3: not in vis and not in out; both words share one 8-byte load
+        if (KM == KM_RESTORE) {  // Alg. 3: not in vis and not in out; both words share one 8-byte load
             // (a stale out word only sends v on to pass B)
 #pragma unroll
             for (int k = 0; k < UA; ++k) {
@@ -482,7 +515,7 @@ __device__ __forceinline__ void process_item(WarpSmem &ws, const WParams &p, int
         }
     }
     __syncwarp();
-    if constexpr (RST) {
+    if constexpr (KM == KM_RESTORE) {
         // pass B of Alg. 3: plain read-modify-write of the out word, then
         // P[v] = u - n.  Lanes whose vertices share a word combine their bits
         // and the lowest of them writes the word once (rows are sorted, so
@@ -529,7 +562,7 @@ __device__ __forceinline__ void process_item(WarpSmem &ws, const WParams &p, int
     for (int c0 = 0; c0 < nc; c0 += 32 * UB) {
         // room for a whole batch of winners, flushed outside the claim loop
         if (ocnt > OBW - 32 * UB) {
-            warp_flush(ws, p, set_out, qo, ocnt, next_level);
+            warp_flush<KM == KM_HYBRID ? (FL_LP | FL_CNT) : FL_LP>(ws, p, set_out, qo, ocnt, next_level);
             ocnt = 0;
         }
         int v[UB], e[UB];
@@ -571,7 +604,206 @@ __device__ __forceinline__ void process_item(WarpSmem &ws, const WParams &p, int
     }
 }
 
-template <int WPB, bool RST>
+// ---- direction-optimising mode (KM_HYBRID) ---------------------------------
+
+// Is u in the frontier bitmap F?  Its first `ncache` words are in shared memory.
+__device__ __forceinline__ bool in_front(const uint32_t *sF, int ncache, const uint32_t *__restrict__ F, int u)
+{
+    const unsigned wd = (unsigned)u >> 5;
+    const unsigned x = (int)wd < ncache ? sF[wd] : __ldcg(F + wd);
+    return (x >> (u & 31)) & 1u;
+}
+
+// Top-down -> bottom-up: set the bit of every vertex of the frontier queue
+// (entries and hub slices of buffer qi) in the cleared bitmap F.
+__device__ __forceinline__ void queue_to_bitmap(const WParams &p, int qi, unsigned nE, unsigned nH, uint32_t *F)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (int64_t i = t0; i < nE; i += stride) {
+        const int u = __ldcg(p.eu[qi] + i);
+        atomicOr(F + ((unsigned)u >> 5), 1u << (u & 31));
+    }
+    for (int64_t i = t0; i < nH; i += stride) {
+        const int u = __ldcg(p.hu[qi] + i);
+        atomicOr(F + ((unsigned)u >> 5), 1u << (u & 31));
+    }
+}
+
+// Bottom-up -> top-down: queue the vertices of bitmap F as frontier entries
+// and hub slices (buffer qi, counter set si); their levels and parents were
+// written by the bottom-up layer that found them.  Words are dealt
+// round-robin to the warps.
+__device__ __forceinline__ void bitmap_to_queue(WarpSmem &ws, const WParams &p, const uint32_t *F, int si, int qi,
+                                                unsigned gw, unsigned GW)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = lanemask_lt();
+    const int64_t nwords = p.bitmap_words;
+    int ocnt = 0;
+    for (int64_t j0 = 0; (int64_t)gw + (int64_t)GW * j0 < nwords; j0 += 32) {
+        const int64_t wi = (int64_t)gw + (int64_t)GW * (j0 + lane);
+        const unsigned x = wi < nwords ? __ldcg(F + wi) : 0u;
+        unsigned nz = __ballot_sync(FULL, x != 0u);
+        while (nz) {
+            const int src = __ffs(nz) - 1;
+            nz &= nz - 1;
+            if (ocnt > OBW - 32) {
+                warp_flush<0>(ws, p, si, qi, ocnt, 0);
+                ocnt = 0;
+            }
+            const unsigned m = __shfl_sync(FULL, x, src);
+            const int64_t word = (int64_t)gw + (int64_t)GW * (j0 + src);
+            if ((m >> lane) & 1u) ws.wv[ocnt + __popc(m & lt)] = (int)(word * 32 + lane);
+            ocnt += __popc(m);
+        }
+    }
+    if (ocnt > 0) warp_flush<0>(ws, p, si, qi, ocnt, 0);
+}
+
+// One bottom-up layer: every unvisited vertex looks for a neighbour in the
+// frontier bitmap F; the first one found is its parent.  A warp owns the
+// visited words it is dealt (word gw + GW * j), so their bits and the words
+// of the next frontier Fn are written without atomics.  Each lane loads one
+// of 32 dealt words; words without an unvisited vertex only clear their Fn
+// word, the others are taken VW at a time: every unvisited vertex probes its
+// own list in its lane, PK edges per step (rows are sorted, so the hubs come
+// first), a vertex of degree < 32 to the end, one of degree >= 32 for its
+// first PK edges, after which the whole warp scans the rest, 32 per step.
+template <int WPB>
+__device__ __forceinline__ void bottom_up(CtaSmem<WPB> &cs, const WParams &p, const uint32_t *__restrict__ F,
+                                          uint32_t *Fn, int next_level, unsigned gw, unsigned GW,
+                                          unsigned long long &my_new, unsigned long long &my_edges,
+                                          unsigned long long &my_mf)
+{
+    constexpr int PK = 4;
+    const int tid = threadIdx.x, lane = tid & 31;
+    uint32_t *sF = reinterpret_cast<uint32_t *>(cs.w);  // the top-down buffers are idle here
+    constexpr int CW = (int)(sizeof(WarpSmem) * WPB / 4);
+    const int64_t nwords = p.bitmap_words;
+    const int ncache = (int)min((int64_t)CW, nwords);
+    __syncthreads();
+    for (int i = tid; i < ncache; i += WPB * 32) sF[i] = __ldcg(F + i);
+    __syncthreads();
+    for (int64_t j0 = 0; (int64_t)gw + (int64_t)GW * j0 < nwords; j0 += 32) {
+        const int64_t lw = (int64_t)gw + (int64_t)GW * (j0 + lane);  // this lane's word
+        unsigned lraw = 0xffffffffu, lseen = 0xffffffffu;  // visited bits; + vertices without edges
+        bool has = false;
+        if (lw < nwords) {
+            lraw = __ldcg(p.bitmap + lw);
+            const int64_t first = lw * 32;  // vertices >= n_nonzero have no edge: never reached
+            const unsigned valid = first >= p.n_nonzero ? 0u
+                                   : (p.n_nonzero - first >= 32 ? 0xffffffffu
+                                                                : (1u << (p.n_nonzero - first)) - 1u);
+            lseen = lraw | ~valid;
+            has = lseen != 0xffffffffu;
+            if (!has) Fn[lw] = 0u;
+        }
+        unsigned work = __ballot_sync(FULL, has);
+        while (work) {
+            int64_t v[VW];
+            unsigned vis[VW];
+            int src[VW], beg[VW], end[VW], par[VW], e[VW];
+            bool unv[VW];
+#pragma unroll
+            for (int j = 0; j < VW; ++j) {
+                src[j] = work ? __ffs(work) - 1 : -1;
+                if (work) work &= work - 1;
+                const int sl = src[j] < 0 ? 0 : src[j];
+                const unsigned seen = __shfl_sync(FULL, lseen, sl);
+                vis[j] = __shfl_sync(FULL, lraw, sl);
+                v[j] = ((int64_t)gw + (int64_t)GW * (j0 + sl)) * 32 + lane;
+                unv[j] = src[j] >= 0 && !((seen >> lane) & 1u);
+            }
+#pragma unroll
+            for (int j = 0; j < VW; ++j) {
+                beg[j] = unv[j] ? __ldg(p.ro + v[j]) : 0;
+                end[j] = unv[j] ? __ldg(p.ro + v[j] + 1) : 0;
+                par[j] = -1;
+                e[j] = beg[j];
+            }
+            // every unvisited vertex in its own lane, PK edges per step
+            while (true) {
+                bool act[VW], any = false;
+#pragma unroll
+                for (int j = 0; j < VW; ++j) {
+                    act[j] = par[j] < 0 && e[j] < end[j] && (v[j] >= p.split32 || e[j] == beg[j]);
+                    any |= act[j];
+                }
+                if (!__any_sync(FULL, any)) break;
+                int u[VW][PK];
+                bool f[VW][PK];
+#pragma unroll
+                for (int j = 0; j < VW; ++j)
+#pragma unroll
+                    for (int t = 0; t < PK; ++t)
+                        u[j][t] = (act[j] && e[j] + t < end[j]) ? __ldg(p.col + e[j] + t) : -1;
+#pragma unroll
+                for (int j = 0; j < VW; ++j)
+#pragma unroll
+                    for (int t = 0; t < PK; ++t) f[j][t] = u[j][t] >= 0 && in_front(sF, ncache, F, u[j][t]);
+#pragma unroll
+                for (int j = 0; j < VW; ++j) {
+                    if (!act[j]) continue;
+#pragma unroll
+                    for (int t = PK - 1; t >= 0; --t)
+                        if (f[j][t]) par[j] = u[j][t];  // the first of the step
+                    my_edges += (unsigned long long)min(PK, end[j] - e[j]);
+                    e[j] += PK;
+                }
+            }
+            // degree >= 32 and not found yet: the warp scans the rest of one list at a time
+#pragma unroll
+            for (int j = 0; j < VW; ++j) {
+                unsigned hv = __ballot_sync(FULL, par[j] < 0 && e[j] < end[j]);
+                while (hv) {
+                    const int hl = __ffs(hv) - 1;
+                    hv &= hv - 1;
+                    const int hb = __shfl_sync(FULL, e[j], hl), he = __shfl_sync(FULL, end[j], hl);
+                    int found = -1;
+                    for (int e0 = hb; e0 < he; e0 += 32) {
+                        const int ee = e0 + lane;
+                        const int u = ee < he ? __ldg(p.col + ee) : -1;
+                        const bool f = u >= 0 && in_front(sF, ncache, F, u);
+                        const unsigned m = __ballot_sync(FULL, f);
+                        if (lane == 0) my_edges += (unsigned long long)min(32, he - e0);
+                        if (m) {
+                            found = __shfl_sync(FULL, u, __ffs(m) - 1);
+                            break;
+                        }
+                    }
+                    if (lane == hl) par[j] = found;
+                }
+            }
+            // the vertices found: level, parent, visited bits, next frontier
+            int ov[VW], ou[VW];
+#pragma unroll
+            for (int j = 0; j < VW; ++j) {
+                ov[j] = par[j] >= 0 ? __ldg(p.orig + v[j]) : 0;
+                ou[j] = (par[j] >= 0 && p.parent) ? __ldg(p.orig + par[j]) : 0;
+            }
+#pragma unroll
+            for (int j = 0; j < VW; ++j) {
+                const bool found = par[j] >= 0;
+                const unsigned m = __ballot_sync(FULL, found);
+                if (found) {
+                    p.level[ov[j]] = next_level;
+                    if (p.parent) p.parent[ov[j]] = ou[j];
+                    my_mf += (unsigned long long)(end[j] - beg[j]);
+                }
+                if (lane == 0 && src[j] >= 0) {
+                    const int64_t w = (int64_t)gw + (int64_t)GW * (j0 + src[j]);
+                    Fn[w] = m;
+                    if (m) p.bitmap[w] = vis[j] | m;
+                    my_new += (unsigned long long)__popc(m);
+                }
+            }
+        }
+    }
+    __syncthreads();  // the shared buffers go back to the top-down layers
+}
+
+template <int WPB, int KM>
 __global__ void __launch_bounds__(WPB * 32, (24 / WPB) > 0 ? (24 / WPB) : 1) td_warp_kernel(WParams p)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -592,13 +824,13 @@ __global__ void __launch_bounds__(WPB * 32, (24 / WPB) > 0 ? (24 / WPB) : 1) td_
             const bool is_root = (i == p.root);
             p.level[i] = is_root ? 0 : -1;
             if (p.parent) p.parent[i] = is_root ? p.root : -1;
-            if (RST) p.pint[i] = (i == rint) ? rint : INT_MAX;  // Alg. 3: P = infinity, P[s] = s
+            if (KM == KM_RESTORE) p.pint[i] = (i == rint) ? rint : INT_MAX;  // Alg. 3: P = infinity, P[s] = s
         }
         const int rw = rint >> 5;
         for (int64_t w = (int64_t)blockIdx.x * WPB * 32 + tid; w < p.bitmap_words; w += stride) {
             const uint32_t b0 = (w == rw) ? (1u << (rint & 31)) : 0u;
             p.bitmap[w] = b0;
-            if (RST) p.vo[w] = make_uint2(b0, 0u);
+            if (KM == KM_RESTORE) p.vo[w] = make_uint2(b0, 0u);
         }
         if (blockIdx.x == 0) {
             if (p.stats)
@@ -607,6 +839,8 @@ __global__ void __launch_bounds__(WPB * 32, (24 / WPB) > 0 ? (24 / WPB) : 1) td_
                 const int rb = p.ro[rint], len = p.ro[rint + 1] - rb;
                 c->eu_count[0] = 0;
                 c->hub_count[0] = 0;
+                c->nf[0] = 1;
+                c->mf[0] = (unsigned long long)len;
                 if (len >= 1 && len <= W) {
                     p.eu[0][0] = rint;
                     p.eb[0][0] = rb;
@@ -628,8 +862,76 @@ __global__ void __launch_bounds__(WPB * 32, (24 / WPB) > 0 ? (24 / WPB) : 1) td_
     }
     bool ok = grid_sync(&c->bar_count, &c->bar_gen, &c->status, G, p.timeout_ns, &cs.ok);
 
+    bool bu_prev = false;               // mode 3: the previous layer ran bottom-up
+    unsigned long long m_seen = 0;      // mode 3: summed degrees of the vertices reached
     for (int d = 0; ok; ++d) {
         const int set_in = d % 3, set_out = (d + 1) % 3, set_rst = (d + 2) % 3;
+        const int qi = d & 1, qo = qi ^ 1;
+        bool bu = false;
+        if constexpr (KM == KM_HYBRID) {
+            // direction of this layer, taken alike by every CTA from the
+            // frontier's size nf and summed degrees mf
+            if (tid == 0) {
+                cs.hnf = ld_relaxed64(&c->nf[set_in]);
+                cs.hmf = ld_relaxed64(&c->mf[set_in]);
+            }
+            __syncthreads();
+            const unsigned long long nf = cs.hnf, mf = cs.hmf;
+            if (nf == 0) {
+                if (blockIdx.x == 0 && tid == 0) c->layers = (unsigned)d;
+                break;
+            }
+            m_seen += mf;
+            const unsigned long long m_u = (unsigned long long)p.m > m_seen ? (unsigned long long)p.m - m_seen : 0ull;
+            if (p.symmetric && p.alpha > 0) {
+                if (!bu_prev) bu = (double)mf * (double)p.alpha > (double)m_u;
+                else bu = (double)nf * (double)p.beta >= (double)p.n;
+            }
+            if (blockIdx.x == 0 && tid == 0) {
+                c->eu_count[set_rst] = 0;
+                c->hub_count[set_rst] = 0;
+                c->nf[set_rst] = 0;
+                c->mf[set_rst] = 0;
+                if (p.stats && d < kMaxStatLayers) p.stats[4 * d + 0] = (int64_t)nf;
+            }
+            if (bu && !bu_prev) {  // the frontier queue as a bitmap
+                const int64_t stride = (int64_t)G * WPB * 32;
+                for (int64_t w = (int64_t)blockIdx.x * WPB * 32 + tid; w < p.bitmap_words; w += stride)
+                    p.front[qi][w] = 0u;
+                ok = grid_sync(&c->bar_count, &c->bar_gen, &c->status, G, p.timeout_ns, &cs.ok);
+                if (!ok) break;
+                if (tid == 0) {
+                    cs.nE = min((unsigned)(ld_relaxed64(&c->eu_count[set_in]) & 0xffffffffull), p.ecap);
+                    cs.nH = min(ld_relaxed(&c->hub_count[set_in]), p.hcap);
+                }
+                __syncthreads();
+                queue_to_bitmap(p, qi, cs.nE, cs.nH, p.front[qi]);
+                ok = grid_sync(&c->bar_count, &c->bar_gen, &c->status, G, p.timeout_ns, &cs.ok);
+                if (!ok) break;
+            } else if (!bu && bu_prev) {  // the frontier bitmap as a queue
+                bitmap_to_queue(ws, p, p.front[qi], set_in, qi, gw, GW);
+                ok = grid_sync(&c->bar_count, &c->bar_gen, &c->status, G, p.timeout_ns, &cs.ok);
+                if (!ok) break;
+            }
+        }
+        const int next_level = d + 1;
+        unsigned long long my_new = 0;
+        unsigned long long my_vertices = 0, my_edges = 0;
+        if (bu) {
+            unsigned long long my_mf = 0;
+            if (tid == 0 && p.stats) cs.st[0] = cs.st[1] = cs.st[2] = 0;
+            bottom_up<WPB>(cs, p, p.front[qi], p.front[qo], next_level, gw, GW, my_new, my_edges, my_mf);
+            unsigned long long a = my_new, b = my_mf;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                a += __shfl_down_sync(FULL, a, o);
+                b += __shfl_down_sync(FULL, b, o);
+            }
+            if (lane == 0 && a) {
+                atomicAdd(&c->nf[set_out], a);
+                atomicAdd(&c->mf[set_out], b);
+            }
+        } else {
         if (tid == 0) {
             const unsigned long long eu = ld_relaxed64(&c->eu_count[set_in]);
             cs.nU = min((unsigned)(eu >> 32), p.ucap);
@@ -638,19 +940,18 @@ __global__ void __launch_bounds__(WPB * 32, (24 / WPB) > 0 ? (24 / WPB) : 1) td_
         }
         __syncthreads();
         const unsigned nH = cs.nH, n_items = cs.nU + cs.nH;
-        if (n_items == 0) {
-            if (blockIdx.x == 0 && tid == 0) c->layers = (unsigned)d;
-            break;
+        if (KM != KM_HYBRID) {
+            if (n_items == 0) {
+                if (blockIdx.x == 0 && tid == 0) c->layers = (unsigned)d;
+                break;
+            }
+            if (blockIdx.x == 0 && tid == 0) {
+                c->eu_count[set_rst] = 0;
+                c->hub_count[set_rst] = 0;
+            }
         }
-        if (blockIdx.x == 0 && tid == 0) {
-            c->eu_count[set_rst] = 0;
-            c->hub_count[set_rst] = 0;
-        }
-        const int qi = d & 1, qo = qi ^ 1;
-        const int next_level = d + 1;
-        unsigned my_new = 0;
-        unsigned long long my_vertices = 0, my_edges = 0;
         int ocnt = 0;
+        unsigned td_new = 0;
 
         // software pipeline over this warp's items gw, gw+GW, ...
         unsigned id = gw;
@@ -659,7 +960,7 @@ __global__ void __launch_bounds__(WPB * 32, (24 / WPB) > 0 ? (24 / WPB) : 1) td_
         int buf = 0;
         int et_cur = (id < n_items) ? stage_item(ws, p, cur, buf) : 0;
         int cnt_cur = cur.cnt;
-        if (p.stats && id < n_items && lane == 0)
+        if (KM != KM_HYBRID && p.stats && id < n_items && lane == 0)
             my_vertices += (d0.c < 0) ? (cur.b == __ldg(p.ro + cur.u) ? 1 : 0) : (unsigned)cur.cnt;
         Desc d1 = load_desc(p, qi, nH, n_items, id + GW);
         Item nxt = load_item(p, qi, d1, id + GW < n_items);
@@ -669,7 +970,7 @@ __global__ void __launch_bounds__(WPB * 32, (24 / WPB) > 0 ? (24 / WPB) : 1) td_
             int et_nxt = 0;
             if (id1 < n_items) {
                 et_nxt = stage_item(ws, p, nxt, buf ^ 1);
-                if (p.stats && lane == 0)
+                if (KM != KM_HYBRID && p.stats && lane == 0)
                     my_vertices += (d1.c < 0) ? (nxt.b == __ldg(p.ro + nxt.u) ? 1 : 0) : (unsigned)nxt.cnt;
             } else {
                 cp_async_commit();  // keep one group per item on every lane
@@ -680,7 +981,7 @@ __global__ void __launch_bounds__(WPB * 32, (24 / WPB) > 0 ? (24 / WPB) : 1) td_
             asm volatile("cp.async.wait_group 1;" ::: "memory");
             __syncwarp();
             if (lane == 0) my_edges += (unsigned long long)et_cur;
-            process_item<RST>(ws, p, buf, et_cur, cnt_cur, next_level, set_out, qo, ocnt, my_new);
+            process_item<KM>(ws, p, buf, et_cur, cnt_cur, next_level, set_out, qo, ocnt, td_new);
             buf ^= 1;
             id = id1;
             et_cur = et_nxt;
@@ -691,9 +992,9 @@ __global__ void __launch_bounds__(WPB * 32, (24 / WPB) > 0 ? (24 / WPB) : 1) td_
         }
         cp_async_wait_all();
         __syncwarp();
-        if (ocnt > 0) warp_flush(ws, p, set_out, qo, ocnt, next_level);
+        if (ocnt > 0) warp_flush<KM == KM_HYBRID ? (FL_LP | FL_CNT) : FL_LP>(ws, p, set_out, qo, ocnt, next_level);
 
-        if (RST) {
+        if (KM == KM_RESTORE) {
             // restoration (Alg. 3), once every racy set of the layer is done:
             // each non-zero out word is owned by one warp, which restores the
             // vertices of its bits with P < 0, sets their visited bits, clears
@@ -712,7 +1013,7 @@ __global__ void __launch_bounds__(WPB * 32, (24 / WPB) > 0 ? (24 / WPB) : 1) td_
                     const int src = __ffs(nz) - 1;
                     nz &= nz - 1;
                     if (ocnt > OBW - 32) {
-                        warp_flush(ws, p, set_out, qo, ocnt, next_level);
+                        warp_flush<FL_LP>(ws, p, set_out, qo, ocnt, next_level);
                         ocnt = 0;
                     }
                     const int64_t word = (int64_t)gw + GW * (j0 + src);
@@ -732,12 +1033,14 @@ __global__ void __launch_bounds__(WPB * 32, (24 / WPB) > 0 ? (24 / WPB) : 1) td_
                         p.bitmap[word] = x.x | m;  // the plain visited bitmap, for export
                     }
                     ocnt += __popc(m);
-                    if (lane == 0) my_new += (unsigned)__popc(m);
+                    if (lane == 0) td_new += (unsigned)__popc(m);
                 }
             }
-            if (ocnt > 0) warp_flush(ws, p, set_out, qo, ocnt, next_level);
+            if (ocnt > 0) warp_flush<FL_LP>(ws, p, set_out, qo, ocnt, next_level);
             ocnt = 0;
         }
+        my_new = td_new;
+        }  // top-down layer
 
         if (p.stats && d < kMaxStatLayers) {
             unsigned long long a = my_vertices, e = my_edges, t = my_new;
@@ -762,6 +1065,7 @@ __global__ void __launch_bounds__(WPB * 32, (24 / WPB) > 0 ? (24 / WPB) : 1) td_
         ok = grid_sync(&c->bar_count, &c->bar_gen, &c->status, G, p.timeout_ns, &cs.ok);
         if (p.stats && d < kMaxStatLayers && blockIdx.x == 0 && tid == 0)
             p.stats[4 * d + 3] = (int64_t)(globaltimer() - t_start);
+        bu_prev = bu;
     }
 
     __syncthreads();
@@ -773,6 +1077,8 @@ __global__ void __launch_bounds__(WPB * 32, (24 / WPB) > 0 ? (24 / WPB) : 1) td_
                 c->eu_count[j] = 0;
                 c->hub_count[j] = 0;
                 c->work[j] = 0;
+                c->nf[j] = 0;
+                c->mf[j] = 0;
             }
             c->bar_count = 0;
             c->exit_count = 0;
@@ -781,10 +1087,10 @@ __global__ void __launch_bounds__(WPB * 32, (24 / WPB) > 0 ? (24 / WPB) : 1) td_
     }
 }
 
-template <int WPB, bool RST>
+template <int WPB, int KM>
 int launch(Graph *g, const WParams &prm, cudaStream_t s)
 {
-    auto kern = td_warp_kernel<WPB, RST>;
+    auto kern = td_warp_kernel<WPB, KM>;
     const int smem = (int)sizeof(CtaSmem<WPB>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute(td_warp_kernel)");
@@ -809,10 +1115,13 @@ int launch(Graph *g, const WParams &prm, cudaStream_t s)
 // slices, so a layer has at most 2m/W of them (+2).
 int64_t td_hub_capacity(int64_t m) { return 2 * (m / W) + 2; }
 
-int td_warp_launch(Graph *g, int32_t root, int32_t *level, int32_t *parent, cudaStream_t s, bool restore)
+int td_warp_launch(Graph *g, int32_t root, int32_t *level, int32_t *parent, cudaStream_t s, int mode)
 {
+    const bool restore = mode == MODE_RESTORE, hybrid = mode == MODE_HYBRID;
     if (restore && (!g->d_vo || !g->d_pint))
         return set_error(BFS_ERR_INVALID_ARG, "mode 2: restoration workspace not allocated");
+    if (hybrid && (!g->d_front[0] || !g->d_front[1]))
+        return set_error(BFS_ERR_INVALID_ARG, "mode 3: frontier bitmaps not allocated");
     WParams p;
     p.ro = g->d_row_offsets;
     p.col = g->d_col_idx;
@@ -822,6 +1131,14 @@ int td_warp_launch(Graph *g, int32_t root, int32_t *level, int32_t *parent, cuda
     p.orig = g->d_orig;
     p.bitmap = g->d_bitmap;
     p.vo = restore ? g->d_vo : nullptr;
+    p.front[0] = hybrid ? g->d_front[0] : nullptr;
+    p.front[1] = hybrid ? g->d_front[1] : nullptr;
+    p.m = g->m;
+    p.split32 = (int32_t)g->split32;
+    p.n_nonzero = (int32_t)g->n_nonzero;
+    p.alpha = g->opt.alpha;
+    p.beta = g->opt.beta;
+    p.symmetric = g->symmetric ? 1 : 0;
     p.pint = restore ? g->d_pint : nullptr;
     for (int b = 0; b < 2; ++b) {
         p.eu[b] = g->d_eq[b][0];
@@ -843,8 +1160,12 @@ int td_warp_launch(Graph *g, int32_t root, int32_t *level, int32_t *parent, cuda
     p.bitmap_words = (int32_t)g->bitmap_words;
     p.timeout_ns = (uint64_t)g->opt.timeout_ns;
     switch (g->opt.block) {
-    case 256: return restore ? launch<8, true>(g, p, s) : launch<8, false>(g, p, s);
-    case 512: return restore ? launch<16, true>(g, p, s) : launch<16, false>(g, p, s);
+    case 256:
+        return restore ? launch<8, KM_RESTORE>(g, p, s)
+                       : hybrid ? launch<8, KM_HYBRID>(g, p, s) : launch<8, KM_ATOMIC>(g, p, s);
+    case 512:
+        return restore ? launch<16, KM_RESTORE>(g, p, s)
+                       : hybrid ? launch<16, KM_HYBRID>(g, p, s) : launch<16, KM_ATOMIC>(g, p, s);
     default: return set_error(BFS_ERR_INVALID_ARG, "warp mode supports BLOCK 256 or 512");
     }
 }
