@@ -33,9 +33,9 @@
 // race can only drop a bit from a word that the last writer left non-zero,
 // so the pass sees every vertex discovered in the layer (Sec. 3.3.2).
 //
-// Mode 3 (HYB) is the direction-optimising search (bottom-up steps of the
-// related work named in Sec. 2; future work in Sec. 8) on graphs whose every
-// edge has its reverse: a layer runs bottom-up once the frontier's edges
+// Mode 3 (HYB) is the direction-optimising search (the bottom-up steps of the
+// hybrid algorithm that Sec. 3 calls the state of the art and Sec. 8 plans
+// for) on graphs whose every edge has its reverse: a layer runs bottom-up once the frontier's edges
 // exceed the unexplored edges / alpha, and top-down again once the frontier
 // has fewer than n / beta vertices.  In a bottom-up layer each warp owns
 // whole visited words (dealt round-robin); every unvisited vertex scans its
