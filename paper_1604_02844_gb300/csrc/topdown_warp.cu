@@ -17,7 +17,8 @@
 // where the running edge count crosses a multiple of W or every 32 entries.
 //
 // Work items of a layer (hub slices, then units) are dealt round-robin to
-// the grid's warps.  Per item a warp: stages the adjacency into its shared
+// the grid's warps; a layer with fewer items than half the warps deals each
+// hub slice in up to 12 parts of >= 32 edges.  Per item a warp: stages the adjacency into its shared
 // buffer with cp.async (issued one item ahead), tests the visited word of
 // every staged edge (8 loads per lane in flight) and compacts the unvisited
 // ones in place with ballots (pass A), then claims those with atomicOr and
@@ -136,21 +137,22 @@ struct Desc {
     int a, c;  // unit: first entry, count; hub: index into the hub queue, -1
 };
 
-__device__ __forceinline__ Desc load_desc(const WParams &p, int qi, unsigned nH, unsigned n_items, unsigned id)
+__device__ __forceinline__ Desc load_desc(const WParams &p, int qi, unsigned nH, unsigned n_items, unsigned id,
+                                          unsigned split)
 {
     Desc d{0, 0};
     if (id >= n_items) return d;
-    if (id < nH) {
-        d.a = (int)id;
-        d.c = -1;
+    if (id < nH * split) {  // part (id % split) of hub slice id / split
+        d.a = (int)(id / split);
+        d.c = -1 - (int)(id % split);
     } else {
-        d.a = __ldcg(p.us[qi] + (id - nH));
-        d.c = __ldcg(p.uc[qi] + (id - nH));
+        d.a = __ldcg(p.us[qi] + (id - nH * split));
+        d.c = __ldcg(p.uc[qi] + (id - nH * split));
     }
     return d;  // checked where it is used, so the loads stay in flight
 }
 
-__device__ __forceinline__ Item load_item(const WParams &p, int qi, const Desc &d, bool valid)
+__device__ __forceinline__ Item load_item(const WParams &p, int qi, const Desc &d, bool valid, unsigned split)
 {
     const int lane = threadIdx.x & 31;
     Item it{0, 0, 0, 0};
@@ -161,6 +163,13 @@ __device__ __forceinline__ Item load_item(const WParams &p, int qi, const Desc &
             it.u = __ldcg(p.hu[qi] + d.a);
             it.b = __ldcg(p.hb[qi] + d.a);
             it.l = __ldcg(p.hl[qi] + d.a);
+            if (split > 1) {  // a part of at least 32 edges
+                const int part = -1 - d.c;
+                const int sub = max(32, (it.l + (int)split - 1) / (int)split);
+                const int lo = min(it.l, part * sub);
+                it.b += lo;
+                it.l = min(sub, it.l - lo);
+            }
         }
     } else {
         it.cnt = (d.c < 0 || d.c > 32) ? 0 : d.c;  // a unit holds <= 32 entries
@@ -176,12 +185,11 @@ __device__ __forceinline__ Item load_item(const WParams &p, int qi, const Desc &
 
 // Prefix-sum the item's lengths into off[buf], record vertices, and issue the
 // cp.async copies of its adjacency into stage[buf].  Lists of >= 32 edges
-// are copied by the whole warp striding over each (coalesced, no search);
-// the short lists are flattened: consecutive lanes copy consecutive edges of
-// the concatenated short lists, each lane finding its list with a warp-level
-// search (the short lists starting inside a batch of 32 edges form a bit
-// mask, redux.or; a popc counts the boundaries before the lane).  Commits
-// one group per lane.  Returns the item's edge count (uniform).
+// are copied by the whole warp striding over each (coalesced); a list of
+// < 32 edges is copied by its own lane, one edge per step (as many steps as
+// the longest short list; a search over the flattened lists costs more
+// instructions than it saves).  Commits one group per lane.  Returns the
+// item's edge count (uniform).
 __device__ __forceinline__ int stage_item(WarpSmem &ws, const WParams &p, const Item &it_in, int buf)
 {
     const int lane = threadIdx.x & 31;
@@ -191,27 +199,20 @@ __device__ __forceinline__ int stage_item(WarpSmem &ws, const WParams &p, const 
         it.l = 0;
     }
     const bool real = lane < it.cnt;
-    const bool shortl = real && it.l < 32;
-    const int sl = shortl ? it.l : 0;
-    int inc = it.l, sinc = sl;
+    const int sl = (real && it.l < 32) ? it.l : 0;
+    int inc = it.l;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
         const int y = __shfl_up_sync(FULL, inc, o);
-        const int z = __shfl_up_sync(FULL, sinc, o);
-        if (lane >= o) {
-            inc += y;
-            sinc += z;
-        }
+        if (lane >= o) inc += y;
     }
     int et = __shfl_sync(FULL, inc, 31);
-    const int st = __shfl_sync(FULL, sinc, 31);
     const bool fits = et < MAXI;  // cannot fail: units < 2W edges, slices <= W
     if (!fits) {
         if (lane == 0) atomicOr(&p.ctrl->status, ST_OVERFLOW);
         et = 0;
     }
     const int off = inc - it.l;
-    const int soff = sinc - sl;
     if (real) {
         ws.off[buf][lane] = off;
         ws.iu[buf][lane] = it.u;
@@ -228,34 +229,10 @@ __device__ __forceinline__ int stage_item(WarpSmem &ws, const WParams &p, const 
             const int bl = __shfl_sync(FULL, it.l, src);
             for (int k = lane; k < bl; k += 32) cp_async4(&ws.stage[buf][bo + k], p.col + bb + k);
         }
-        // short lists, flattened
-        const unsigned sm = __ballot_sync(FULL, shortl);
-#pragma unroll 2
-        for (int base = 0; base < st; base += 32) {
-            unsigned starts = (shortl && soff > base && soff < base + 32) ? (1u << (soff - base)) : 0u;
-            starts = __reduce_or_sync(FULL, starts);
-            const unsigned below = __ballot_sync(FULL, shortl && soff <= base);
-            // the short list holding edge base + lane: the (rank)-th short list
-            const int rank = __popc(below) - 1 + __popc(starts & ((2u << lane) - 1u));
-            // lane of the rank-th (0-based) short list: the smallest j with
-            // more than `rank` short lists among lanes 0..j (5 fixed steps)
-            int j = 0;
-            {
-                int lo = 0, hi = 31;
-#pragma unroll
-                for (int step = 0; step < 5; ++step) {
-                    const int mid = (lo + hi) >> 1;
-                    if (__popc(sm & ((2u << mid) - 1u)) > rank) hi = mid;
-                    else lo = mid + 1;
-                }
-                j = lo & 31;
-            }
-            const int jb = __shfl_sync(FULL, it.b, j);
-            const int jo = __shfl_sync(FULL, off, j);
-            const int js = __shfl_sync(FULL, soff, j);
-            const int e = base + lane;
-            if (e < st) cp_async4(&ws.stage[buf][jo + (e - js)], p.col + jb + (e - js));
-        }
+        // short lists: each lane copies its own, one edge per step
+        const int maxl = (int)__reduce_max_sync(FULL, (unsigned)sl);
+        for (int k = 0; k < maxl; ++k)
+            if (k < sl) cp_async4(&ws.stage[buf][off + k], p.col + it.b + k);
     }
     cp_async_commit();
     return et;
@@ -939,7 +916,10 @@ __global__ void __launch_bounds__(WPB * 32, (24 / WPB) > 0 ? (24 / WPB) : 1) td_
             if (p.stats) cs.st[0] = cs.st[1] = cs.st[2] = 0;
         }
         __syncthreads();
-        const unsigned nH = cs.nH, n_items = cs.nU + cs.nH;
+        const unsigned nH0 = cs.nH;
+        // few items: hub slices are dealt in up to 12 parts so that more warps share them
+        const unsigned split = (cs.nU + nH0 > 0 && cs.nU + nH0 < GW / 2) ? min(12u, GW / (cs.nU + nH0)) : 1u;
+        const unsigned nH = nH0, n_items = cs.nU + nH0 * split;
         if (KM != KM_HYBRID) {
             if (n_items == 0) {
                 if (blockIdx.x == 0 && tid == 0) c->layers = (unsigned)d;
@@ -955,16 +935,16 @@ __global__ void __launch_bounds__(WPB * 32, (24 / WPB) > 0 ? (24 / WPB) : 1) td_
 
         // software pipeline over this warp's items gw, gw+GW, ...
         unsigned id = gw;
-        Desc d0 = load_desc(p, qi, nH, n_items, id);
-        Item cur = load_item(p, qi, d0, id < n_items);
+        Desc d0 = load_desc(p, qi, nH, n_items, id, split);
+        Item cur = load_item(p, qi, d0, id < n_items, split);
         int buf = 0;
         int et_cur = (id < n_items) ? stage_item(ws, p, cur, buf) : 0;
         int cnt_cur = cur.cnt;
         if (KM != KM_HYBRID && p.stats && id < n_items && lane == 0)
             my_vertices += (d0.c < 0) ? (cur.b == __ldg(p.ro + cur.u) ? 1 : 0) : (unsigned)cur.cnt;
-        Desc d1 = load_desc(p, qi, nH, n_items, id + GW);
-        Item nxt = load_item(p, qi, d1, id + GW < n_items);
-        Desc d2 = load_desc(p, qi, nH, n_items, id + 2 * GW);
+        Desc d1 = load_desc(p, qi, nH, n_items, id + GW, split);
+        Item nxt = load_item(p, qi, d1, id + GW < n_items, split);
+        Desc d2 = load_desc(p, qi, nH, n_items, id + 2 * GW, split);
         while (id < n_items) {
             const unsigned id1 = id + GW, id2 = id + 2 * GW;
             int et_nxt = 0;
@@ -976,8 +956,8 @@ __global__ void __launch_bounds__(WPB * 32, (24 / WPB) > 0 ? (24 / WPB) : 1) td_
                 cp_async_commit();  // keep one group per item on every lane
             }
             const int cnt_nxt = nxt.cnt;
-            const Item nn = load_item(p, qi, d2, id2 < n_items);
-            const Desc d3 = load_desc(p, qi, nH, n_items, id2 + GW);
+            const Item nn = load_item(p, qi, d2, id2 < n_items, split);
+            const Desc d3 = load_desc(p, qi, nH, n_items, id2 + GW, split);
             asm volatile("cp.async.wait_group 1;" ::: "memory");
             __syncwarp();
             if (lane == 0) my_edges += (unsigned long long)et_cur;
