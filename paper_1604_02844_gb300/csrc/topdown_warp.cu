@@ -20,7 +20,7 @@
 // the grid's warps; a layer with fewer items than half the warps deals each
 // hub slice in up to 12 parts of >= 32 edges.  Per item a warp: stages the adjacency into its shared
 // buffer with cp.async (issued one item ahead), tests the visited word of
-// every staged edge (8 loads per lane in flight) and compacts the unvisited
+// every staged edge (12 loads per lane in flight) and compacts the unvisited
 // ones in place with ballots (pass A), then claims those with atomicOr and
 // queues the winners (pass B).  Descriptors and entries of the next items
 // are prefetched into registers while the current item is processed.
@@ -61,7 +61,7 @@ using namespace dev;
 constexpr int W = 384;       // unit edge target and hub slice length
 constexpr int MAXI = 2 * W;  // edges of one work item are < MAXI
 constexpr int OBW = 128;     // out-buffer entries per warp
-constexpr int UA = 8;        // pass A: visited-word loads per lane in flight
+constexpr int UA = 12;       // pass A: visited-word loads per lane in flight
 constexpr int UB = 2;        // pass B: claims per lane in flight
 constexpr int VW = 4;        // bottom-up: visited words per warp in flight
 
