@@ -56,6 +56,8 @@ struct GraphState {
     bool has_ws = false;              // (under Server::mu)
     int64_t ws_bytes = 0;
     uint8_t *d_stage = nullptr;       // [64][n] extraction rows
+    MsCtrl last{};                    // counters after the previous round (worker thread only)
+    bool have_last = false;
     std::thread worker;
     std::condition_variable cv;
 };
@@ -159,8 +161,19 @@ int Server::finish(GraphState &gs, unsigned long long mask)
     return BFS_OK;
 }
 
-// One round for one graph: waiting queries into free lanes, a few
-// iterations, finished lanes out.
+// Would the next iteration of this batch be a pull step, were no lane
+// younger than two iterations?  (The kernel's test in msbfs.cu.)  While it
+// would, new queries wait a round: joining now would keep the batch pushing.
+static bool pull_phase(const Graph *g, const MsCtrl &st, unsigned long long running)
+{
+    const int par = (int)(st.iter & 1);
+    const unsigned long long live = st.alive[par] & running;
+    return g->symmetric && live && (long long)st.fedges[par] * 16 > g->m &&
+           (double)st.seen_pairs >= 0.3 * (double)__builtin_popcountll(live) * (double)g->n_nonzero;
+}
+
+// One round for one graph: waiting queries into free lanes (unless the
+// batch is in its pull phase), a few iterations, finished lanes out.
 int Server::round(GraphState &gs)
 {
     unsigned long long add = 0, running;
@@ -169,7 +182,8 @@ int Server::round(GraphState &gs)
     {
         std::lock_guard<std::mutex> lk(mu);
         if (!ensure_ws(gs)) return BFS_NOT_READY;  // no room yet: the queries wait
-        while (!gs.waiting.empty() && (gs.running | add) != ~0ull) {
+        const bool hold = gs.running && gs.have_last && pull_phase(gs.g, gs.last, gs.running);
+        while (!hold && !gs.waiting.empty() && (gs.running | add) != ~0ull) {
             const int lane = __builtin_ctzll(~(gs.running | add));
             const uint64_t t = gs.waiting.front();
             gs.waiting.pop_front();
@@ -191,9 +205,10 @@ int Server::round(GraphState &gs)
     const int share = std::max(gs.g->num_sms, total_ctas / std::max(1, active));
     int rc = ms_step_capped(gs.g, iters_per_step, share);
     if (rc != BFS_OK) return rc;
-    MsCtrl st;
+    MsCtrl &st = gs.last;
     rc = ms_read_ctrl(gs.g, &st);
     if (rc != BFS_OK) return rc;
+    gs.have_last = true;
     if (st.status & (ST_TIMEOUT | ST_OVERFLOW | ST_DEPTH))
         return set_error(st.status & ST_DEPTH ? BFS_ERR_DEPTH : (st.status & ST_TIMEOUT ? BFS_ERR_TIMEOUT : BFS_ERR_CUDA),
                          "server: device-side error in a batched search");
