@@ -54,6 +54,9 @@ using namespace dev;
 
 constexpr int H = 256;   // hub slice length
 constexpr int UX = 4;    // 32-edge batches per warp in flight
+constexpr int GRAB = 4;  // frontier entries a warp takes from the dispenser at a time: few, so
+                         // that runs of hub slices (up to GRAB * H edges) do not leave one warp
+                         // working while the grid waits at the barrier
 constexpr int MS_WPB = 8;
 
 struct MsParams {
@@ -135,13 +138,19 @@ __device__ __forceinline__ void ms_expand(const MsParams &p, int par, unsigned n
     const unsigned lt = lanemask_lt();
     MsCtrl *c = p.ctrl;
     int tcnt = 0;  // warp-uniform fill of tbuf
-    for (;;) {
+    const unsigned gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const unsigned GWn = (gridDim.x * blockDim.x) >> 5;
+    // the first GRAB entries of every warp are its own; the rest come from the dispenser
+    for (bool first = true;; first = false) {
         unsigned base = 0;
-        if (lane == 0) base = atomicAdd(&c->work[par], 32u);
-        base = __shfl_sync(FULL, base, 0);
+        if (first) base = gw * GRAB;
+        else {
+            if (lane == 0) base = GWn * GRAB + atomicAdd(&c->work[par], (unsigned)GRAB);
+            base = __shfl_sync(FULL, base, 0);
+        }
         if (base >= nF) break;
         const unsigned j = base + lane;
-        const bool real = j < nF;
+        const bool real = j < nF && lane < GRAB;
         int u = 0, b = 0, l = 0;
         unsigned long long f = 0;
         if (real) {
