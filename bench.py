@@ -301,6 +301,41 @@ def ablation_measurement(g, gb, torch, roots, mcc, checks, level, parent, flush,
     return out
 
 
+def uneven_mix_measurement(args, gb, torch, dev, main_graph):
+    """256 seeded sources spread round-robin over six resident Kronecker
+    graphs of scales 12, 14, 16, 18, 20 and 22 (43/43/43/43/42/42), each
+    graph's share run by one bfs_run_batch (one persistent launch sequence);
+    host wall clock around the six calls, best of 3."""
+    import graphgen
+    scales = [12, 14, 16, 18, 20, 22]
+    counts = [len(range(i, 256, len(scales))) for i in range(len(scales))]
+    parts = []
+    for s_, k in zip(scales, counts):
+        if s_ == args.scale and args.edgefactor == 16:
+            ro, g, own = main_graph[0], main_graph[1], False
+        else:
+            ro, col = graphgen.kronecker(s_, 16, args.seed + s_)
+            g, own = gb.Graph(ro, col), True
+        roots = graphgen.pick_roots(ro, k, args.seed + 50 + s_)
+        parts.append((g, own, roots, torch.empty((k, len(ro) - 1), dtype=torch.uint8, device=dev)))
+    for g, _, roots, out in parts:  # warm-up: batch workspaces
+        gb.bfs_run_batch(g.handle, roots, out)
+    best = None
+    for _ in range(3):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for g, _, roots, out in parts:
+            gb.bfs_run_batch(g.handle, roots, out)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        best = el if best is None else min(best, el)
+    for g, own, _, _ in parts:
+        if own:
+            g.close()
+    return {"workload": "kronecker_scales_12_14_16_18_20_22_256sources", "sources_per_graph": counts,
+            "queries_per_s": 256 / best, "s_per_256": best}
+
+
 def batched_measurement(args, gb, torch, dev):
     """1,024 seeded sources on a Kronecker graph (scale 20, ef 16) through
     bfs_run_batch (64 sources per bit-parallel batch), against the plain path
@@ -575,6 +610,7 @@ def run_ours(args):
     batched = None
     if not args.no_batched and rank == 0:
         batched = batched_measurement(args, gb, torch, dev)
+        batched["uneven_mix"] = uneven_mix_measurement(args, gb, torch, dev, (ro, g))
     serving = None
     if not args.no_serving and rank == 0:
         serving = serving_measurement(args, gb, torch, dev)
