@@ -44,6 +44,8 @@ def parse_args(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--scale", type=int, default=22)
+    ap.add_argument("--graph", choices=["kronecker", "erdos_renyi"], default="kronecker",
+                    help="erdos_renyi: the low-skew contrast graph with the same n and tuple count")
     ap.add_argument("--edgefactor", type=int, default=16)
     ap.add_argument("--roots", type=int, default=64)
     ap.add_argument("--seed", type=int, default=1)
@@ -86,8 +88,8 @@ def harmonic_mean(xs):
     return len(xs) / sum(1.0 / x for x in xs)
 
 
-def workload_name(scale, ef, roots):
-    return f"kronecker_scale{scale}_ef{ef}_{roots}roots"
+def workload_name(scale, ef, roots, graph="kronecker"):
+    return f"{graph}_scale{scale}_ef{ef}_{roots}roots"
 
 
 def dist_env():
@@ -172,7 +174,7 @@ def profiled_traffic(args, options):
     """DRAM bytes per launch from the committed ncu summary, or None when the
     kernel sources or the configuration differ from what was profiled."""
     import hashlib
-    prof = os.path.join(ROOT, "profiles", f"td_warp_kernel_kronecker_s{args.scale}.txt")
+    prof = os.path.join(ROOT, "profiles", f"td_warp_kernel_{args.graph}_s{args.scale}.txt")
     if not os.path.exists(prof) or options.get("mode") != 0 or options.get("block") != 512:
         return None
     kv = {}
@@ -198,7 +200,7 @@ def measured_peaks():
 
 def build_workload(args, rank):
     import graphgen
-    ro, col = graphgen.kronecker(args.scale, args.edgefactor, args.seed)
+    ro, col = getattr(graphgen, args.graph)(args.scale, args.edgefactor, args.seed)
     roots = graphgen.pick_roots(ro, args.roots, args.seed + 1000 * rank)
     return ro, col, roots
 
@@ -250,7 +252,7 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
         "data": "synthetic",
-        "config": {"workload": workload_name(args.scale, args.edgefactor, args.roots),
+        "config": {"workload": workload_name(args.scale, args.edgefactor, args.roots, args.graph),
                    "scale": args.scale, "edgefactor": args.edgefactor, "roots": args.roots,
                    "n": len(ro) - 1, "m_directed": int(len(col)),
                    "step": f"{per_step} oracle searches (a bounded sample of the {args.roots} roots)"},
@@ -311,7 +313,7 @@ def uneven_mix_measurement(args, gb, torch, dev, main_graph):
     counts = [len(range(i, 256, len(scales))) for i in range(len(scales))]
     parts = []
     for s_, k in zip(scales, counts):
-        if s_ == args.scale and args.edgefactor == 16:
+        if s_ == args.scale and args.edgefactor == 16 and args.graph == "kronecker":
             ro, g, own = main_graph[0], main_graph[1], False
         else:
             ro, col = graphgen.kronecker(s_, 16, args.seed + s_)
@@ -622,7 +624,7 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": {"workload": workload_name(args.scale, args.edgefactor, args.roots),
+            "config": {"workload": workload_name(args.scale, args.edgefactor, args.roots, args.graph),
                        "scale": args.scale, "edgefactor": args.edgefactor, "roots": args.roots,
                        "n": n, "m_directed": m, "seed": args.seed, "parallelism": "replicas",
                        "l2": "flushed between searches (512 MiB write); col_idx also > L2",
