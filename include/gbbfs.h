@@ -13,8 +13,9 @@
  *     and set P[v] = u;
  *   - the visited set is a bitmap, vertex v at word v/32, bit v%32
  *     (Sec. 3.3.1, Listing 1).  Where two threads race on one word the paper
- *     restores the bitmap afterwards (Alg. 3); this library sets bits with a
- *     32-bit atomic OR instead, so no restoration step exists.
+ *     restores the bitmap afterwards (Alg. 3); by default this library sets
+ *     bits with a 32-bit atomic OR instead, and BFS_OPT_MODE 2 runs the
+ *     paper's racy bitmap with its restoration pass.
  *
  * Graph layout: CSR with int32 row_offsets[n+1] ("colstarts" in Sec. 3.3.1)
  * and int32 col_idx[m] ("rows"): Adj[u] = col_idx[row_offsets[u] ..
@@ -64,8 +65,8 @@ typedef enum {
     BFS_ERR_BUSY = -7           /* no free slot / HBM budget exhausted     */
 } bfs_status;
 
-/* Tunables of a graph (bfs_graph_set_option).  Defaults are chosen at
- * bfs_graph_create from the device; the autotuner overrides them. */
+/* Tunables of a graph (bfs_graph_set_option).  The defaults are the values
+ * measured fastest on GB300; a caller may override them per graph. */
 typedef enum {
     BFS_OPT_BLOCK = 1,          /* threads per CTA: 256, 512 or 1024                  */
     BFS_OPT_CTAS_PER_SM = 2,    /* resident CTAs per SM of the persistent grid (>=1)  */
@@ -145,7 +146,8 @@ int bfs_graph_set_option(bfs_graph *g, int option, int64_t value);
 int64_t bfs_graph_get_option(const bfs_graph *g, int option);
 
 /*
- * Single-source top-down BFS from `root` (Alg. 2 with atomic bitmap updates).
+ * Single-source BFS from `root`, expanded as BFS_OPT_MODE selects (default:
+ * top-down, Alg. 2 with atomic bitmap updates; see BFS_OPT_MODE).
  *   root       : 0 <= root < n, else BFS_ERR_INVALID_ARG
  *   level_out  : int32[n], device memory or host memory (detected)
  *   parent_out : int32[n], device or host memory, or NULL to skip parents
@@ -198,8 +200,9 @@ int bfs_graph_status(bfs_graph *g);
 
 /*
  * Per-layer counters of the last bfs_run, the columns of Table 1: for layer
- * d, vertices[d] = frontier entries expanded, edges[d] = adjacency entries
- * scanned, traversed[d] = vertices first reached.  Recorded only while
+ * d, vertices[d] = frontier vertices, edges[d] = adjacency entries scanned
+ * (in a bottom-up layer of mode 3: entries examined by the unvisited
+ * vertices), traversed[d] = vertices first reached.  Recorded only while
  * BFS_OPT_LAYER_STATS is 1.  Arrays are host int64[max_layers].  Returns the
  * number of layers (<= max_layers are written) or a negative bfs_status.
  * Synchronous.
@@ -237,7 +240,10 @@ int bfs_run_batch(bfs_graph *g, const int32_t *roots, int32_t k, uint8_t *level_
  * arrive; a lane freed by a finished query is given to the next waiting one
  * while the batch keeps running.  Work is admitted while the device memory
  * it needs fits `hbm_budget_bytes` (0 = a default fraction of free memory).
- * The server runs its own host thread and CUDA stream.
+ * Each registered graph gets its own host worker thread and CUDA stream.
+ * While a batch is in its heavy (pull) phase, new queries on that graph wait
+ * a few iterations and then join together, so that young lanes do not keep
+ * the batch in its slower push form.
  */
 bfs_server *bfs_server_create(int64_t hbm_budget_bytes);
 int bfs_server_destroy(bfs_server *s);
