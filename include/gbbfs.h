@@ -215,6 +215,29 @@ int bfs_graph_layer_stats(bfs_graph *g, int64_t *vertices, int64_t *edges,
  * number of layers or a negative bfs_status.  Synchronous. */
 int bfs_graph_layer_times(bfs_graph *g, int64_t *t_end_ns, int32_t max_layers);
 
+/*
+ * Autotuner (not in the paper): times candidate values of the graph's own
+ * tunables on `samples` sample searches of this graph (0 = 8; roots spread
+ * over the vertices with edges) and leaves the fastest values set.  Options
+ * are tuned one at a time, each keeping its best value before the next is
+ * tried.  `what` combines:
+ *   BFS_TUNE_SINGLE : the current BFS_OPT_MODE's tunables -- BLOCK; in mode 1
+ *                     also WARP_DEGREE, CTA_DEGREE and SEGMENT; in mode 3
+ *                     also ALPHA and BETA
+ *   BFS_TUNE_BATCH  : BATCH_WIDTH and BATCH_BLOCK, timed on bfs_run_batch
+ *                     over 128 sources
+ *   BFS_TUNE_MODE   : BFS_OPT_MODE 0 or 3, whichever is faster (applied
+ *                     before BFS_TUNE_SINGLE)
+ * Results never depend on the options, only the time does.  Synchronous;
+ * allocates its own scratch (two int32[n] and, for BFS_TUNE_BATCH, uint8
+ * [128][n]) and frees it.  On an error the options are restored and the
+ * status returned.
+ */
+#define BFS_TUNE_SINGLE 1
+#define BFS_TUNE_BATCH 2
+#define BFS_TUNE_MODE 4
+int bfs_graph_autotune(bfs_graph *g, int what, int32_t samples);
+
 /* Copy the visited bitmap of the last bfs_run (uint32 words, vertex v at
  * word v>>5, bit v&31; Sec. 3.3.1, Listing 1) to host memory `words_out` of
  * `nwords` >= ceil(n/32) entries.  Synchronous. */

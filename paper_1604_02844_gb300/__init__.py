@@ -78,6 +78,7 @@ SIGNATURES = {
     "bfs_graph_layer_stats": (_INT, [_P, _P, _P, _P, _I32]),
     "bfs_graph_layer_times": (_INT, [_P, _P, _I32]),
     "bfs_graph_visited_bitmap": (_INT, [_P, _P, _I64]),
+    "bfs_graph_autotune": (_INT, [_P, _INT, ctypes.c_int32]),
     "bfs_run_batch": (_INT, [_P, _P, _I32, _P]),
     "bfs_server_create": (_P, [_I64]),
     "bfs_server_destroy": (_INT, [_P]),
@@ -218,6 +219,14 @@ def bfs_graph_layer_times(g, max_layers: int = 256) -> np.ndarray:
     return t[:L]
 
 
+BFS_TUNE_SINGLE, BFS_TUNE_BATCH, BFS_TUNE_MODE = 1, 2, 4
+
+
+def bfs_graph_autotune(g, what: int, samples: int = 0) -> None:
+    """Time candidate option values on sample searches and keep the fastest."""
+    _check(load().bfs_graph_autotune(g, what, samples))
+
+
 def bfs_graph_visited_bitmap(g, n: int) -> np.ndarray:
     words = np.zeros((n + 31) // 32, np.uint32)
     _check(load().bfs_graph_visited_bitmap(g, words.ctypes.data, words.shape[0]))
@@ -305,6 +314,11 @@ class Graph:
 
     def visited_bitmap(self):
         return bfs_graph_visited_bitmap(self.handle, self.n)
+
+    def autotune(self, what: int = BFS_TUNE_SINGLE, samples: int = 0) -> dict:
+        """Run the autotuner; returns the options it left set."""
+        bfs_graph_autotune(self.handle, what, samples)
+        return {k: self.get_option(k) for k in OPTION_NAMES}
 
     def close(self):
         if self.handle:
