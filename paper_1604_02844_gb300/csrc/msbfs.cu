@@ -771,50 +771,76 @@ __global__ void map_ids_kernel(int32_t *ids, const int32_t *__restrict__ perm, i
     if (i < k) ids[i] = perm[ids[i]];
 }
 
+__global__ void batch_lanes_kernel(const int32_t *__restrict__ roots, const int32_t *__restrict__ perm, int32_t k,
+                                   int out_dev, int width, int32_t *src, int32_t *rows)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < k) {
+        src[i] = perm[roots[i]];
+        rows[i] = out_dev ? i : i % width;
+    }
+}
+
 // bfs_run_batch: batches of `batch_width` sources, each run to completion.
+// The sources (mapped to internal ids) and output rows of every batch are
+// put on the device first; the batches then follow each other on the
+// workspace stream with no host round trip: each batch's lanes are injected
+// from device memory, run to completion, and extracted with recycling
+// (which leaves the workspace clean for the next batch).  Device-side status
+// bits accumulate over the batches and are read once at the end.
 int ms_run_batch(Graph *g, const int32_t *roots, int32_t k, uint8_t *level_out)
 {
     MsWs *w = nullptr;
     int rc = ms_alloc(g, &w);
     if (rc != BFS_OK) return rc;
+    if (k == 0) return BFS_OK;
     const int64_t n = g->n;
+    cudaStream_t s = w->stream;
     const bool out_dev = is_device_pointer(level_out);
+    const int width = g->opt.batch_width;
     uint8_t *d_out = level_out;
     uint8_t *tmp = nullptr;
-    const int width = g->opt.batch_width;
+    int32_t *d_lanes = nullptr;  // roots, then [k] internal sources and [k] rows
+    auto done = [&](int code) {
+        cudaStreamSynchronize(s);
+        cudaFree(tmp);
+        cudaFree(d_lanes);
+        return code;
+    };
+    cudaError_t e;
+    if ((e = cudaMalloc(&d_lanes, (size_t)k * 3 * 4)) != cudaSuccess) return done(cuda_error(e, "cudaMalloc(batch lanes)"));
     if (!out_dev) {
-        GB_CUDA(cudaMalloc(&tmp, (size_t)width * n));
+        if ((e = cudaMalloc(&tmp, (size_t)width * n)) != cudaSuccess) return done(cuda_error(e, "cudaMalloc(batch rows)"));
         d_out = tmp;
     }
-    bool depth = false;
-    for (int32_t b0 = 0; b0 < k && rc == BFS_OK; b0 += width) {
+    int32_t *d_roots = d_lanes, *d_src = d_lanes + k, *d_rows = d_lanes + 2 * (size_t)k;
+    if ((e = cudaMemcpyAsync(d_roots, roots, (size_t)k * 4, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+        return done(cuda_error(e, "cudaMemcpy(batch roots)"));
+    batch_lanes_kernel<<<(unsigned)((k + 255) / 256), 256, 0, s>>>(d_roots, g->d_perm, k, out_dev ? 1 : 0, width, d_src,
+                                                                 d_rows);
+    if ((rc = ms_reset(g)) != BFS_OK) return done(rc);
+    const MsParams p0 = make_params(g, w, 0);
+    for (int32_t b0 = 0; b0 < k; b0 += width) {
         const int kb = std::min<int32_t>(width, k - b0);
-        unsigned long long mask = (kb == 64) ? ~0ull : ((1ull << kb) - 1ull);
-        int32_t src[64], rows[64];
-        for (int i = 0; i < 64; ++i) {
-            src[i] = i < kb ? roots[b0 + i] : 0;
-            rows[i] = i < kb ? (out_dev ? b0 + i : i) : -1;
-        }
-        if ((rc = ms_reset(g)) != BFS_OK) break;
-        if ((rc = ms_inject(g, src, mask)) != BFS_OK) break;
-        if ((rc = ms_step(g, 0x7FFFFFFFu)) != BFS_OK) break;
-        MsCtrl st;
-        if ((rc = ms_read_ctrl(g, &st)) != BFS_OK) break;
-        if (st.status & ST_TIMEOUT) rc = set_error(BFS_ERR_TIMEOUT, "bfs_run_batch: a device-side wait ran out");
-        else if (st.status & ST_OVERFLOW) rc = set_error(BFS_ERR_CUDA, "bfs_run_batch: a frontier append ran past its capacity");
-        if (st.status & ST_DEPTH) depth = true;
-        if (rc != BFS_OK) break;
-        if ((rc = ms_extract(g, mask, rows, d_out, n, false)) != BFS_OK) break;
-        if (!out_dev) {
-            cudaError_t e = cudaMemcpyAsync(level_out + (size_t)b0 * n, d_out, (size_t)kb * n, cudaMemcpyDeviceToHost, w->stream);
-            if (e != cudaSuccess) rc = cuda_error(e, "cudaMemcpy(batch levels)");
-        }
+        const unsigned long long mask = (kb == 64) ? ~0ull : ((1ull << kb) - 1ull);
+        ms_inject_kernel<<<8, 256, 0, s>>>(p0, d_src + b0, mask, w->start);
+        if ((e = cudaGetLastError()) != cudaSuccess) return done(cuda_error(e, "ms_inject_kernel"));
+        if ((rc = ms_step(g, 0x7FFFFFFFu)) != BFS_OK) return done(rc);
+        const int64_t blocks = (n + 127) / 128;
+        ms_extract_kernel<<<(unsigned)blocks, 128, 0, s>>>(w->lvl, w->seen, g->d_perm, n, mask, d_rows + b0, d_out, n, 1,
+                                                          w->ctrl);
+        if ((e = cudaGetLastError()) != cudaSuccess) return done(cuda_error(e, "ms_extract_kernel"));
+        if (!out_dev && (e = cudaMemcpyAsync(level_out + (size_t)b0 * n, d_out, (size_t)kb * n, cudaMemcpyDeviceToHost,
+                                             s)) != cudaSuccess)
+            return done(cuda_error(e, "cudaMemcpy(batch levels)"));
     }
-    cudaError_t e = cudaStreamSynchronize(w->stream);
-    if (rc == BFS_OK && e != cudaSuccess) rc = cuda_error(e, "bfs_run_batch");
-    cudaFree(tmp);
-    if (rc == BFS_OK && depth) rc = set_error(BFS_ERR_DEPTH, "bfs_run_batch: a level exceeds 254");
-    return rc;
+    MsCtrl st;
+    if ((rc = ms_read_ctrl(g, &st)) != BFS_OK) return done(rc);
+    if (st.status & ST_TIMEOUT) return done(set_error(BFS_ERR_TIMEOUT, "bfs_run_batch: a device-side wait ran out"));
+    if (st.status & ST_OVERFLOW)
+        return done(set_error(BFS_ERR_CUDA, "bfs_run_batch: a frontier append ran past its capacity"));
+    if (st.status & ST_DEPTH) return done(set_error(BFS_ERR_DEPTH, "bfs_run_batch: a level exceeds 254"));
+    return done(BFS_OK);
 }
 
 }  // namespace gbbfs
