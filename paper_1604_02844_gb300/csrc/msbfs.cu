@@ -40,6 +40,7 @@
 // two bounded grid barriers per iteration.
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
 
 #include <algorithm>
 
@@ -57,7 +58,6 @@ constexpr int UX = 4;    // 32-edge batches per warp in flight
 constexpr int GRAB = 4;  // frontier entries a warp takes from the dispenser at a time: few, so
                          // that runs of hub slices (up to GRAB * H edges) do not leave one warp
                          // working while the grid waits at the barrier
-constexpr int MS_WPB = 8;
 
 struct MsParams {
     const int32_t *__restrict__ ro;
@@ -401,6 +401,7 @@ __device__ __forceinline__ void ms_pull(const MsParams &p, int par, unsigned lon
     }
 }
 
+template <int MS_WPB>
 __global__ void __launch_bounds__(MS_WPB * 32) ms_kernel(MsParams p)
 {
     __shared__ int s_ok;
@@ -646,6 +647,10 @@ void ms_free(Graph *g)
     cudaFree(w->lane_row);
     if (w->h_ctrl) cudaFreeHost(w->h_ctrl);
     if (w->h_lanes) cudaFreeHost(w->h_lanes);
+    if (w->b_exec) cudaGraphExecDestroy(w->b_exec);
+    cudaFree(w->b_lanes);
+    if (w->h_roots) cudaFreeHost(w->h_roots);
+    cudaFree(w->b_tmp);
     if (w->stream) cudaStreamDestroy(w->stream);
     delete w;
     g->batch_ws = nullptr;
@@ -715,24 +720,32 @@ int ms_inject(Graph *g, const int32_t *lane_src_caller, unsigned long long mask)
     return BFS_OK;
 }
 
-// Run up to max_iters iterations (stops early when no lane has a frontier),
-// with at most max_ctas CTAs (0 = as many as fit).
-int ms_step_capped(Graph *g, uint32_t max_iters, int max_ctas)
+// One cooperative launch of ms_kernel with CTAs of MS_WPB warps.
+template <int MS_WPB>
+static int launch_ms(Graph *g, MsWs *w, const MsParams &prm, int max_ctas)
 {
-    MsWs *w = ws_of(g);
-    MsParams p = make_params(g, w, max_iters);
-    auto kern = ms_kernel;
+    auto kern = ms_kernel<MS_WPB>;
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, MS_WPB * 32, 0);
     if (e != cudaSuccess) return cuda_error(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor(ms_kernel)");
     if (per_sm < 1) return set_error(BFS_ERR_CUDA, "ms_kernel: no CTA fits on an SM");
-    per_sm = std::min(per_sm, 4);
+    per_sm = std::min(per_sm, 32 / MS_WPB);  // up to 32 warps per SM
     int grid = per_sm * g->num_sms;
     if (max_ctas > 0) grid = std::min(grid, max_ctas);
+    MsParams p = prm;
     void *args[] = {&p};
     e = cudaLaunchCooperativeKernel((const void *)kern, dim3(grid), dim3(MS_WPB * 32), args, 0, w->stream);
     if (e != cudaSuccess) return cuda_error(e, "cudaLaunchCooperativeKernel(ms_kernel)");
     return BFS_OK;
+}
+
+// Run up to max_iters iterations (stops early when no lane has a frontier),
+// with at most max_ctas CTAs (0 = as many as fit) of BATCH_BLOCK threads.
+int ms_step_capped(Graph *g, uint32_t max_iters, int max_ctas)
+{
+    MsWs *w = ws_of(g);
+    const MsParams p = make_params(g, w, max_iters);
+    return g->opt.batch_block == 512 ? launch_ms<16>(g, w, p, max_ctas) : launch_ms<8>(g, w, p, max_ctas);
 }
 
 int ms_step(Graph *g, uint32_t max_iters) { return ms_step_capped(g, max_iters, g->opt.max_ctas); }
@@ -781,13 +794,46 @@ __global__ void batch_lanes_kernel(const int32_t *__restrict__ roots, const int3
     }
 }
 
+// The launch sequence of one bfs_run_batch call, on the workspace stream:
+// the roots from the pinned staging buffer to the device, their internal ids
+// and output rows, a workspace reset, then per batch of `width` sources:
+// inject the lanes from device memory, run to completion, extract the level
+// rows with lane recycling (which leaves the workspace clean for the next
+// batch) and, for host outputs, copy the rows back.  No host round trip.
+static int enqueue_batches(Graph *g, MsWs *w, int32_t k, uint8_t *level_out, bool out_dev, uint8_t *d_out)
+{
+    const int64_t n = g->n;
+    cudaStream_t s = w->stream;
+    const int width = g->opt.batch_width;
+    int32_t *d_roots = w->b_lanes, *d_src = w->b_lanes + w->b_cap, *d_rows = w->b_lanes + 2 * w->b_cap;
+    GB_CUDA(cudaMemcpyAsync(d_roots, w->h_roots, (size_t)k * 4, cudaMemcpyHostToDevice, s));
+    batch_lanes_kernel<<<(unsigned)((k + 255) / 256), 256, 0, s>>>(d_roots, g->d_perm, k, out_dev ? 1 : 0, width, d_src,
+                                                                 d_rows);
+    GB_CUDA(cudaGetLastError());
+    int rc = ms_reset(g);
+    if (rc != BFS_OK) return rc;
+    const MsParams p0 = make_params(g, w, 0);
+    for (int32_t b0 = 0; b0 < k; b0 += width) {
+        const int kb = std::min<int32_t>(width, k - b0);
+        const unsigned long long mask = (kb == 64) ? ~0ull : ((1ull << kb) - 1ull);
+        ms_inject_kernel<<<8, 256, 0, s>>>(p0, d_src + b0, mask, w->start);
+        GB_CUDA(cudaGetLastError());
+        if ((rc = ms_step(g, 0x7FFFFFFFu)) != BFS_OK) return rc;
+        ms_extract_kernel<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(w->lvl, w->seen, g->d_perm, n, mask, d_rows + b0,
+                                                                     d_out, n, 1, w->ctrl);
+        GB_CUDA(cudaGetLastError());
+        if (!out_dev)
+            GB_CUDA(cudaMemcpyAsync(level_out + (size_t)b0 * n, d_out, (size_t)kb * n, cudaMemcpyDeviceToHost, s));
+    }
+    return BFS_OK;
+}
+
 // bfs_run_batch: batches of `batch_width` sources, each run to completion.
-// The sources (mapped to internal ids) and output rows of every batch are
-// put on the device first; the batches then follow each other on the
-// workspace stream with no host round trip: each batch's lanes are injected
-// from device memory, run to completion, and extracted with recycling
-// (which leaves the workspace clean for the next batch).  Device-side status
-// bits accumulate over the batches and are read once at the end.
+// The first call of a shape (k, output buffer, options) captures the launch
+// sequence into a CUDA graph (persistent cooperative kernels included); a
+// later call of the same shape copies its roots to the staging buffer and
+// replays the graph.  Device-side status bits accumulate over the batches
+// and are read once at the end.
 int ms_run_batch(Graph *g, const int32_t *roots, int32_t k, uint8_t *level_out)
 {
     MsWs *w = nullptr;
@@ -798,49 +844,69 @@ int ms_run_batch(Graph *g, const int32_t *roots, int32_t k, uint8_t *level_out)
     cudaStream_t s = w->stream;
     const bool out_dev = is_device_pointer(level_out);
     const int width = g->opt.batch_width;
-    uint8_t *d_out = level_out;
-    uint8_t *tmp = nullptr;
-    int32_t *d_lanes = nullptr;  // roots, then [k] internal sources and [k] rows
-    auto done = [&](int code) {
-        cudaStreamSynchronize(s);
-        cudaFree(tmp);
-        cudaFree(d_lanes);
-        return code;
+    // buffers sized for this call (a new buffer invalidates the captured graph)
+    auto drop_graph = [&] {
+        if (w->b_exec) cudaGraphExecDestroy(w->b_exec);
+        w->b_exec = nullptr;
+        w->b_key = MsWs::Key{};
     };
-    cudaError_t e;
-    if ((e = cudaMalloc(&d_lanes, (size_t)k * 3 * 4)) != cudaSuccess) return done(cuda_error(e, "cudaMalloc(batch lanes)"));
-    if (!out_dev) {
-        if ((e = cudaMalloc(&tmp, (size_t)width * n)) != cudaSuccess) return done(cuda_error(e, "cudaMalloc(batch rows)"));
-        d_out = tmp;
+    if (w->b_cap < k) {
+        drop_graph();
+        cudaFree(w->b_lanes);
+        if (w->h_roots) cudaFreeHost(w->h_roots);
+        w->b_lanes = nullptr;
+        w->h_roots = nullptr;
+        w->b_cap = 0;
+        GB_CUDA(cudaMalloc(&w->b_lanes, (size_t)k * 3 * 4));
+        GB_CUDA(cudaMallocHost(&w->h_roots, (size_t)k * 4));
+        w->b_cap = k;
     }
-    int32_t *d_roots = d_lanes, *d_src = d_lanes + k, *d_rows = d_lanes + 2 * (size_t)k;
-    if ((e = cudaMemcpyAsync(d_roots, roots, (size_t)k * 4, cudaMemcpyHostToDevice, s)) != cudaSuccess)
-        return done(cuda_error(e, "cudaMemcpy(batch roots)"));
-    batch_lanes_kernel<<<(unsigned)((k + 255) / 256), 256, 0, s>>>(d_roots, g->d_perm, k, out_dev ? 1 : 0, width, d_src,
-                                                                 d_rows);
-    if ((rc = ms_reset(g)) != BFS_OK) return done(rc);
-    const MsParams p0 = make_params(g, w, 0);
-    for (int32_t b0 = 0; b0 < k; b0 += width) {
-        const int kb = std::min<int32_t>(width, k - b0);
-        const unsigned long long mask = (kb == 64) ? ~0ull : ((1ull << kb) - 1ull);
-        ms_inject_kernel<<<8, 256, 0, s>>>(p0, d_src + b0, mask, w->start);
-        if ((e = cudaGetLastError()) != cudaSuccess) return done(cuda_error(e, "ms_inject_kernel"));
-        if ((rc = ms_step(g, 0x7FFFFFFFu)) != BFS_OK) return done(rc);
-        const int64_t blocks = (n + 127) / 128;
-        ms_extract_kernel<<<(unsigned)blocks, 128, 0, s>>>(w->lvl, w->seen, g->d_perm, n, mask, d_rows + b0, d_out, n, 1,
-                                                          w->ctrl);
-        if ((e = cudaGetLastError()) != cudaSuccess) return done(cuda_error(e, "ms_extract_kernel"));
-        if (!out_dev && (e = cudaMemcpyAsync(level_out + (size_t)b0 * n, d_out, (size_t)kb * n, cudaMemcpyDeviceToHost,
-                                             s)) != cudaSuccess)
-            return done(cuda_error(e, "cudaMemcpy(batch levels)"));
+    if (!out_dev && w->b_tmp_width < width) {
+        drop_graph();
+        cudaFree(w->b_tmp);
+        w->b_tmp = nullptr;
+        w->b_tmp_width = 0;
+        GB_CUDA(cudaMalloc(&w->b_tmp, (size_t)width * n));
+        w->b_tmp_width = width;
+    }
+    uint8_t *d_out = out_dev ? level_out : w->b_tmp;
+    memcpy(w->h_roots, roots, (size_t)k * 4);
+
+    MsWs::Key key;
+    key.k = k;
+    key.out = level_out;
+    key.out_dev = out_dev ? 1 : 0;
+    key.width = width;
+    key.block = g->opt.batch_block;
+    key.max_ctas = g->opt.max_ctas;
+    key.timeout_ns = g->opt.timeout_ns;
+    if (!(w->b_exec && w->b_key == key)) {
+        drop_graph();
+        cudaGraph_t graph = nullptr;
+        bool captured = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        if (captured) {
+            const int erc = enqueue_batches(g, w, k, level_out, out_dev, d_out);
+            captured = cudaStreamEndCapture(s, &graph) == cudaSuccess && erc == BFS_OK && graph;
+            if (captured) captured = cudaGraphInstantiate(&w->b_exec, graph, 0) == cudaSuccess;
+            if (graph) cudaGraphDestroy(graph);
+            if (!captured) w->b_exec = nullptr;
+        }
+        cudaGetLastError();  // a failed capture leaves no sticky error
+        clear_error();
+        if (captured) w->b_key = key;
+    }
+    if (w->b_exec) {
+        GB_CUDA(cudaGraphLaunch(w->b_exec, s));
+    } else if ((rc = enqueue_batches(g, w, k, level_out, out_dev, d_out)) != BFS_OK) {
+        cudaStreamSynchronize(s);
+        return rc;
     }
     MsCtrl st;
-    if ((rc = ms_read_ctrl(g, &st)) != BFS_OK) return done(rc);
-    if (st.status & ST_TIMEOUT) return done(set_error(BFS_ERR_TIMEOUT, "bfs_run_batch: a device-side wait ran out"));
-    if (st.status & ST_OVERFLOW)
-        return done(set_error(BFS_ERR_CUDA, "bfs_run_batch: a frontier append ran past its capacity"));
-    if (st.status & ST_DEPTH) return done(set_error(BFS_ERR_DEPTH, "bfs_run_batch: a level exceeds 254"));
-    return done(BFS_OK);
+    if ((rc = ms_read_ctrl(g, &st)) != BFS_OK) return rc;
+    if (st.status & ST_TIMEOUT) return set_error(BFS_ERR_TIMEOUT, "bfs_run_batch: a device-side wait ran out");
+    if (st.status & ST_OVERFLOW) return set_error(BFS_ERR_CUDA, "bfs_run_batch: a frontier append ran past its capacity");
+    if (st.status & ST_DEPTH) return set_error(BFS_ERR_DEPTH, "bfs_run_batch: a level exceeds 254");
+    return BFS_OK;
 }
 
 }  // namespace gbbfs

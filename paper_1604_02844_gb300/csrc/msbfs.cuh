@@ -38,6 +38,24 @@ struct MsWs {
     int32_t *h_lanes = nullptr;   // pinned, 128 entries
     int64_t fcap = 0;
     cudaStream_t stream = nullptr;
+    // bfs_run_batch: buffers and the captured launch sequence of the last call shape
+    int32_t *b_lanes = nullptr;   // [3][b_cap] roots, internal sources, output rows
+    int32_t *h_roots = nullptr;   // pinned staging of the roots
+    int64_t b_cap = 0;
+    uint8_t *b_tmp = nullptr;     // [b_tmp_width][n] level rows for host outputs
+    int b_tmp_width = 0;
+    cudaGraphExec_t b_exec = nullptr;
+    struct Key {
+        int32_t k = -1;
+        uint8_t *out = nullptr;
+        int out_dev = 0, width = 0, block = 0, max_ctas = 0;
+        int64_t timeout_ns = 0;
+        bool operator==(const Key &o) const
+        {
+            return k == o.k && out == o.out && out_dev == o.out_dev && width == o.width && block == o.block &&
+                   max_ctas == o.max_ctas && timeout_ns == o.timeout_ns;
+        }
+    } b_key;
 };
 
 int ms_alloc(Graph *g, MsWs **out);

@@ -162,3 +162,22 @@ def test_pull_steps_and_push_steps_agree():
         np.testing.assert_array_equal(batch_levels(g, roots), ref)
     with gb.Graph(ro, col_rev) as g:
         np.testing.assert_array_equal(batch_levels(g, roots), ref)
+
+
+def test_repeated_calls_replay_the_captured_sequence():
+    """The second call of a shape replays the launch sequence captured by the
+    first, with the new roots; a changed option or output re-captures it."""
+    ro, col = graphgen.kronecker(13, 16, 41)
+    n = len(ro) - 1
+    with gb.Graph(ro, col) as g:
+        dev_out = torch.empty((100, n), dtype=torch.uint8, device="cuda")
+        host_out = np.empty((100, n), np.uint8)
+        for rep, seed in enumerate((41, 42, 43, 44)):
+            roots = graphgen.pick_roots(ro, 100, seed)
+            ref = oracle.bfs_batch(ro, col, roots)
+            if rep == 2:
+                g.set_option("batch_width", 32)
+            gb.bfs_run_batch(g.handle, roots, dev_out)
+            np.testing.assert_array_equal(dev_out.cpu().numpy(), ref, err_msg=f"device output, call {rep}")
+            gb.bfs_run_batch(g.handle, roots, host_out)
+            np.testing.assert_array_equal(host_out, ref, err_msg=f"host output, call {rep}")
