@@ -181,3 +181,20 @@ def test_repeated_calls_replay_the_captured_sequence():
             np.testing.assert_array_equal(dev_out.cpu().numpy(), ref, err_msg=f"device output, call {rep}")
             gb.bfs_run_batch(g.handle, roots, host_out)
             np.testing.assert_array_equal(host_out, ref, err_msg=f"host output, call {rep}")
+
+
+def test_bounded_wait_times_out_and_next_call_is_exact():
+    """Device waits limited to 0 ns: bfs_run_batch reports BFS_ERR_TIMEOUT;
+    with the limit restored the next call on the same workspace is exact."""
+    ro, col = graphgen.kronecker(12, 16, 62)
+    roots = graphgen.pick_roots(ro, 70, 62)
+    n = len(ro) - 1
+    with gb.Graph(ro, col) as g:
+        out = torch.empty((len(roots), n), dtype=torch.uint8, device="cuda")
+        g.set_option("timeout_ns", 0)
+        with pytest.raises(gb.BfsError) as ei:
+            gb.bfs_run_batch(g.handle, roots, out)
+        assert ei.value.status == gb.BFS_ERR_TIMEOUT
+        g.set_option("timeout_ns", 4_000_000_000)
+        gb.bfs_run_batch(g.handle, roots, out)
+        np.testing.assert_array_equal(out.cpu().numpy(), oracle.bfs_batch(ro, col, roots))

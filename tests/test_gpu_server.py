@@ -123,3 +123,31 @@ def test_submit_errors(resident):
             s.submit(gid + 5, 0, buf)
         with pytest.raises(gb.BfsError):
             gb.bfs_poll(s.handle, 12345)
+
+
+def test_device_timeout_fails_queries_without_hanging():
+    """Device waits limited to 0 ns: the graph's batched search gives up at
+    its first grid barrier.  The server reports BFS_ERR_TIMEOUT for every
+    query instead of leaving callers waiting, refuses new queries, and shuts
+    down cleanly; no GPU fault is involved."""
+    ro, col = graphgen.kronecker(12, 16, 61)
+    roots = graphgen.pick_roots(ro, 4, 61)
+    n = len(ro) - 1
+    with gb.Graph(ro, col) as g:
+        g.set_option("timeout_ns", 0)
+        s = gb.Server()
+        try:
+            gid = s.add_graph(g)
+            bufs = [np.empty(n, np.uint8) for _ in roots]
+            tickets = [s.submit(gid, int(r), b) for r, b in zip(roots, bufs)]
+            with pytest.raises(gb.BfsError) as ei:
+                s.drain()
+            assert ei.value.status == gb.BFS_ERR_TIMEOUT
+            for t in tickets:
+                with pytest.raises(gb.BfsError) as ei:
+                    s.poll(t)
+                assert ei.value.status == gb.BFS_ERR_TIMEOUT
+            with pytest.raises(gb.BfsError):
+                s.submit(gid, int(roots[0]), bufs[0])
+        finally:
+            s.close()
