@@ -202,7 +202,10 @@ int Server::round(GraphState &gs)
         if (rc != BFS_OK) return rc;
     }
     if (!running) return BFS_OK;
-    const int share = std::max(gs.g->num_sms, total_ctas / std::max(1, active));
+    // the GPU's CTAs (of 256 threads) shared among the graphs with work; a
+    // graph set to 512-thread CTAs gets half as many
+    const int per_cta = gs.g->opt.batch_block == 512 ? 2 : 1;
+    const int share = std::max(gs.g->num_sms, total_ctas / std::max(1, active)) / per_cta;
     int rc = ms_step_capped(gs.g, iters_per_step, share);
     if (rc != BFS_OK) return rc;
     MsCtrl &st = gs.last;
