@@ -93,11 +93,13 @@ typedef enum {
                                    the first run in this mode;
                                    3 = direction-optimising: layers run as in mode 0
                                    or bottom-up (every unvisited vertex looks for a
-                                   parent in the frontier bitmap), chosen per layer by
-                                   ALPHA and BETA; bottom-up only on graphs where every
-                                   edge (u, v) has its reverse (checked at creation),
-                                   else every layer is top-down; BLOCK 256 or 512;
-                                   2 bitmaps of workspace, allocated on first use      */
+                                   parent among its in-neighbours in the frontier
+                                   bitmap), chosen per layer by ALPHA and BETA; on a
+                                   graph where some edge (u, v) lacks its reverse
+                                   (checked at creation) the in-edges come from a
+                                   transposed CSR built on the first run in this mode
+                                   (4(n+m) bytes); BLOCK 256 or 512; 2 bitmaps of
+                                   workspace, allocated on first use                   */
     BFS_OPT_ALPHA = 12,         /* mode 3: a layer runs bottom-up once the frontier's
                                    summed degree exceeds (edges of unreached vertices)
                                    / ALPHA (0 .. 2^30, default 14; 0 = never)          */

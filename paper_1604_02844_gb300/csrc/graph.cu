@@ -87,6 +87,8 @@ static void free_graph(Graph *g)
     cudaFree(g->d_vo);
     cudaFree(g->d_front[0]);
     cudaFree(g->d_front[1]);
+    cudaFree(g->d_tro);
+    cudaFree(g->d_tcol);
     cudaFree(g->d_pint);
     cudaFree(g->d_ctrl);
     cudaFree(g->d_stats);
@@ -127,12 +129,13 @@ static int alloc_restore(Graph *g)
     return BFS_OK;
 }
 
-// Hybrid-mode frontier bitmaps (bottom-up layers), allocated the first time
-// that mode runs.
+// Hybrid-mode frontier bitmaps (bottom-up layers) and, on a graph that is
+// not symmetric, the in-edge CSR they scan, built the first time that mode runs.
 static int alloc_hybrid(Graph *g)
 {
-    if (g->d_front[0]) return BFS_OK;
-    for (int b = 0; b < 2; ++b) GB_CUDA(cudaMalloc(&g->d_front[b], (size_t)g->bitmap_words * 4));
+    if (!g->d_front[0])
+        for (int b = 0; b < 2; ++b) GB_CUDA(cudaMalloc(&g->d_front[b], (size_t)g->bitmap_words * 4));
+    if (!g->symmetric && !g->d_tro) return transpose_graph(g);
     return BFS_OK;
 }
 

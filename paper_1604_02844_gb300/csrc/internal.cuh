@@ -96,6 +96,8 @@ struct Graph {
     int64_t qcap = 0, bqcap = 0;
     uint2 *d_vo = nullptr;         // restoration mode (lazy): (visited, output) word pairs
     uint32_t *d_front[2] = {};     // hybrid mode (lazy): frontier bitmaps of bottom-up layers
+    int32_t *d_tro = nullptr;      // hybrid mode on a non-symmetric graph (lazy): in-edge CSR
+    int32_t *d_tcol = nullptr;
     int32_t *d_pint = nullptr;     // restoration mode (lazy): internal predecessors
     Ctrl *d_ctrl = nullptr;
     int64_t *d_stats = nullptr;    // [kMaxStatLayers][4]: vertices, edges, new, t_end_ns
@@ -131,6 +133,7 @@ void ms_free(Graph *g);
 
 // implemented in relabel.cu
 int relabel_graph(Graph *g, const int32_t *d_ro, const int32_t *d_col);
+int transpose_graph(Graph *g);  // d_tro / d_tcol from the internal CSR
 int bitmap_to_caller(Graph *g, uint32_t *d_out);
 
 bool is_device_pointer(const void *p);

@@ -212,6 +212,24 @@ __global__ void bitmap_to_caller_kernel(const uint32_t *__restrict__ bm, const i
 
 }  // namespace
 
+// In-degree of every vertex (internal numbering), into tro[v].
+__global__ void indeg_kernel(const int32_t *__restrict__ col, int64_t m, int32_t *tro)
+{
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(tro + col[e], 1);
+}
+
+// One warp per row u: every edge (u, v) lands in v's in-list.
+__global__ void scatter_in_kernel(const int32_t *__restrict__ ro, const int32_t *__restrict__ col, int64_t n,
+                                  int32_t *cursor, int32_t *tcol)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t u = w0; u < n; u += nw)
+        for (int k = ro[u] + lane; k < ro[u + 1]; k += 32) tcol[atomicAdd(cursor + col[k], 1)] = (int32_t)u;
+}
+
 // Build g->d_row_offsets / d_col_idx (internal numbering), g->d_perm and
 // g->d_orig from a validated device CSR in the caller's numbering.
 int relabel_graph(Graph *g, const int32_t *d_ro, const int32_t *d_col)
@@ -278,6 +296,43 @@ int bitmap_to_caller(Graph *g, uint32_t *d_out)
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(e, "bitmap_to_caller_kernel");
     return BFS_OK;
+}
+
+}  // namespace gbbfs
+
+namespace gbbfs {
+
+// The transposed CSR (in-edges, internal numbering) for bottom-up layers on
+// a graph that is not symmetric: in-degrees, their exclusive scan, then the
+// edges scattered into the in-lists (list order is not defined).
+int transpose_graph(Graph *g)
+{
+    const int64_t n = g->n, m = g->m;
+    const int64_t ntile = (n + TILE - 1) / TILE;
+    int32_t *cursor = nullptr, *tsum = nullptr;
+    int rc = BFS_OK;
+    cudaError_t e;
+    if ((e = cudaMalloc(&g->d_tro, (size_t)(n + 1) * 4)) != cudaSuccess) return cuda_error(e, "cudaMalloc(in-edge offsets)");
+    if ((e = cudaMalloc(&g->d_tcol, (size_t)(((m + 3) / 4) * 4 + 4) * 4)) != cudaSuccess) return cuda_error(e, "cudaMalloc(in-edges)");
+    if ((e = cudaMalloc(&cursor, (size_t)(n + 1) * 4)) != cudaSuccess) { rc = cuda_error(e, "cudaMalloc(cursor)"); goto done; }
+    if ((e = cudaMalloc(&tsum, (size_t)(ntile + 1) * 4)) != cudaSuccess) { rc = cuda_error(e, "cudaMalloc(tile sums)"); goto done; }
+    if ((e = cudaMemset(g->d_tro, 0, (size_t)(n + 1) * 4)) != cudaSuccess) { rc = cuda_error(e, "cudaMemset(in-degrees)"); goto done; }
+    indeg_kernel<<<g->num_sms * 8, 256>>>(g->d_col_idx, m, g->d_tro);
+    tile_scan_kernel<<<(unsigned)ntile, 256>>>(g->d_tro, n, tsum);
+    scan_single_block_kernel<<<1, SCAN_T>>>(tsum, ntile, nullptr);
+    tile_add_kernel<<<(unsigned)ntile, 256>>>(g->d_tro, n, tsum, m);
+    if ((e = cudaMemcpy(cursor, g->d_tro, (size_t)(n + 1) * 4, cudaMemcpyDeviceToDevice)) != cudaSuccess) { rc = cuda_error(e, "cudaMemcpy(cursor)"); goto done; }
+    scatter_in_kernel<<<g->num_sms * 16, 256>>>(g->d_row_offsets, g->d_col_idx, n, cursor, g->d_tcol);
+    if ((e = cudaDeviceSynchronize()) != cudaSuccess) rc = cuda_error(e, "transpose_graph");
+done:
+    cudaFree(cursor);
+    cudaFree(tsum);
+    if (rc != BFS_OK) {
+        cudaFree(g->d_tro);
+        cudaFree(g->d_tcol);
+        g->d_tro = g->d_tcol = nullptr;
+    }
+    return rc;
 }
 
 }  // namespace gbbfs

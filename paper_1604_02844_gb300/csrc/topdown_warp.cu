@@ -36,11 +36,12 @@
 //
 // Mode 3 (HYB) is the direction-optimising search (the bottom-up steps of the
 // hybrid algorithm that Sec. 3 calls the state of the art and Sec. 8 plans
-// for) on graphs whose every edge has its reverse: a layer runs bottom-up once the frontier's edges
-// exceed the unexplored edges / alpha, and top-down again once the frontier
-// has fewer than n / beta vertices.  In a bottom-up layer each warp owns
-// whole visited words (dealt round-robin); every unvisited vertex scans its
-// row (sorted, so hubs come first) until it meets a vertex of the frontier
+// for): a layer runs bottom-up once the frontier's edges exceed the
+// unexplored edges / alpha, and top-down again once the frontier has fewer
+// than n / beta vertices.  In a bottom-up layer each warp owns whole visited
+// words (dealt round-robin); every unvisited vertex scans its in-edges (the
+// CSR itself when every edge has its reverse, whose sorted rows put the hubs
+// first; else the transposed CSR) until it meets a vertex of the frontier
 // bitmap, whose low (hub) words sit in the CTA's shared memory.
 //
 // All waits are bounded (grid barrier timeout -> ST_TIMEOUT, clean exit).
@@ -87,10 +88,11 @@ struct WParams {
     int32_t n;
     int32_t root;
     int64_t m;            // directed entries (sum of degrees)
-    int32_t split32;      // internal ids below have degree >= 32
     int32_t n_nonzero;    // internal ids below have degree >= 1
     int32_t alpha, beta;  // mode 3 switching parameters
-    int32_t symmetric;    // mode 3 goes bottom-up only if every edge has its reverse
+    const int32_t *__restrict__ bro;   // mode 3: in-edge CSR of bottom-up layers (the CSR itself
+    const int32_t *__restrict__ bcol;  // when every edge has its reverse); null: top-down only
+    int32_t bu_n;         // mode 3: vertices a bottom-up layer may reach (internal ids below)
     uint32_t ecap, ucap, hcap;
     int32_t bitmap_words;
     uint64_t timeout_ns;
@@ -668,10 +670,9 @@ __device__ __forceinline__ void bottom_up(CtaSmem<WPB> &cs, const WParams &p, co
         bool has = false;
         if (lw < nwords) {
             lraw = __ldcg(p.bitmap + lw);
-            const int64_t first = lw * 32;  // vertices >= n_nonzero have no edge: never reached
-            const unsigned valid = first >= p.n_nonzero ? 0u
-                                   : (p.n_nonzero - first >= 32 ? 0xffffffffu
-                                                                : (1u << (p.n_nonzero - first)) - 1u);
+            const int64_t first = lw * 32;  // vertices >= bu_n have no in-edge: never reached
+            const unsigned valid = first >= p.bu_n ? 0u
+                                   : (p.bu_n - first >= 32 ? 0xffffffffu : (1u << (p.bu_n - first)) - 1u);
             lseen = lraw | ~valid;
             has = lseen != 0xffffffffu;
             if (!has) Fn[lw] = 0u;
@@ -694,8 +695,8 @@ __device__ __forceinline__ void bottom_up(CtaSmem<WPB> &cs, const WParams &p, co
             }
 #pragma unroll
             for (int j = 0; j < VW; ++j) {
-                beg[j] = unv[j] ? __ldg(p.ro + v[j]) : 0;
-                end[j] = unv[j] ? __ldg(p.ro + v[j] + 1) : 0;
+                beg[j] = unv[j] ? __ldg(p.bro + v[j]) : 0;
+                end[j] = unv[j] ? __ldg(p.bro + v[j] + 1) : 0;
                 par[j] = -1;
                 e[j] = beg[j];
             }
@@ -704,7 +705,7 @@ __device__ __forceinline__ void bottom_up(CtaSmem<WPB> &cs, const WParams &p, co
                 bool act[VW], any = false;
 #pragma unroll
                 for (int j = 0; j < VW; ++j) {
-                    act[j] = par[j] < 0 && e[j] < end[j] && (v[j] >= p.split32 || e[j] == beg[j]);
+                    act[j] = par[j] < 0 && e[j] < end[j] && (end[j] - beg[j] < 32 || e[j] == beg[j]);
                     any |= act[j];
                 }
                 if (!__any_sync(FULL, any)) break;
@@ -714,7 +715,7 @@ __device__ __forceinline__ void bottom_up(CtaSmem<WPB> &cs, const WParams &p, co
                 for (int j = 0; j < VW; ++j)
 #pragma unroll
                     for (int t = 0; t < PK; ++t)
-                        u[j][t] = (act[j] && e[j] + t < end[j]) ? __ldg(p.col + e[j] + t) : -1;
+                        u[j][t] = (act[j] && e[j] + t < end[j]) ? __ldg(p.bcol + e[j] + t) : -1;
 #pragma unroll
                 for (int j = 0; j < VW; ++j)
 #pragma unroll
@@ -740,7 +741,7 @@ __device__ __forceinline__ void bottom_up(CtaSmem<WPB> &cs, const WParams &p, co
                     int found = -1;
                     for (int e0 = hb; e0 < he; e0 += 32) {
                         const int ee = e0 + lane;
-                        const int u = ee < he ? __ldg(p.col + ee) : -1;
+                        const int u = ee < he ? __ldg(p.bcol + ee) : -1;
                         const bool f = u >= 0 && in_front(sF, ncache, F, u);
                         const unsigned m = __ballot_sync(FULL, f);
                         if (lane == 0) my_edges += (unsigned long long)min(32, he - e0);
@@ -860,7 +861,7 @@ __global__ void __launch_bounds__(WPB * 32, (24 / WPB) > 0 ? (24 / WPB) : 1) td_
             }
             m_seen += mf;
             const unsigned long long m_u = (unsigned long long)p.m > m_seen ? (unsigned long long)p.m - m_seen : 0ull;
-            if (p.symmetric && p.alpha > 0) {
+            if (p.bro && p.alpha > 0) {
                 if (!bu_prev) bu = (double)mf * (double)p.alpha > (double)m_u;
                 else bu = (double)nf * (double)p.beta >= (double)p.n;
             }
@@ -1114,11 +1115,13 @@ int td_warp_launch(Graph *g, int32_t root, int32_t *level, int32_t *parent, cuda
     p.front[0] = hybrid ? g->d_front[0] : nullptr;
     p.front[1] = hybrid ? g->d_front[1] : nullptr;
     p.m = g->m;
-    p.split32 = (int32_t)g->split32;
     p.n_nonzero = (int32_t)g->n_nonzero;
     p.alpha = g->opt.alpha;
     p.beta = g->opt.beta;
-    p.symmetric = g->symmetric ? 1 : 0;
+    p.bro = hybrid ? (g->symmetric ? g->d_row_offsets : g->d_tro) : nullptr;
+    p.bcol = hybrid ? (g->symmetric ? g->d_col_idx : g->d_tcol) : nullptr;
+    if (!p.bcol) p.bro = nullptr;
+    p.bu_n = (int32_t)(g->symmetric ? g->n_nonzero : g->n);
     p.pint = restore ? g->d_pint : nullptr;
     for (int b = 0; b < 2; ++b) {
         p.eu[b] = g->d_eq[b][0];

@@ -115,17 +115,48 @@ def test_cliques_and_shared_leaves():
                 check_root(g, ro, col, r)
 
 
-def test_directed_graph_runs_top_down_only():
-    """Bottom-up needs every edge's reverse; on a directed graph every layer
-    runs top-down, even with the parameters that force bottom-up."""
+@pytest.mark.parametrize("regime", REGIMES)
+def test_directed_graph_bottom_up_on_in_edges(regime):
+    """On a directed graph the bottom-up layers scan in-edges (a transposed
+    CSR built on first use)."""
     rng = np.random.default_rng(3)
     n, ne = 5000, 40000
     src = rng.integers(0, n, ne).astype(np.int32)
     dst = rng.integers(0, n, ne).astype(np.int32)
+    src[:50] = dst[:50]
     ro, col = graphgen.csr_from_tuples(n, src, dst, symmetrize=False, drop_loops=False, dedup=False)
-    with gb.Graph(ro, col, mode=HYB, **REGIMES["bottom_up"]) as g:
+    with gb.Graph(ro, col, mode=HYB, **REGIMES[regime]) as g:
         for r in (0, 1234, 4999):
             check_root(g, ro, col, r)
+
+
+def test_directed_star_reached_through_in_edges():
+    """Edges hub -> leaf only: the leaves have no out-edge (they sort last in
+    the degree order), so a bottom-up layer finds them by their in-edges alone."""
+    leaves = 20000
+    e = [(0, 1 + i) for i in range(leaves)] + [(1 + i, 1 + leaves) for i in range(0, leaves, 7)]
+    ro, col = csr_from_edges(leaves + 2, e, True)
+    for regime in ("bottom_up", "alternate", "default"):
+        with gb.Graph(ro, col, mode=HYB, **REGIMES[regime]) as g:
+            for r in (0, 1, 8):
+                check_root(g, ro, col, r)
+
+
+def test_directed_bottom_up_layers_ran():
+    """Forced bottom-up on a directed Kronecker-shaped graph: some layer's
+    examined edges differ from the top-down count, so the in-edge path ran."""
+    tup_src, tup_dst = graphgen.rmat_tuples(14, 16, 37)
+    n = 1 << 14
+    ro, col = graphgen.csr_from_tuples(n, tup_src, tup_dst, symmetrize=False, drop_loops=True, dedup=True)
+    with gb.Graph(ro, col, mode=HYB, layer_stats=1, **REGIMES["bottom_up"]) as g:
+        for r in graphgen.pick_roots(ro, 3, 37):
+            lv, _ = check_root(g, ro, col, r)
+            v, e, t = g.layer_stats()
+            ov, oe, ot = oracle.layer_profile(ro, lv)
+            np.testing.assert_array_equal(v, ov)
+            np.testing.assert_array_equal(t, ot)
+            if len(e) > 1:
+                assert (e != oe).any()
 
 
 def test_uncleaned_symmetric_graph():
