@@ -5,7 +5,7 @@
 // visited bitmap, word v>>5 bit v&31 as in Listing 1; P[s] = s; layer L_d
 // finished before L_{d+1}, Sec. 3); one persistent cooperative kernel per
 // search.  The difference is who works together: every warp runs its own
-// pipeline with only __syncwarp, so the 20-30 warps of an SM overlap each
+// pipeline with only __syncwarp, so the 16 warps of an SM overlap each
 // other's memory latency instead of meeting at CTA barriers.
 //
 // Frontier layout (built by the warps that discover the vertices):
@@ -18,12 +18,13 @@
 //
 // Work items of a layer (hub slices, then units) are dealt round-robin to
 // the grid's warps; a layer with fewer items than half the warps deals each
-// hub slice in up to 12 parts of >= 32 edges.  Per item a warp: stages the adjacency into its shared
-// buffer with cp.async (issued one item ahead), tests the visited word of
-// every staged edge (12 loads per lane in flight) and compacts the unvisited
-// ones in place with ballots (pass A), then claims those with atomicOr and
-// queues the winners (pass B).  Descriptors and entries of the next items
-// are prefetched into registers while the current item is processed.
+// hub slice in up to 12 parts of >= 32 edges.  Per item a warp: stages the
+// adjacency into its shared buffer with cp.async (issued one item ahead),
+// tests the visited word of every staged edge (12 loads per lane in flight)
+// and compacts the unvisited ones in place with ballots (pass A), then claims
+// those with atomicOr and queues the winners (pass B).  Descriptors and
+// entries of the next items are prefetched into registers while the current
+// item is processed.
 //
 // Mode 2 (RST) is the atomic-free variant of Alg. 3: pass B sets the bit of
 // the output bitmap with a plain read-modify-write (bits of other vertices in
