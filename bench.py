@@ -621,7 +621,9 @@ def run_ours(args):
         batched["uneven_mix"] = uneven_mix_measurement(args, gb, torch, dev, (ro, g))
     serving = None
     if not args.no_serving and rank == 0:
-        serving = serving_measurement(args, gb, torch, dev)
+        with ClockSampler(uuid) as sclocks:
+            serving = serving_measurement(args, gb, torch, dev)
+        serving["clocks"] = sclocks.summary()
     if rank == 0:
         cpu = None
         if not args.no_cpu_baseline:
