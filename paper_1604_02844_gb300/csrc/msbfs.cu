@@ -79,6 +79,44 @@ struct MsParams {
     uint64_t timeout_ns;
 };
 
+// Write the slices of one vertex per lane at positions pos.. of frontier
+// buffer q: `few` slices by the lane itself, or `many` slices by the whole
+// warp together (one vertex after another), so that a hub's hundreds of
+// slices do not hold one lane while the rest of the warp waits.
+__device__ __forceinline__ void write_slices(const MsParams &p, int q, int few, int many, int u, int rb, int len,
+                                             unsigned pos)
+{
+    const int lane = threadIdx.x & 31;
+    for (int s = 0; s < few; ++s) {
+        const unsigned at = pos + (unsigned)s;
+        if (at < p.fcap) {
+            p.fu[q][at] = u;
+            p.fb[q][at] = rb + s * H;
+            p.fl[q][at] = min(H, len - s * H);
+        } else {
+            atomicOr(&p.ctrl->status, ST_OVERFLOW);
+        }
+    }
+    unsigned m = __ballot_sync(FULL, many > 0);
+    while (m) {
+        const int src = __ffs(m) - 1;
+        m &= m - 1;
+        const int hu = __shfl_sync(FULL, u, src), hb = __shfl_sync(FULL, rb, src);
+        const int hl = __shfl_sync(FULL, len, src), hn = __shfl_sync(FULL, many, src);
+        const unsigned hp = __shfl_sync(FULL, pos, src);
+        for (int s = lane; s < hn; s += 32) {
+            const unsigned at = hp + (unsigned)s;
+            if (at < p.fcap) {
+                p.fu[q][at] = hu;
+                p.fb[q][at] = hb + s * H;
+                p.fl[q][at] = min(H, hl - s * H);
+            } else {
+                atomicOr(&p.ctrl->status, ST_OVERFLOW);
+            }
+        }
+    }
+}
+
 // Append the slices of vertex u (degree >= 1) to frontier buffer q.  Called
 // by all lanes of a warp; `want` marks the lanes with a vertex to append.
 __device__ __forceinline__ void append_frontier(const MsParams &p, int q, bool want, int u, int rb, int len)
@@ -102,16 +140,8 @@ __device__ __forceinline__ void append_frontier(const MsParams &p, int q, bool w
         atomicAdd(&p.ctrl->fedges[q], edges);
     }
     base = __shfl_sync(FULL, base, 31);
-    unsigned pos = base + (unsigned)(inc - ns);
-    for (int s = 0; s < ns; ++s, ++pos) {
-        if (pos < p.fcap) {
-            p.fu[q][pos] = u;
-            p.fb[q][pos] = rb + s * H;
-            p.fl[q][pos] = min(H, len - s * H);
-        } else {
-            atomicOr(&p.ctrl->status, ST_OVERFLOW);
-        }
-    }
+    const unsigned pos0 = base + (unsigned)(inc - ns);
+    write_slices(p, q, ns <= 8 ? ns : 0, ns > 8 ? ns : 0, u, rb, len, pos0);
 }
 
 constexpr int TB = 128;  // touched-vertex buffer per warp (shared memory)
@@ -311,17 +341,10 @@ __device__ __forceinline__ void ms_update(const MsParams &p, int par, unsigned n
         base = __shfl_sync(FULL, base, 31);
         unsigned pos = base + (unsigned)(inc - ns);
 #pragma unroll
-        for (int k = 0; k < UU; ++k) {
-            if (!nn[k] || len[k] <= 0) continue;
-            for (int sg = 0; sg * H < len[k]; ++sg, ++pos) {
-                if (pos < p.fcap) {
-                    p.fu[q][pos] = v[k];
-                    p.fb[q][pos] = rb[k] + sg * H;
-                    p.fl[q][pos] = min(H, len[k] - sg * H);
-                } else {
-                    atomicOr(&c->status, ST_OVERFLOW);
-                }
-            }
+        for (int k = 0; k < UU; ++k) {  // warp-uniform calls: every lane takes part
+            const int nk = (nn[k] && len[k] > 0) ? (len[k] + H - 1) / H : 0;
+            write_slices(p, q, nk <= 8 ? nk : 0, nk > 8 ? nk : 0, v[k], rb[k], len[k], pos);
+            pos += (unsigned)nk;
         }
     }
 }
