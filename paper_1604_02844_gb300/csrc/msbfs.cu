@@ -9,9 +9,11 @@
 //   next[v]      lanes that reach v in the current iteration
 // One iteration (all lanes advance one layer):
 //   EXPAND: for every frontier entry (u, beg, len) and every v in its slice
-//           of Adj[u]: nb = front[u] & ~seen[v]; if nb, atomicOr(next[v], nb)
-//           (64-bit); the warp whose atomicOr found next[v] == 0 queues v in
-//           the touched list.
+//           of Adj[u]: nb = front[u] & ~(seen[v] | next[v]); if nb,
+//           atomicOr(next[v], nb) (64-bit); the warp whose atomicOr found
+//           next[v] == 0 queues v in the touched list.  Warps take frontier
+//           entries 4 at a time (the first 4 statically, the rest from an
+//           atomic dispenser) and flatten their edges across the lanes.
 //   UPDATE: for every touched v: nn = next[v] & ~seen[v]; next[v] = 0;
 //           seen[v] |= nn; front[v] = nn; lane i of nn gets level
 //           iter + 1 - start[i]; v is queued for the next EXPAND (vertices of
@@ -36,8 +38,11 @@
 // still far away and would scan their whole adjacency without an early exit
 // (the multi-lane form of the direction-optimising switch).
 //
-// All iterations of a launch run in one persistent cooperative kernel with
-// two bounded grid barriers per iteration.
+// All iterations of a launch run in one persistent cooperative kernel
+// (CTAs of 8 or 16 warps, BFS_OPT_BATCH_BLOCK) with two bounded grid
+// barriers per iteration.  bfs_run_batch captures its whole launch sequence
+// (inject, run, extract per batch) in a CUDA graph and replays it for later
+// calls of the same shape.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
