@@ -4,8 +4,10 @@
 // search of msbfs.cu.  Each graph with work owns a 64-lane workspace and a
 // worker thread with its own CUDA stream, which repeats:
 //   1. put waiting queries into free lanes of the running search (a lane
-//      that joins at iteration t reports levels iter + 1 - t);
-//   2. advance the search a few iterations (one cooperative launch on the
+//      that joins at iteration t reports levels iter + 1 - t) -- unless the
+//      search is in its heavy pull phase, which young lanes would keep from
+//      pulling: then they wait one round and join together;
+//   2. advance the search 4 iterations (one cooperative launch on the
 //      graph's own stream, its grid capped to a share of the GPU so that
 //      several graphs' searches run on the device at the same time);
 //   3. read which lanes still have a frontier; the others are finished:
