@@ -446,10 +446,10 @@ __device__ __forceinline__ void ms_pull(const MsParams &p, int par, unsigned lon
                     p.front[q][v] = nn;
                     alive |= nn;
                     if (nn & over) atomicOr(&c->status, ST_DEPTH);
+                    merge_levels(reinterpret_cast<uint4 *>(p.lvl + (size_t)__ldg(p.orig + v) * 64), nn, s_lv);
                 }
             }
         }
-        merge_row(p.lvl, nn ? __ldg(p.orig + v) : -1, nn, s_lv);  // every lane: loads issued together
         unsigned long long pairs = (unsigned long long)__popcll(nn);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) pairs += __shfl_xor_sync(FULL, pairs, o);
