@@ -268,34 +268,7 @@ __device__ __forceinline__ void merge_levels(uint4 *row, unsigned long long nn, 
     }
 }
 
-// The same merge for the level row of caller vertex ov, or nothing if
-// ov < 0, with no branch around the memory accesses: the whole 64-byte row
-// is loaded (four 16-byte loads in flight, predicated), merged, and the
-// changed chunks stored.  Lanes of a warp with different lane masks then
-// still issue their loads together.
-__device__ __forceinline__ void merge_row(uint8_t *lvl, int ov, unsigned long long nn, const uint32_t *lv)
-{
-    const bool act = ov >= 0;
-    uint4 *row = reinterpret_cast<uint4 *>(lvl + (size_t)(act ? ov : 0) * 64);
-    uint4 x[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) x[q] = act ? row[q] : make_uint4(0u, 0u, 0u, 0u);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const unsigned m16 = act ? (unsigned)(nn >> (16 * q)) & 0xFFFFu : 0u;
-        uint32_t *xw = reinterpret_cast<uint32_t *>(&x[q]);
-#pragma unroll
-        for (int w = 0; w < 4; ++w) {
-            const unsigned m4 = (m16 >> (4 * w)) & 0xFu;
-            const uint32_t bm = ((m4 & 1u) ? 0x000000FFu : 0u) | ((m4 & 2u) ? 0x0000FF00u : 0u) |
-                                ((m4 & 4u) ? 0x00FF0000u : 0u) | ((m4 & 8u) ? 0xFF000000u : 0u);
-            xw[w] = (xw[w] & ~bm) | (lv[4 * q + w] & bm);
-        }
-        if (m16) row[q] = x[q];
-    }
-}
-
-constexpr int UU = 2;  // touched vertices per lane per round (2 and 4 measured)
+constexpr int UU = 4;  // touched vertices per lane per round
 
 __device__ __forceinline__ void ms_update(const MsParams &p, int par, unsigned nF, unsigned iter, unsigned long long &alive,
                                           const uint32_t *s_lv, unsigned long long over)
@@ -322,28 +295,26 @@ __device__ __forceinline__ void ms_update(const MsParams &p, int par, unsigned n
             x[k] = v[k] >= 0 ? __ldcg(p.next + v[k]) : 0ull;
             sn[k] = v[k] >= 0 ? __ldcg(p.seen + v[k]) : 0ull;
         }
-        int ns = 0, ov[UU];
-        // the loads of all UU vertices first, then the stores and merges
+        int ns = 0;
 #pragma unroll
         for (int k = 0; k < UU; ++k) {
             nn[k] = x[k] & ~sn[k];
-            const bool got = v[k] >= 0 && nn[k];
-            ov[k] = got ? __ldg(p.orig + v[k]) : -1;
-            rb[k] = got ? __ldg(p.ro + v[k]) : 0;
-            len[k] = got ? __ldg(p.ro + v[k] + 1) : 0;
-        }
-#pragma unroll
-        for (int k = 0; k < UU; ++k) {
-            if (v[k] >= 0) p.next[v[k]] = 0ull;
-            if (ov[k] >= 0) {
-                p.seen[v[k]] = sn[k] | nn[k];
-                p.front[q][v[k]] = nn[k];
-                alive |= nn[k];
-                if (nn[k] & over) atomicOr(&c->status, ST_DEPTH);
-                len[k] -= rb[k];
-                ns += (len[k] + H - 1) / H;
+            rb[k] = 0;
+            len[k] = 0;
+            if (v[k] >= 0) {
+                p.next[v[k]] = 0ull;
+                if (nn[k]) {
+                    p.seen[v[k]] = sn[k] | nn[k];
+                    p.front[q][v[k]] = nn[k];
+                    alive |= nn[k];
+                    if (nn[k] & over) atomicOr(&c->status, ST_DEPTH);
+                    const int ov = __ldg(p.orig + v[k]);
+                    merge_levels(reinterpret_cast<uint4 *>(p.lvl + (size_t)ov * 64), nn[k], s_lv);
+                    rb[k] = __ldg(p.ro + v[k]);
+                    len[k] = __ldg(p.ro + v[k] + 1) - rb[k];
+                    ns += (len[k] + H - 1) / H;
+                }
             }
-            merge_row(p.lvl, ov[k], nn[k], s_lv);
         }
         {
             unsigned long long pairs = 0;
@@ -459,7 +430,7 @@ __device__ __forceinline__ void ms_pull(const MsParams &p, int par, unsigned lon
 }
 
 template <int MS_WPB>
-__global__ void __launch_bounds__(MS_WPB * 32, 32 / MS_WPB) ms_kernel(MsParams p)
+__global__ void __launch_bounds__(MS_WPB * 32) ms_kernel(MsParams p)
 {
     __shared__ int s_ok;
     __shared__ unsigned s_nF, s_iter0;
