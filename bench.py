@@ -387,6 +387,9 @@ def batched_measurement(args, gb, torch, dev):
                    "plain = CUDA events around back-to-back bfs_run (levels only) on one stream"}
 
 
+_KEEP_ALIVE = []  # objects of a serving run that did not finish
+
+
 def serving_measurement(args, gb, torch, dev):
     """Eight resident Kronecker graphs (scales 12..23; edgefactor 16 from
     scale 16, 8 below), requests choosing a graph with probability
@@ -419,6 +422,22 @@ def serving_measurement(args, gb, torch, dev):
     server = gb.Server()
     ids = [server.add_graph(g) for _, g in graphs]
 
+    class Stuck(Exception):
+        pass
+
+    def wait_all(tickets, limit_s):
+        """Bounded wait for every ticket (a query that never finished would
+        otherwise stop the whole bench line from being printed)."""
+        deadline = time.perf_counter() + limit_s
+        i = 0
+        while i < len(tickets):
+            if server.poll(tickets[i]):
+                i += 1
+                continue
+            if time.perf_counter() > deadline:
+                raise Stuck(f"{len(tickets) - i} of {len(tickets)} queries unfinished after {limit_s:.0f} s")
+            time.sleep(0.0002)
+
     def run(reqs, rate):
         """Submit reqs at Poisson times (rate None = all at once); returns
         (elapsed_s, latencies_s)."""
@@ -443,7 +462,7 @@ def serving_measurement(args, gb, torch, dev):
             t = server.submit(ids[gi], r, b)
             tickets.append(t)
             inflight.append((t, gi, b))
-        server.drain()
+        wait_all(tickets, 120.0 + len(reqs) / 500.0)
         elapsed = time.perf_counter() - t0
         for t, g_, b in inflight:
             pools[g_].append(b)
@@ -454,17 +473,28 @@ def serving_measurement(args, gb, torch, dev):
             lat.append((b2 - a) * 1e-9)
         return elapsed, np.array(lat)
 
-    run(draw(2000), None)  # warm-up: workspaces, kernels
-    n_sat = min(20000, args.serving_requests)
-    el, lat = run(draw(n_sat), None)
-    sat = n_sat / el
-    points = []
-    for frac in (0.5, 0.7, 0.9):
-        k = args.serving_requests if frac == 0.7 else max(1000, args.serving_requests // 5)
-        el, lat = run(draw(k), frac * sat)
-        points.append({"rate_fraction_of_saturation": frac, "offered_qps": frac * sat, "requests": k,
-                       "queries_per_s": k / el, "p50_ms": float(np.percentile(lat, 50) * 1e3),
-                       "p99_ms": float(np.percentile(lat, 99) * 1e3)})
+    try:
+        run(draw(2000), None)  # warm-up: workspaces, kernels
+        n_sat = min(20000, args.serving_requests)
+        el, lat = run(draw(n_sat), None)
+        sat = n_sat / el
+        points = []
+        for frac in (0.5, 0.7, 0.9):
+            k = args.serving_requests if frac == 0.7 else max(1000, args.serving_requests // 5)
+            el, lat = run(draw(k), frac * sat)
+            points.append({"rate_fraction_of_saturation": frac, "offered_qps": frac * sat, "requests": k,
+                           "queries_per_s": k / el, "p50_ms": float(np.percentile(lat, 50) * 1e3),
+                           "p99_ms": float(np.percentile(lat, 99) * 1e3)})
+    except Stuck as e:
+        # report instead of hanging; the server and its graphs are left alive
+        # (closing them under a stuck worker could block the process)
+        import threading
+        closer = threading.Thread(target=server.close, daemon=True)
+        closer.start()
+        closer.join(30.0)
+        _KEEP_ALIVE.append((server, graphs))
+        return {"workload": "kronecker_scales_" + "_".join(map(str, scales)) + "_poisson",
+                "error": f"serving measurement stopped: {e}"}
     server.close()
     # plain path: bfs_run one query at a time (levels to pinned host memory)
     plain_reqs = draw(2000)
