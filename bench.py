@@ -390,6 +390,25 @@ def batched_measurement(args, gb, torch, dev):
 _KEEP_ALIVE = []  # objects of a serving run that did not finish
 
 
+class ServingStuck(Exception):
+    pass
+
+
+def wait_tickets(poll, tickets, limit_s, sleep_s=0.0002):
+    """Wait until ``poll(t)`` is true for every ticket, for at most
+    ``limit_s`` seconds; raises ServingStuck past it (a query that never
+    finished would otherwise keep the bench line from being printed)."""
+    deadline = time.perf_counter() + limit_s
+    i = 0
+    while i < len(tickets):
+        if poll(tickets[i]):
+            i += 1
+            continue
+        if time.perf_counter() > deadline:
+            raise ServingStuck(f"{len(tickets) - i} of {len(tickets)} queries unfinished after {limit_s:.0f} s")
+        time.sleep(sleep_s)
+
+
 def serving_measurement(args, gb, torch, dev):
     """Eight resident Kronecker graphs (scales 12..23; edgefactor 16 from
     scale 16, 8 below), requests choosing a graph with probability
@@ -422,21 +441,6 @@ def serving_measurement(args, gb, torch, dev):
     server = gb.Server()
     ids = [server.add_graph(g) for _, g in graphs]
 
-    class Stuck(Exception):
-        pass
-
-    def wait_all(tickets, limit_s):
-        """Bounded wait for every ticket (a query that never finished would
-        otherwise stop the whole bench line from being printed)."""
-        deadline = time.perf_counter() + limit_s
-        i = 0
-        while i < len(tickets):
-            if server.poll(tickets[i]):
-                i += 1
-                continue
-            if time.perf_counter() > deadline:
-                raise Stuck(f"{len(tickets) - i} of {len(tickets)} queries unfinished after {limit_s:.0f} s")
-            time.sleep(0.0002)
 
     def run(reqs, rate):
         """Submit reqs at Poisson times (rate None = all at once); returns
@@ -462,7 +466,7 @@ def serving_measurement(args, gb, torch, dev):
             t = server.submit(ids[gi], r, b)
             tickets.append(t)
             inflight.append((t, gi, b))
-        wait_all(tickets, 120.0 + len(reqs) / 500.0)
+        wait_tickets(server.poll, tickets, 120.0 + len(reqs) / 500.0)
         elapsed = time.perf_counter() - t0
         for t, g_, b in inflight:
             pools[g_].append(b)
@@ -485,7 +489,7 @@ def serving_measurement(args, gb, torch, dev):
             points.append({"rate_fraction_of_saturation": frac, "offered_qps": frac * sat, "requests": k,
                            "queries_per_s": k / el, "p50_ms": float(np.percentile(lat, 50) * 1e3),
                            "p99_ms": float(np.percentile(lat, 99) * 1e3)})
-    except Stuck as e:
+    except ServingStuck as e:
         # report instead of hanging; the server and its graphs are left alive
         # (closing them under a stuck worker could block the process)
         import threading
@@ -685,6 +689,12 @@ def run_ours(args):
             "wall_s_timed": wall,
         }
         print(json.dumps(line), flush=True)
+    if _KEEP_ALIVE:
+        # a serving run did not finish: leave without the destructors that
+        # would wait on its server
+        sys.stdout.flush()
+        sys.stderr.flush()
+        os._exit(0)
     g.close()
     if world > 1:
         dist.destroy_process_group()
