@@ -489,7 +489,7 @@ def serving_measurement(args, gb, torch, dev):
             points.append({"rate_fraction_of_saturation": frac, "offered_qps": frac * sat, "requests": k,
                            "queries_per_s": k / el, "p50_ms": float(np.percentile(lat, 50) * 1e3),
                            "p99_ms": float(np.percentile(lat, 99) * 1e3)})
-    except ServingStuck as e:
+    except (ServingStuck, gb.BfsError) as e:
         # report instead of hanging; the server and its graphs are left alive
         # (closing them under a stuck worker could block the process)
         import threading

@@ -269,6 +269,11 @@ int bfs_run_batch(bfs_graph *g, const int32_t *roots, int32_t k, uint8_t *level_
  * While a batch is in its heavy (pull) phase, new queries on that graph wait
  * a few iterations and then join together, so that young lanes do not keep
  * the batch in its slower push form.
+ * A query waits at most 60 s for room for its graph's workspace; past that
+ * it fails with BFS_ERR_BUSY.  If the device itself cannot hold the
+ * workspace (no other graph holds one that it could give back), the graph's
+ * waiting queries fail with BFS_ERR_OOM.  Either way the server and its
+ * other graphs keep running.
  */
 bfs_server *bfs_server_create(int64_t hbm_budget_bytes);
 int bfs_server_destroy(bfs_server *s);

@@ -24,6 +24,10 @@ int set_error(int status, const std::string &msg)
 int cuda_error(cudaError_t e, const char *what)
 {
     std::string m = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    // consume the runtime's record of a non-sticky error (a failed
+    // allocation), so that the next launch check of this thread does not
+    // report it again
+    cudaGetLastError();
     return set_error(e == cudaErrorMemoryAllocation ? BFS_ERR_OOM : BFS_ERR_CUDA, m);
 }
 

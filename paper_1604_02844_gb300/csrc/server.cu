@@ -15,7 +15,9 @@
 //      are reset and become free for the next queries.
 // A workspace is created only while the device memory it needs fits the
 // server's budget; a graph with no running or waiting query gives its
-// workspace back when another graph needs the room.
+// workspace back when another graph needs the room.  Queries wait at most
+// kRoomWaitNs for room; past that, or when the device itself cannot hold the
+// workspace, the graph's waiting queries fail (the server keeps running).
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
@@ -60,6 +62,7 @@ struct GraphState {
     uint8_t *d_stage = nullptr;       // [64][n] extraction rows
     MsCtrl last{};                    // counters after the previous round (worker thread only)
     bool have_last = false;
+    int64_t room_wait_since = 0;      // start of the current wait for room, 0 = none (under Server::mu)
     std::thread worker;
     std::condition_variable cv;
 };
@@ -70,6 +73,8 @@ int64_t workspace_bytes(const Graph *g)
     const int64_t n = g->n, fcap = n + 2 * (g->m / 256) + 2;
     return n * (8 * 4 + 64 + 4) + fcap * 4 * 6 + 64 * n + (1 << 20);
 }
+
+constexpr int64_t kRoomWaitNs = 60'000'000'000;  // longest wait of a query for workspace room
 
 }  // namespace
 
@@ -89,41 +94,90 @@ struct Server {
     void run(GraphState &gs);
     int round(GraphState &gs);
     int finish(GraphState &gs, unsigned long long mask);
-    bool ensure_ws(GraphState &gs);  // with mu held
+    int ensure_ws(GraphState &gs);                 // with mu held
+    void evict_idle(GraphState &gs, int64_t need);  // with mu held
+    int alloc_ws(GraphState &gs);
+    void fail_waiting(GraphState &gs, int rc);     // with mu held
     void fail_all(int rc);
 };
 
-// With mu held.  Makes room by dropping the workspaces of graphs that have
+// With mu held.  Drops the workspaces of graphs other than gs that have
 // nothing running or waiting (their workers are idle and their streams are
-// drained).
-bool Server::ensure_ws(GraphState &gs)
+// drained) until `need` more bytes fit the budget; need < 0 drops them all.
+void Server::evict_idle(GraphState &gs, int64_t need)
 {
-    if (gs.has_ws) return true;
+    for (auto &o : graphs) {
+        if (need >= 0 && used + need <= budget) break;
+        if (o.get() != &gs && o->has_ws && o->running == 0 && o->waiting.empty()) {
+            ms_free(o->g);
+            cudaFree(o->d_stage);
+            o->d_stage = nullptr;
+            o->has_ws = false;
+            used -= o->ws_bytes;
+        }
+    }
+}
+
+// The batched-search workspace and the extraction rows of one graph.
+int Server::alloc_ws(GraphState &gs)
+{
+    MsWs *w = nullptr;
+    int rc = ms_alloc(gs.g, &w);
+    if (rc != BFS_OK) {
+        ms_free(gs.g);  // a workspace left without its reset is not reused
+        return rc;
+    }
+    const cudaError_t e = cudaMalloc(&gs.d_stage, (size_t)64 * gs.g->n);
+    if (e != cudaSuccess) {
+        rc = cuda_error(e, "server: extraction rows");
+        gs.d_stage = nullptr;
+        ms_free(gs.g);
+        return rc;
+    }
+    return BFS_OK;
+}
+
+// With mu held.  BFS_OK once gs has its workspace; BFS_NOT_READY while it
+// has to wait for room (over the budget, or the device short of memory while
+// other graphs hold workspaces that they give back when idle); another
+// status when the device cannot hold it.
+int Server::ensure_ws(GraphState &gs)
+{
+    if (gs.has_ws) return BFS_OK;
     const int64_t need = workspace_bytes(gs.g);
     if (used + need > budget) {
-        for (auto &o : graphs) {
-            if (used + need <= budget) break;
-            if (o.get() != &gs && o->has_ws && o->running == 0 && o->waiting.empty()) {
-                ms_free(o->g);
-                cudaFree(o->d_stage);
-                o->d_stage = nullptr;
-                o->has_ws = false;
-                used -= o->ws_bytes;
-            }
-        }
-        if (used + need > budget) return false;
+        evict_idle(gs, need);
+        if (used + need > budget) return BFS_NOT_READY;
     }
-    MsWs *w = nullptr;
-    if (ms_alloc(gs.g, &w) != BFS_OK) return false;
-    if (cudaMalloc(&gs.d_stage, (size_t)64 * gs.g->n) != cudaSuccess) {
-        ms_free(gs.g);
-        return false;
+    int rc = alloc_ws(gs);
+    if (rc == BFS_ERR_OOM) {  // less free device memory than the budget assumed
+        evict_idle(gs, -1);
+        rc = alloc_ws(gs);
     }
+    if (rc == BFS_ERR_OOM)
+        for (auto &o : graphs)
+            if (o.get() != &gs && o->has_ws) return BFS_NOT_READY;
+    if (rc != BFS_OK) return rc;
     gs.has_ws = true;
     gs.ws_bytes = need;
     used += need;
     gs.running = 0;
-    return true;
+    return BFS_OK;
+}
+
+// With mu held.  The graph's waiting queries fail with rc; the server and
+// the other graphs carry on.
+void Server::fail_waiting(GraphState &gs, int rc)
+{
+    const int64_t t = now_ns();
+    for (uint64_t tk : gs.waiting) {
+        Request &r = *reqs[tk - 1];
+        r.t_done = t;
+        r.status.store(rc);
+        --outstanding;
+    }
+    gs.waiting.clear();
+    done_cv.notify_all();
 }
 
 // Copy finished lanes to their callers and free the lanes.
@@ -183,7 +237,19 @@ int Server::round(GraphState &gs)
     int active = 1;
     {
         std::lock_guard<std::mutex> lk(mu);
-        if (!ensure_ws(gs)) return BFS_NOT_READY;  // no room yet: the queries wait
+        int ws = ensure_ws(gs);
+        if (ws != BFS_OK) {
+            if (ws == BFS_NOT_READY) {  // no room yet: the queries wait, for a while
+                const int64_t t = now_ns();
+                if (!gs.room_wait_since) gs.room_wait_since = t;
+                if (t - gs.room_wait_since <= kRoomWaitNs) return BFS_NOT_READY;
+                ws = set_error(BFS_ERR_BUSY, "server: no room for the graph's workspace");
+            }
+            fail_waiting(gs, ws);
+            gs.room_wait_since = 0;
+            return BFS_OK;
+        }
+        gs.room_wait_since = 0;
         const bool hold = gs.running && gs.have_last && pull_phase(gs.g, gs.last, gs.running);
         while (!hold && !gs.waiting.empty() && (gs.running | add) != ~0ull) {
             const int lane = __builtin_ctzll(~(gs.running | add));
