@@ -56,6 +56,7 @@ struct GraphState {
     Graph *g = nullptr;
     std::deque<uint64_t> waiting;     // tickets (under Server::mu)
     uint64_t lane_ticket[64] = {};
+    unsigned lane_iter0[64] = {};     // search iteration at which each lane joined (worker thread only)
     unsigned long long running = 0;   // occupied lanes (under Server::mu)
     bool has_ws = false;              // (under Server::mu)
     int64_t ws_bytes = 0;
@@ -162,6 +163,7 @@ int Server::ensure_ws(GraphState &gs)
     gs.ws_bytes = need;
     used += need;
     gs.running = 0;
+    gs.have_last = false;  // a new workspace starts at iteration 0
     return BFS_OK;
 }
 
@@ -256,6 +258,7 @@ int Server::round(GraphState &gs)
             const uint64_t t = gs.waiting.front();
             gs.waiting.pop_front();
             gs.lane_ticket[lane] = t;
+            gs.lane_iter0[lane] = gs.have_last ? gs.last.iter : 0u;
             src[lane] = reqs[t - 1]->root;
             add |= 1ull << lane;
         }
@@ -283,6 +286,14 @@ int Server::round(GraphState &gs)
     if (st.status & (ST_TIMEOUT | ST_OVERFLOW | ST_DEPTH))
         return set_error(st.status & ST_DEPTH ? BFS_ERR_DEPTH : (st.status & ST_TIMEOUT ? BFS_ERR_TIMEOUT : BFS_ERR_CUDA),
                          "server: device-side error in a batched search");
+    // Backstop: a lane still searching 300 iterations after it joined would
+    // have levels past 254, which the kernel itself reports (ST_DEPTH); should
+    // that ever fail, the query ends with an error instead of running forever.
+    for (unsigned long long a = running & st.alive[st.iter & 1]; a; a &= a - 1) {
+        const int lane = __builtin_ctzll(a);
+        if (st.iter - gs.lane_iter0[lane] > 300u)
+            return set_error(BFS_ERR_DEPTH, "server: a query kept searching past 254 levels");
+    }
     return finish(gs, running & ~st.alive[st.iter & 1]);
 }
 
