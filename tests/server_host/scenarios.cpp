@@ -1,0 +1,342 @@
+// scenarios.cpp -- drives the serving loop of server.cu, built for the host
+// against fake_backend.cpp, through its C ABI.  One scenario per run:
+//   server_host <scenario>      prints "ok" and exits 0, or names the
+//                               failed check and exits 1.
+#include <stdio.h>
+#include <stdlib.h>
+#include <unistd.h>
+
+#include <algorithm>
+#include <chrono>
+#include <random>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "fake_backend.h"
+
+using gbbfs::Graph;
+
+#define CHECK(cond)                                                             \
+    do {                                                                        \
+        if (!(cond)) {                                                          \
+            fprintf(stderr, "check failed at line %d: %s\n", __LINE__, #cond); \
+            exit(1);                                                            \
+        }                                                                       \
+    } while (0)
+
+namespace {
+
+Graph *make_graph(int64_t n, int64_t m)
+{
+    Graph *g = new Graph();
+    g->n = n;
+    g->m = m;
+    g->num_sms = 4;
+    g->symmetric = true;
+    g->n_nonzero = n;
+    return g;
+}
+
+// The server's admission size of one graph's workspace (restated here so
+// that a budget can be chosen to hold exactly one of them).
+int64_t ws_bytes(const Graph *g)
+{
+    const int64_t n = g->n, fcap = n + 2 * (g->m / 256) + 2;
+    return n * (8 * 4 + 64 + 4) + fcap * 4 * 6 + 64 * n + (1 << 20);
+}
+
+constexpr int64_t kOneWorkspace = -1;
+
+struct Query {
+    int gi = 0;
+    int32_t root = 0;
+    std::vector<uint8_t> buf;
+    uint64_t ticket = 0;
+};
+
+struct Bench {
+    std::vector<Graph *> graphs;
+    std::vector<int> ids;
+    bfs_server *s = nullptr;
+
+    // budget: bytes, 0 = the server's default, kOneWorkspace = room for the
+    // largest graph's workspace only
+    Bench(std::vector<int64_t> ns, int64_t budget)
+    {
+        for (int64_t n : ns) graphs.push_back(make_graph(n, 16 * n));
+        if (budget == kOneWorkspace) {
+            budget = 0;
+            for (Graph *g : graphs) budget = std::max(budget, ws_bytes(g) + 1000);
+        }
+        s = bfs_server_create(budget);
+        CHECK(s);
+        for (Graph *g : graphs) {
+            ids.push_back(bfs_server_add_graph(s, reinterpret_cast<bfs_graph *>(g)));
+            CHECK(ids.back() == (int)ids.size() - 1);
+        }
+    }
+    ~Bench()
+    {
+        if (s) bfs_server_destroy(s);
+        for (Graph *g : graphs) delete g;
+    }
+    int submit(Query &q)
+    {
+        q.buf.assign((size_t)graphs[q.gi]->n, 0xAB);
+        return bfs_submit(s, ids[q.gi], q.root, q.buf.data(), &q.ticket);
+    }
+    bool result_ok(const Query &q) const
+    {
+        const int64_t n = graphs[q.gi]->n;
+        for (int64_t v = 0; v < n; ++v)
+            if (q.buf[(size_t)v] != fake::level_of(n, q.root, v)) return false;
+        return true;
+    }
+    // poll until the ticket is no longer running, at most limit_s seconds
+    int wait(const Query &q, double limit_s = 20.0) const
+    {
+        const auto t0 = std::chrono::steady_clock::now();
+        while (true) {
+            const int st = bfs_poll(s, q.ticket);
+            if (st != BFS_NOT_READY) return st;
+            if (std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() > limit_s) return 99;
+            std::this_thread::sleep_for(std::chrono::microseconds(100));
+        }
+    }
+};
+
+std::vector<Query> random_queries(const Bench &b, int k, unsigned seed)
+{
+    std::mt19937 rng(seed);
+    std::vector<Query> qs((size_t)k);
+    for (auto &q : qs) {
+        q.gi = (int)(rng() % b.graphs.size());
+        q.root = (int32_t)(rng() % (uint32_t)b.graphs[q.gi]->n);
+    }
+    return qs;
+}
+
+// Submit from a producer thread with occasional pauses, then drain.
+int submit_mixed(Bench &b, std::vector<Query> &qs, unsigned seed)
+{
+    std::thread producer([&] {
+        std::mt19937 rng(seed);
+        for (auto &q : qs) {
+            CHECK(b.submit(q) == BFS_OK);
+            if (rng() % 8 == 0) std::this_thread::sleep_for(std::chrono::microseconds(rng() % 300));
+        }
+    });
+    producer.join();
+    return bfs_server_drain(b.s);
+}
+
+// ---- scenarios ---------------------------------------------------------------
+
+// Queries on three graphs arriving while others run: every result lands in
+// its own buffer, lanes are recycled (far more queries than 64 lanes), and
+// the ticket times are ordered.
+void mixed()
+{
+    Bench b({1000, 3000, 700}, 0);
+    auto qs = random_queries(b, 3000, 1);
+    CHECK(submit_mixed(b, qs, 2) == BFS_OK);
+    for (auto &q : qs) {
+        CHECK(bfs_poll(b.s, q.ticket) == BFS_OK);
+        CHECK(b.result_ok(q));
+        int64_t t0 = 0, t1 = 0;
+        CHECK(bfs_ticket_times(b.s, q.ticket, &t0, &t1) == BFS_OK);
+        CHECK(t1 >= t0 && t0 > 0);
+    }
+    CHECK(fake::min_share.load() >= 1);
+}
+
+// An HBM budget that holds one workspace at a time: graphs take turns, every
+// query completes, and all device memory comes back at shutdown.
+void tight_budget()
+{
+    const int64_t free0 = fake::device_free.load();
+    {
+        Bench b({1000, 3000, 2000}, kOneWorkspace);
+        auto qs = random_queries(b, 600, 3);
+        CHECK(submit_mixed(b, qs, 4) == BFS_OK);
+        for (auto &q : qs) {
+            CHECK(bfs_poll(b.s, q.ticket) == BFS_OK);
+            CHECK(b.result_ok(q));
+        }
+    }
+    CHECK(fake::device_free.load() == free0);
+}
+
+// The device has room for one workspace only, although the budget allows
+// more: a graph whose allocation fails waits while another holds one, and
+// gets it once that graph is idle.
+void device_oom_wait()
+{
+    fake::device_free = 600'000;  // 164 B per vertex: n = 2000 or 3000 fits, not both
+    Bench b({2000, 3000}, int64_t(1) << 40);
+    auto qs = random_queries(b, 400, 5);
+    CHECK(submit_mixed(b, qs, 6) == BFS_OK);
+    for (auto &q : qs) {
+        CHECK(bfs_poll(b.s, q.ticket) == BFS_OK);
+        CHECK(b.result_ok(q));
+    }
+}
+
+// A graph whose workspace the device can never hold: its queries fail with
+// BFS_ERR_OOM, the other graph's queries complete, and the server keeps
+// serving.
+void device_oom_fail()
+{
+    fake::device_free = 400'000;  // n = 1000 fits (164 KB), n = 3000 (492 KB) never does
+    Bench b({1000, 3000}, int64_t(1) << 40);
+    auto qs = random_queries(b, 300, 7);
+    CHECK(submit_mixed(b, qs, 8) == BFS_OK);
+    int failed = 0;
+    for (auto &q : qs) {
+        const int st = bfs_poll(b.s, q.ticket);
+        if (q.gi == 1) {
+            CHECK(st == BFS_ERR_OOM);
+            ++failed;
+        } else {
+            CHECK(st == BFS_OK);
+            CHECK(b.result_ok(q));
+        }
+    }
+    CHECK(failed > 0);
+    Query again;
+    again.gi = 0;
+    again.root = 17;
+    CHECK(b.submit(again) == BFS_OK);
+    CHECK(b.wait(again) == BFS_OK);
+    CHECK(b.result_ok(again));
+}
+
+// A query that waits longer than the room limit (0.2 s in this build) for
+// its graph's workspace fails with BFS_ERR_BUSY; later queries are served.
+void room_limit()
+{
+    Bench b({3000, 2000}, kOneWorkspace);
+    fake::deep_root = 11;
+    fake::deep_depth = 240;  // 60 rounds of 4 iterations
+    fake::slow_graph_n = 3000;
+    fake::slow_step_us = 8000;  // about 0.5 s in all
+    Query deep;
+    deep.gi = 0;
+    deep.root = 11;
+    CHECK(b.submit(deep) == BFS_OK);
+    std::this_thread::sleep_for(std::chrono::milliseconds(30));  // its workspace is taken
+    Query starved;
+    starved.gi = 1;
+    starved.root = 5;
+    CHECK(b.submit(starved) == BFS_OK);
+    CHECK(b.wait(starved) == BFS_ERR_BUSY);
+    int64_t t0 = 0, t1 = 0;
+    CHECK(bfs_ticket_times(b.s, starved.ticket, &t0, &t1) == BFS_OK);
+    CHECK(t1 - t0 >= 190'000'000);
+    CHECK(b.wait(deep) == BFS_OK);
+    CHECK(b.result_ok(deep));
+    Query later;
+    later.gi = 1;
+    later.root = 6;
+    CHECK(b.submit(later) == BFS_OK);
+    CHECK(b.wait(later) == BFS_OK);
+    CHECK(b.result_ok(later));
+}
+
+// A device-side timeout fails every outstanding query with BFS_ERR_TIMEOUT,
+// drain reports it, new queries are refused, and shutdown does not hang.
+void timeout()
+{
+    fake::timeout_graph_n = 1000;
+    Bench b({1000, 700}, 0);
+    auto qs = random_queries(b, 200, 9);
+    // the failure may come while queries are still being submitted: those
+    // are refused with the server's error
+    std::vector<Query *> taken;
+    for (auto &q : qs) {
+        const int rc = b.submit(q);
+        CHECK(rc == BFS_OK || rc == BFS_ERR_TIMEOUT);
+        if (rc == BFS_OK) taken.push_back(&q);
+    }
+    CHECK(bfs_server_drain(b.s) == BFS_ERR_TIMEOUT);
+    for (Query *qp : taken) {
+        const Query &q = *qp;
+        const int st = bfs_poll(b.s, q.ticket);
+        CHECK(st == BFS_OK || st == BFS_ERR_TIMEOUT);
+        if (q.gi == 0) CHECK(st == BFS_ERR_TIMEOUT);
+        if (st == BFS_OK) CHECK(b.result_ok(q));
+    }
+    Query q;
+    q.gi = 1;
+    CHECK(b.submit(q) == BFS_ERR_TIMEOUT);
+}
+
+// A lane whose search never ends and never reports a depth overflow (a
+// broken kernel): the host backstop ends it with BFS_ERR_DEPTH.
+void depth_backstop()
+{
+    fake::never_finish_root = 5;
+    Bench b({1000}, 0);
+    Query q;
+    q.root = 5;
+    CHECK(b.submit(q) == BFS_OK);
+    CHECK(bfs_server_drain(b.s) == BFS_ERR_DEPTH);
+    CHECK(bfs_poll(b.s, q.ticket) == BFS_ERR_DEPTH);
+}
+
+// A query deeper than 254 levels: the device's own ST_DEPTH report ends it.
+void kernel_depth()
+{
+    fake::deep_root = 7;
+    fake::deep_depth = 300;
+    Bench b({1000}, 0);
+    Query q;
+    q.root = 7;
+    CHECK(b.submit(q) == BFS_OK);
+    CHECK(bfs_server_drain(b.s) == BFS_ERR_DEPTH);
+    CHECK(bfs_poll(b.s, q.ticket) == BFS_ERR_DEPTH);
+}
+
+// While a batch is in its heavy (pull) phase, waiting queries are not put
+// into it; they join once it ends, and every query completes.
+void pull_hold()
+{
+    fake::pull_mode = 1;
+    Bench b({1000, 2000}, 0);
+    auto qs = random_queries(b, 2000, 11);
+    CHECK(submit_mixed(b, qs, 12) == BFS_OK);
+    for (auto &q : qs) {
+        CHECK(bfs_poll(b.s, q.ticket) == BFS_OK);
+        CHECK(b.result_ok(q));
+    }
+    CHECK(fake::pull_seen.load() > 0);
+    CHECK(fake::injections_during_pull.load() == 0);
+}
+
+}  // namespace
+
+int main(int argc, char **argv)
+{
+    if (argc != 2) {
+        fprintf(stderr, "usage: server_host <scenario>\n");
+        return 2;
+    }
+    alarm(60);  // a hung scenario ends the process
+    const std::string s = argv[1];
+    if (s == "mixed") mixed();
+    else if (s == "tight_budget") tight_budget();
+    else if (s == "device_oom_wait") device_oom_wait();
+    else if (s == "device_oom_fail") device_oom_fail();
+    else if (s == "room_limit") room_limit();
+    else if (s == "timeout") timeout();
+    else if (s == "depth_backstop") depth_backstop();
+    else if (s == "kernel_depth") kernel_depth();
+    else if (s == "pull_hold") pull_hold();
+    else {
+        fprintf(stderr, "unknown scenario %s\n", s.c_str());
+        return 2;
+    }
+    printf("ok\n");
+    return 0;
+}

@@ -1,0 +1,99 @@
+"""Host-only tests of the serving loop's scheduling (server.cu), no GPU.
+
+server.cu holds no device code, so it is compiled here with g++ against
+tests/server_host/fake_backend.cpp. That file stands in for the CUDA runtime
+calls and for the batched-search entry points. In the stand-in, a lane's
+search is a countdown, and its level row depends only on the graph, the root
+and the vertex. The scenarios in tests/server_host/scenarios.cpp drive the
+loop through its C ABI and check that:
+- results reach their own buffers while lanes are recycled;
+- graphs take turns under a tight HBM budget, and the device memory comes
+  back at shutdown;
+- when the device is out of memory, a graph waits while another holds a
+  workspace, and fails when none does;
+- the room limit holds;
+- device timeouts and depth overflows fail the queries instead of hanging;
+- the host backstop ends a lane that never finishes;
+- the pull-phase hold is kept.
+
+The loop's wait for room is shortened to 0.2 s in this build. A second test
+plants mistakes in a copy of server.cu and checks that each one is caught.
+"""
+import os
+import shutil
+import subprocess
+
+import pytest
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+CSRC = os.path.join(ROOT, "paper_1604_02844_gb300", "csrc")
+HOST = os.path.join(HERE, "server_host")
+SCENARIOS = ["mixed", "tight_budget", "device_oom_wait", "device_oom_fail", "room_limit", "timeout",
+             "depth_backstop", "kernel_depth", "pull_hold"]
+
+
+def _cuda_include():
+    for base in (os.environ.get("CUDA_HOME"), os.environ.get("CUDA_PATH"), "/usr/local/cuda"):
+        if base and os.path.exists(os.path.join(base, "include", "cuda_runtime_api.h")):
+            return os.path.join(base, "include")
+    return None
+
+
+def _build(server_src, out):
+    inc = _cuda_include()
+    cmd = ["g++", "-std=c++17", "-O1", "-pthread", "-DGBBFS_ROOM_WAIT_NS=200000000",
+           f"-I{CSRC}", f"-I{HOST}", f"-I{inc}",
+           "-x", "c++", server_src, "-x", "none",
+           os.path.join(HOST, "fake_backend.cpp"), os.path.join(HOST, "scenarios.cpp"), "-o", out]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr[-4000:]
+    return out
+
+
+def _run(exe, scenario, timeout=120):
+    return subprocess.run([exe, scenario], capture_output=True, text=True, timeout=timeout)
+
+
+@pytest.fixture(scope="module")
+def server_host(tmp_path_factory):
+    if shutil.which("g++") is None or _cuda_include() is None:
+        pytest.skip("needs g++ and the CUDA runtime headers")
+    d = tmp_path_factory.mktemp("server_host")
+    return _build(os.path.join(CSRC, "server.cu"), str(d / "server_host"))
+
+
+@pytest.mark.parametrize("scenario", SCENARIOS)
+def test_scenario(server_host, scenario):
+    r = _run(server_host, scenario)
+    assert r.returncode == 0 and r.stdout.strip() == "ok", r.stdout + r.stderr
+
+
+# (name, text in server.cu, replacement, scenario that must then fail)
+MUTANTS = [
+    ("no pull-phase hold",
+     "const bool hold = gs.running && gs.have_last && pull_phase(gs.g, gs.last, gs.running);",
+     "const bool hold = false;", "pull_hold"),
+    ("results to a neighbouring lane's buffer",
+     "out = reqs[gs.lane_ticket[i] - 1]->out;",
+     "out = reqs[gs.lane_ticket[i ^ 1] ? gs.lane_ticket[i ^ 1] - 1 : gs.lane_ticket[i] - 1]->out;", "mixed"),
+    ("no room limit",
+     "if (t - gs.room_wait_since <= kRoomWaitNs) return BFS_NOT_READY;",
+     "return BFS_NOT_READY;", "room_limit"),
+    ("a device allocation failure only ever waits",
+     "    if (rc != BFS_OK) return rc;\n    gs.has_ws = true;",
+     "    if (rc != BFS_OK) return BFS_NOT_READY;\n    gs.has_ws = true;", "device_oom_fail"),
+    ("idle workspaces never given back",
+     "        evict_idle(gs, need);\n", "", "tight_budget"),
+]
+
+
+@pytest.mark.parametrize("name,old,new,scenario", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_planted_mistakes_are_caught(server_host, tmp_path, name, old, new, scenario):
+    src = open(os.path.join(CSRC, "server.cu")).read()
+    assert src.count(old) == 1, f"mutant {name!r} no longer applies"
+    mutated = tmp_path / "server.cu"
+    mutated.write_text(src.replace(old, new))
+    exe = _build(str(mutated), str(tmp_path / "server_host"))
+    r = _run(exe, scenario, timeout=90)
+    assert r.returncode != 0, f"{name}: scenario {scenario} still passes"
