@@ -22,3 +22,59 @@ def test_wait_tickets_gives_up_on_a_lost_query():
 
 def test_wait_tickets_empty():
     bench.wait_tickets(lambda t: False, [], limit_s=0.0)
+
+
+def test_algorithmic_bytes_hand_count():
+    # path 0-1-2 (4 directed entries), all reached: adjacency 16 B, row_offsets
+    # pairs 24 B, frontier ids 24 B, level+parent 24 B, bitmap 3/4 B
+    assert bench.algorithmic_bytes(4, 3, 3) == 16 + 24 + 24 + 24 + 0.75
+
+
+def test_harmonic_mean():
+    assert abs(bench.harmonic_mean([1.0, 2.0, 4.0]) - 3.0 / 1.75) < 1e-12
+    assert bench.harmonic_mean([5.0] * 64) == pytest.approx(5.0)
+
+
+def test_clock_summary_parses_samples(tmp_path):
+    s = bench.ClockSampler()
+    s.path = str(tmp_path / "clocks.csv")
+    s.proc = object()  # as if nvidia-smi had run
+    rows = [
+        "0, GPU-a, 345, 2070, 150.0, 0x0, Not Active, Not Active, Not Active, Not Active",  # idle: dropped
+        "0, GPU-a, 2070, 2070, 900.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "0, GPU-a, 2055, 2070, 1390.0, 0x4, Not Active, Not Active, Not Active, Active",
+        "0, GPU-a, 2040, 2070, 1400.0, 0x4, Not Active, Not Active, Not Active, Active",
+        "garbage line",
+    ]
+    open(s.path, "w").write("\n".join(rows) + "\n")
+    out = s.summary()
+    assert out["sm_mhz"] == 2055 and out["sm_max_mhz"] == 2070
+    assert out["reasons"] == ["sw_power_cap"] and out["samples"] == 4
+
+
+def test_clock_summary_flags_thermal_slowdown(tmp_path):
+    s = bench.ClockSampler()
+    s.path = str(tmp_path / "clocks.csv")
+    s.proc = object()
+    open(s.path, "w").write("0, GPU-a, 1500, 2070, 1000.0, 0x40, Not Active, Active, Not Active, Not Active\n")
+    assert s.summary()["reasons"] == ["hw_thermal_slowdown"]
+
+
+def test_profiled_traffic_only_for_the_profiled_kernel(tmp_path, monkeypatch):
+    import argparse
+    args = argparse.Namespace(graph="kronecker", scale=22)
+    t = bench.profiled_traffic(args, {"mode": 0, "block": 512})
+    assert t is None or t > 0  # present while the kernel sources match the summary
+    assert bench.profiled_traffic(args, {"mode": 3, "block": 512}) is None
+    assert bench.profiled_traffic(args, {"mode": 0, "block": 256}) is None
+    # a changed kernel source invalidates the stored figure
+    root = tmp_path / "repo"
+    (root / "profiles").mkdir(parents=True)
+    for f in bench.KERNEL_SOURCES:
+        p = root / f
+        p.parent.mkdir(parents=True, exist_ok=True)
+        p.write_text("changed\n")
+    (root / "profiles" / "td_warp_kernel_kronecker_s22.txt").write_text(
+        "traffic_bytes_per_launch: 123\nsource_sha256_16: 0000000000000000\n")
+    monkeypatch.setattr(bench, "ROOT", str(root))
+    assert bench.profiled_traffic(args, {"mode": 0, "block": 512}) is None
