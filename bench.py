@@ -490,15 +490,28 @@ def serving_measurement(args, gb, torch, dev):
                            "queries_per_s": k / el, "p50_ms": float(np.percentile(lat, 50) * 1e3),
                            "p99_ms": float(np.percentile(lat, 99) * 1e3)})
     except (ServingStuck, gb.BfsError) as e:
-        # report instead of hanging; the server and its graphs are left alive
-        # (closing them under a stuck worker could block the process)
+        # report instead of hanging, with each graph's queue and worker state;
+        # the server and its graphs are left alive (closing them under a stuck
+        # worker could block the process)
         import threading
+        stats = []
+
+        def snapshot():
+            for i, s_ in enumerate(scales):
+                try:
+                    stats.append(dict(scale=s_, **server.graph_stats(ids[i])))
+                except Exception as e2:  # noqa: BLE001
+                    stats.append({"scale": s_, "error": str(e2)})
+
+        th = threading.Thread(target=snapshot, daemon=True)
+        th.start()
+        th.join(10.0)
         closer = threading.Thread(target=server.close, daemon=True)
         closer.start()
         closer.join(30.0)
         _KEEP_ALIVE.append((server, graphs))
         return {"workload": "kronecker_scales_" + "_".join(map(str, scales)) + "_poisson",
-                "error": f"serving measurement stopped: {e}"}
+                "error": f"serving measurement stopped: {e}", "graphs": stats}
     server.close()
     # plain path: bfs_run one query at a time (levels to pinned host memory)
     plain_reqs = draw(2000)

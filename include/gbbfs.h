@@ -298,6 +298,20 @@ int bfs_poll(bfs_server *s, uint64_t ticket);
 /* Block until every submitted query has completed (or failed). */
 int bfs_server_drain(bfs_server *s);
 
+/* Monitoring counters of one graph of the server, written to out[0..6]:
+ *   out[0] queries waiting for a lane     out[1] lanes running
+ *   out[2] rounds its worker has run      out[3] the batch's iteration after
+ *                                                the last round (-1 = none)
+ *   out[4] 1 while it holds its workspace
+ *   out[5] ns since its worker last finished a round (-1 = never)
+ *   out[6] what its worker is doing: 0 waiting for work, 1 admitting
+ *          queries, 2 putting sources on the device, 3 launching iterations,
+ *          4 reading the control block (waits for those iterations),
+ *          5 delivering results, 6 waiting for workspace room, 7 stopped
+ * A snapshot taken without stopping the worker.  Returns BFS_OK or
+ * BFS_ERR_INVALID_ARG (NULL pointer, unknown graph id). */
+int bfs_server_graph_stats(bfs_server *s, int graph_id, int64_t *out);
+
 /* Submission and completion times of a query, ns on a monotonic clock. */
 int bfs_ticket_times(bfs_server *s, uint64_t ticket, int64_t *t_submit_ns,
                      int64_t *t_done_ns);

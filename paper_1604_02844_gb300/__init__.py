@@ -87,6 +87,7 @@ SIGNATURES = {
     "bfs_poll": (_INT, [_P, _U64]),
     "bfs_server_drain": (_INT, [_P]),
     "bfs_ticket_times": (_INT, [_P, _U64, ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
+    "bfs_server_graph_stats": (_INT, [_P, _INT, ctypes.POINTER(_I64)]),
 }
 
 
@@ -262,6 +263,18 @@ def bfs_server_drain(s) -> None:
     _check(load().bfs_server_drain(s))
 
 
+SERVER_PHASES = ("waiting for work", "admitting queries", "putting sources on the device",
+                 "launching iterations", "reading the control block", "delivering results",
+                 "waiting for workspace room", "stopped")
+
+
+def bfs_server_graph_stats(s, graph_id: int) -> dict:
+    out = (_I64 * 7)()
+    _check(load().bfs_server_graph_stats(s, int(graph_id), out))
+    return {"waiting": out[0], "running": out[1], "rounds": out[2], "iter": out[3], "has_workspace": bool(out[4]),
+            "ns_since_round": out[5], "phase": SERVER_PHASES[out[6]] if 0 <= out[6] < len(SERVER_PHASES) else out[6]}
+
+
 def bfs_ticket_times(s, ticket: int):
     a, b = ctypes.c_int64(0), ctypes.c_int64(0)
     _check(load().bfs_ticket_times(s, int(ticket), ctypes.byref(a), ctypes.byref(b)))
@@ -370,6 +383,10 @@ class Server:
 
     def times(self, ticket: int):
         return bfs_ticket_times(self.handle, ticket)
+
+    def graph_stats(self, graph_id: int) -> dict:
+        """Monitoring snapshot of one graph's queue and worker."""
+        return bfs_server_graph_stats(self.handle, graph_id)
 
     def close(self):
         if self.handle:

@@ -52,6 +52,18 @@ struct Request {
     std::atomic<int> status{BFS_NOT_READY};
 };
 
+// What a graph's worker is doing (bfs_server_graph_stats).
+enum Phase : int {
+    PH_IDLE = 0,       // waiting for work
+    PH_ADMIT = 1,      // admitting queries into lanes
+    PH_INJECT = 2,     // putting the new lanes' sources on the device
+    PH_STEP = 3,       // launching iterations
+    PH_READ = 4,       // reading the control block (waits for the iterations)
+    PH_FINISH = 5,     // delivering finished lanes' results
+    PH_ROOM_WAIT = 6,  // waiting for workspace room
+    PH_STOPPED = 7,
+};
+
 struct GraphState {
     Graph *g = nullptr;
     std::deque<uint64_t> waiting;     // tickets (under Server::mu)
@@ -64,6 +76,9 @@ struct GraphState {
     MsCtrl last{};                    // counters after the previous round (worker thread only)
     bool have_last = false;
     int64_t room_wait_since = 0;      // start of the current wait for room, 0 = none (under Server::mu)
+    // monitoring (read by other threads without the lock)
+    std::atomic<int> phase{PH_IDLE};
+    std::atomic<int64_t> rounds{0}, last_iter{-1}, t_round_end{0};
     std::thread worker;
     std::condition_variable cv;
 };
@@ -242,6 +257,7 @@ int Server::round(GraphState &gs)
     unsigned long long add = 0, running;
     int32_t src[64] = {0};
     int active = 1;
+    gs.phase = PH_ADMIT;
     {
         std::lock_guard<std::mutex> lk(mu);
         int ws = ensure_ws(gs);
@@ -274,6 +290,7 @@ int Server::round(GraphState &gs)
             if (o->running) ++active;
     }
     if (add) {
+        gs.phase = PH_INJECT;
         const int rc = ms_inject(gs.g, src, add);
         if (rc != BFS_OK) return rc;
     }
@@ -282,12 +299,15 @@ int Server::round(GraphState &gs)
     // graph set to 512-thread CTAs gets half as many
     const int per_cta = gs.g->opt.batch_block == 512 ? 2 : 1;
     const int share = std::max(gs.g->num_sms, total_ctas / std::max(1, active)) / per_cta;
+    gs.phase = PH_STEP;
     int rc = ms_step_capped(gs.g, iters_per_step, share);
     if (rc != BFS_OK) return rc;
     MsCtrl &st = gs.last;
+    gs.phase = PH_READ;
     rc = ms_read_ctrl(gs.g, &st);
     if (rc != BFS_OK) return rc;
     gs.have_last = true;
+    gs.last_iter = (int64_t)st.iter;
     if (st.status & (ST_TIMEOUT | ST_OVERFLOW | ST_DEPTH))
         return set_error(st.status & ST_DEPTH ? BFS_ERR_DEPTH : (st.status & ST_TIMEOUT ? BFS_ERR_TIMEOUT : BFS_ERR_CUDA),
                          "server: device-side error in a batched search");
@@ -299,6 +319,7 @@ int Server::round(GraphState &gs)
         if (st.iter - gs.lane_iter0[lane] > 300u)
             return set_error(BFS_ERR_DEPTH, "server: a query kept searching past 254 levels");
     }
+    gs.phase = PH_FINISH;
     return finish(gs, running & ~st.alive[st.iter & 1]);
 }
 
@@ -324,13 +345,17 @@ void Server::run(GraphState &gs)
 {
     cudaSetDevice(device);
     while (true) {
+        gs.phase = PH_IDLE;
         {
             std::unique_lock<std::mutex> lk(mu);
             gs.cv.wait(lk, [&] { return stop || error != BFS_OK || !gs.waiting.empty() || gs.running; });
             if (stop || error != BFS_OK) break;
         }
         const int rc = round(gs);
+        ++gs.rounds;
+        gs.t_round_end = now_ns();
         if (rc == BFS_NOT_READY) {  // waiting for HBM budget
+            gs.phase = PH_ROOM_WAIT;
             std::this_thread::sleep_for(std::chrono::microseconds(200));
             continue;
         }
@@ -339,6 +364,7 @@ void Server::run(GraphState &gs)
             break;
         }
     }
+    gs.phase = PH_STOPPED;
 }
 
 }  // namespace gbbfs
@@ -460,6 +486,25 @@ int bfs_server_drain(bfs_server *sh)
     std::unique_lock<std::mutex> lk(s->mu);
     s->done_cv.wait(lk, [&] { return s->outstanding == 0 || s->error != BFS_OK; });
     return s->error;
+}
+
+int bfs_server_graph_stats(bfs_server *sh, int graph_id, int64_t *out)
+{
+    if (!sh || !out) return set_error(BFS_ERR_INVALID_ARG, "bfs_server_graph_stats: NULL argument");
+    Server *s = reinterpret_cast<Server *>(sh);
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (graph_id < 0 || graph_id >= (int)s->graphs.size())
+        return set_error(BFS_ERR_INVALID_ARG, "bfs_server_graph_stats: unknown graph id");
+    const GraphState &gs = *s->graphs[graph_id];
+    out[0] = (int64_t)gs.waiting.size();
+    out[1] = __builtin_popcountll(gs.running);
+    out[2] = gs.rounds.load();
+    out[3] = gs.last_iter.load();
+    out[4] = gs.has_ws ? 1 : 0;
+    const int64_t t = gs.t_round_end.load();
+    out[5] = t ? now_ns() - t : -1;
+    out[6] = gs.phase.load();
+    return BFS_OK;
 }
 
 int bfs_ticket_times(bfs_server *sh, uint64_t ticket, int64_t *t_submit_ns, int64_t *t_done_ns)

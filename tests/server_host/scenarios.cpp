@@ -149,6 +149,15 @@ void mixed()
         CHECK(t1 >= t0 && t0 > 0);
     }
     CHECK(fake::min_share.load() >= 1);
+    // the monitoring counters of an idle server
+    for (int gi = 0; gi < 3; ++gi) {
+        int64_t st[7];
+        CHECK(bfs_server_graph_stats(b.s, gi, st) == BFS_OK);
+        CHECK(st[0] == 0 && st[1] == 0 && st[2] > 0 && st[3] > 0 && st[4] == 1 && st[5] >= 0 && st[6] == 0);
+    }
+    int64_t st[7];
+    CHECK(bfs_server_graph_stats(b.s, 3, st) == BFS_ERR_INVALID_ARG);
+    CHECK(bfs_server_graph_stats(b.s, 0, nullptr) == BFS_ERR_INVALID_ARG);
 }
 
 // An HBM budget that holds one workspace at a time: graphs take turns, every
@@ -230,6 +239,14 @@ void room_limit()
     starved.gi = 1;
     starved.root = 5;
     CHECK(b.submit(starved) == BFS_OK);
+    std::this_thread::sleep_for(std::chrono::milliseconds(50));
+    {
+        int64_t st[7];  // the starved graph's worker is waiting for room, its query queued
+        CHECK(bfs_server_graph_stats(b.s, 1, st) == BFS_OK);
+        CHECK(st[0] == 1 && st[1] == 0 && st[4] == 0 && (st[6] == 6 || st[6] == 1));
+        CHECK(bfs_server_graph_stats(b.s, 0, st) == BFS_OK);  // the busy one holds its workspace
+        CHECK(st[1] == 1 && st[4] == 1);
+    }
     CHECK(b.wait(starved) == BFS_ERR_BUSY);
     int64_t t0 = 0, t1 = 0;
     CHECK(bfs_ticket_times(b.s, starved.ticket, &t0, &t1) == BFS_OK);

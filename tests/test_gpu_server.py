@@ -151,3 +151,25 @@ def test_device_timeout_fails_queries_without_hanging():
                 s.submit(gid, int(roots[0]), bufs[0])
         finally:
             s.close()
+
+
+def test_graph_stats_after_drain(resident):
+    """The monitoring counters: nothing waiting or running after a drain,
+    rounds and iterations counted for the graphs that had queries, and every
+    worker back to waiting for work."""
+    queries = make_queries(resident, 40, 9)
+    with gb.Server() as s:
+        ids = [s.add_graph(g) for _, _, g in resident]
+        run_mixed(s, ids, resident, queries, 10)
+        for gi, gid in enumerate(ids):
+            deadline = time.time() + 5.0
+            st = s.graph_stats(gid)
+            while st["phase"] != "waiting for work" and time.time() < deadline:
+                time.sleep(0.01)  # the worker may still be leaving its last round
+                st = s.graph_stats(gid)
+            assert st["phase"] == "waiting for work", st
+            assert st["waiting"] == 0 and st["running"] == 0, st
+            if any(q[0] == gi for q in queries):
+                assert st["rounds"] > 0 and st["iter"] > 0 and st["has_workspace"], st
+        with pytest.raises(gb.BfsError):
+            s.graph_stats(len(ids))
