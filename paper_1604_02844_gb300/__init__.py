@@ -132,10 +132,12 @@ def _ptr(a) -> int:
     if a is None:
         return None
     if hasattr(a, "data_ptr"):
-        assert a.is_contiguous(), "tensor must be contiguous"
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
         return a.data_ptr()
     if isinstance(a, np.ndarray):
-        assert a.flags["C_CONTIGUOUS"], "array must be C-contiguous"
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
         return a.ctypes.data
     return int(a)
 
@@ -364,7 +366,8 @@ class Server:
         return bfs_server_add_graph(self.handle, graph.handle)
 
     def submit(self, graph_id: int, root: int, level_out: np.ndarray) -> int:
-        assert level_out.dtype == np.uint8 and level_out.flags["C_CONTIGUOUS"]
+        if not (isinstance(level_out, np.ndarray) and level_out.dtype == np.uint8 and level_out.flags["C_CONTIGUOUS"]):
+            raise ValueError("level_out must be a C-contiguous numpy uint8 array")
         t = bfs_submit(self.handle, graph_id, root, level_out)
         self._keep[t] = level_out
         return t
