@@ -34,6 +34,7 @@ std::atomic<int> injections_during_pull{0};
 std::atomic<int> pull_seen{0};
 std::atomic<int> steps{0};
 std::atomic<int> min_share{1 << 30};
+std::atomic<int> jitter_us{0};
 
 static std::mutex alloc_mu;
 static std::map<void *, size_t> allocs;
@@ -204,6 +205,11 @@ int ms_step_capped(Graph *g, uint32_t max_iters, int max_ctas)
     if (max_ctas < fake::min_share.load()) fake::min_share = max_ctas;
     if (g->n == fake::slow_graph_n.load())
         std::this_thread::sleep_for(std::chrono::microseconds(fake::slow_step_us.load()));
+    if (fake::jitter_us.load() > 0) {
+        thread_local unsigned x = 12345u + (unsigned)(uintptr_t)g;
+        x = x * 1664525u + 1013904223u;
+        std::this_thread::sleep_for(std::chrono::microseconds((x >> 8) % (unsigned)fake::jitter_us.load()));
+    }
     if (g->n == fake::timeout_graph_n.load()) {
         c.status |= ST_TIMEOUT;
         return BFS_OK;

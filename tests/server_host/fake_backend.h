@@ -23,6 +23,7 @@ extern std::atomic<int> injections_during_pull;  // queries put into a batch in 
 extern std::atomic<int> pull_seen;                // rounds that ended with a batch in its heavy phase
 extern std::atomic<int> steps;
 extern std::atomic<int> min_share;            // smallest grid share seen by a step
+extern std::atomic<int> jitter_us;            // each step sleeps a pseudo-random time below this
 
 int depth(int32_t root);                      // iterations a query on `root` runs
 uint8_t level_of(int64_t n, int32_t root, int64_t v);  // its level row

@@ -331,6 +331,42 @@ void pull_hold()
     CHECK(fake::injections_during_pull.load() == 0);
 }
 
+// Eight graphs, Poisson-like arrivals in bursts with buffers recycled as
+// queries finish (the serving measurement's pattern), steps of random
+// length, the pull-phase hold active, and a budget that holds only some of
+// the workspaces at once: every query completes, with its own result.
+void stress()
+{
+    fake::pull_mode = 1;
+    fake::jitter_us = 300;
+    std::vector<int64_t> ns = {300, 700, 1000, 1500, 2000, 2500, 3000, 4000};
+    int64_t budget = 0;
+    {
+        std::vector<int64_t> w;
+        for (int64_t n : ns) {
+            Graph *g = make_graph(n, 16 * n);
+            w.push_back(ws_bytes(g));
+            delete g;
+        }
+        std::sort(w.begin(), w.end());
+        budget = w[7] + w[6] + w[5] + 1000;  // the three largest at once
+    }
+    Bench b(ns, budget);
+    std::mt19937 rng(21);
+    for (int run = 0; run < 3; ++run) {
+        auto qs = random_queries(b, 4000, 100 + run);
+        for (size_t i = 0; i < qs.size(); ++i) {
+            CHECK(b.submit(qs[i]) == BFS_OK);
+            if (rng() % 16 == 0) std::this_thread::sleep_for(std::chrono::microseconds(rng() % 2000));
+        }
+        for (auto &q : qs) {
+            CHECK(b.wait(q, 30.0) == BFS_OK);
+            CHECK(b.result_ok(q));
+        }
+    }
+    CHECK(fake::injections_during_pull.load() == 0);
+}
+
 }  // namespace
 
 int main(int argc, char **argv)
@@ -350,6 +386,7 @@ int main(int argc, char **argv)
     else if (s == "depth_backstop") depth_backstop();
     else if (s == "kernel_depth") kernel_depth();
     else if (s == "pull_hold") pull_hold();
+    else if (s == "stress") stress();
     else {
         fprintf(stderr, "unknown scenario %s\n", s.c_str());
         return 2;

@@ -16,8 +16,11 @@ loop through its C ABI and check that:
 - the host backstop ends a lane that never finishes;
 - the pull-phase hold is kept.
 
-The loop's wait for room is shortened to 0.2 s in this build. A second test
-plants mistakes in a copy of server.cu and checks that each one is caught.
+The loop's wait for room is shortened to 0.2 s in this build. A stress
+scenario mixes eight graphs, bursts of queries, steps of random length, the
+hold and a budget for three workspaces. Every scenario also runs under
+ThreadSanitizer. A last test plants mistakes in a copy of server.cu and
+checks that each one is caught.
 """
 import os
 import shutil
@@ -30,7 +33,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(ROOT, "paper_1604_02844_gb300", "csrc")
 HOST = os.path.join(HERE, "server_host")
 SCENARIOS = ["mixed", "tight_budget", "device_oom_wait", "device_oom_fail", "room_limit", "timeout",
-             "depth_backstop", "kernel_depth", "pull_hold"]
+             "depth_backstop", "kernel_depth", "pull_hold", "stress"]
 
 
 def _cuda_include():
@@ -40,9 +43,9 @@ def _cuda_include():
     return None
 
 
-def _build(server_src, out):
+def _build(server_src, out, extra=()):
     inc = _cuda_include()
-    cmd = ["g++", "-std=c++17", "-O1", "-pthread", "-DGBBFS_ROOM_WAIT_NS=200000000",
+    cmd = ["g++", "-std=c++17", "-O1", "-g", "-pthread", *extra, "-DGBBFS_ROOM_WAIT_NS=200000000",
            f"-I{CSRC}", f"-I{HOST}", f"-I{inc}",
            "-x", "c++", server_src, "-x", "none",
            os.path.join(HOST, "fake_backend.cpp"), os.path.join(HOST, "scenarios.cpp"), "-o", out]
@@ -67,6 +70,23 @@ def server_host(tmp_path_factory):
 def test_scenario(server_host, scenario):
     r = _run(server_host, scenario)
     assert r.returncode == 0 and r.stdout.strip() == "ok", r.stdout + r.stderr
+
+
+def test_no_data_races_under_thread_sanitizer(tmp_path):
+    """Every scenario again, built with ThreadSanitizer: the worker threads,
+    the submitting thread and the pollers share no unsynchronised state."""
+    if shutil.which("g++") is None or _cuda_include() is None:
+        pytest.skip("needs g++ and the CUDA runtime headers")
+    probe = tmp_path / "probe.cpp"
+    probe.write_text("int main() { return 0; }\n")
+    if subprocess.run(["g++", "-fsanitize=thread", str(probe), "-o", str(tmp_path / "probe")],
+                      capture_output=True).returncode != 0:
+        pytest.skip("g++ cannot build with -fsanitize=thread here")
+    exe = _build(os.path.join(CSRC, "server.cu"), str(tmp_path / "server_host_tsan"), ["-fsanitize=thread"])
+    env = dict(os.environ, TSAN_OPTIONS="halt_on_error=1 exitcode=66")
+    for scenario in SCENARIOS:
+        r = subprocess.run([exe, scenario], capture_output=True, text=True, timeout=300, env=env)
+        assert r.returncode == 0 and r.stdout.strip() == "ok", f"{scenario}:\n{r.stdout}{r.stderr[-4000:]}"
 
 
 # (name, text in server.cu, replacement, scenario that must then fail)
@@ -97,3 +117,25 @@ def test_planted_mistakes_are_caught(server_host, tmp_path, name, old, new, scen
     exe = _build(str(mutated), str(tmp_path / "server_host"))
     r = _run(exe, scenario, timeout=90)
     assert r.returncode != 0, f"{name}: scenario {scenario} still passes"
+
+
+def test_planted_race_is_caught(tmp_path):
+    """The race detector itself: a lane mask cleared outside the server's
+    lock (other workers read it under the lock) must be reported."""
+    if shutil.which("g++") is None or _cuda_include() is None:
+        pytest.skip("needs g++ and the CUDA runtime headers")
+    probe = tmp_path / "probe.cpp"
+    probe.write_text("int main() { return 0; }\n")
+    if subprocess.run(["g++", "-fsanitize=thread", str(probe), "-o", str(tmp_path / "probe")],
+                      capture_output=True).returncode != 0:
+        pytest.skip("g++ cannot build with -fsanitize=thread here")
+    src = open(os.path.join(CSRC, "server.cu")).read()
+    old = "    const int64_t t = now_ns();\n    std::lock_guard<std::mutex> lk(mu);\n    for (int i = 0; i < 64; ++i) {"
+    assert src.count(old) == 1, "the planted race no longer applies"
+    mutated = tmp_path / "server.cu"
+    mutated.write_text(src.replace(old, "    const int64_t t = now_ns();\n    gs.running &= ~mask;\n"
+                                        "    std::lock_guard<std::mutex> lk(mu);\n    for (int i = 0; i < 64; ++i) {"))
+    exe = _build(str(mutated), str(tmp_path / "racy"), ["-fsanitize=thread"])
+    env = dict(os.environ, TSAN_OPTIONS="halt_on_error=1 exitcode=66")
+    r = subprocess.run([exe, "stress"], capture_output=True, text=True, timeout=300, env=env)
+    assert r.returncode == 66 and "data race" in r.stderr
