@@ -19,7 +19,7 @@ loop through its C ABI and check that:
 The loop's wait for room is shortened to 0.2 s in this build. A stress
 scenario mixes eight graphs, bursts of queries, steps of random length, the
 hold and a budget for three workspaces. Every scenario also runs under
-ThreadSanitizer. A last test plants mistakes in a copy of server.cu and
+ThreadSanitizer, and under AddressSanitizer with UBSan. A last test plants mistakes in a copy of server.cu and
 checks that each one is caught.
 """
 import os
@@ -72,18 +72,28 @@ def test_scenario(server_host, scenario):
     assert r.returncode == 0 and r.stdout.strip() == "ok", r.stdout + r.stderr
 
 
-def test_no_data_races_under_thread_sanitizer(tmp_path):
-    """Every scenario again, built with ThreadSanitizer: the worker threads,
-    the submitting thread and the pollers share no unsynchronised state."""
-    if shutil.which("g++") is None or _cuda_include() is None:
-        pytest.skip("needs g++ and the CUDA runtime headers")
+def _sanitizer_usable(tmp_path, flag):
     probe = tmp_path / "probe.cpp"
     probe.write_text("int main() { return 0; }\n")
-    if subprocess.run(["g++", "-fsanitize=thread", str(probe), "-o", str(tmp_path / "probe")],
-                      capture_output=True).returncode != 0:
-        pytest.skip("g++ cannot build with -fsanitize=thread here")
-    exe = _build(os.path.join(CSRC, "server.cu"), str(tmp_path / "server_host_tsan"), ["-fsanitize=thread"])
-    env = dict(os.environ, TSAN_OPTIONS="halt_on_error=1 exitcode=66")
+    return subprocess.run(["g++", f"-fsanitize={flag}", str(probe), "-o", str(tmp_path / "probe")],
+                          capture_output=True).returncode == 0
+
+
+@pytest.mark.parametrize("flag", ["thread", "address,undefined"])
+def test_scenarios_under_sanitizers(tmp_path, flag):
+    """Every scenario again, built with ThreadSanitizer (the worker threads,
+    the submitting thread and the pollers share no unsynchronised state) or
+    with AddressSanitizer and UBSan (no use of a workspace after eviction, no
+    leak at shutdown, no undefined arithmetic)."""
+    if shutil.which("g++") is None or _cuda_include() is None:
+        pytest.skip("needs g++ and the CUDA runtime headers")
+    if not _sanitizer_usable(tmp_path, flag):
+        pytest.skip(f"g++ cannot build with -fsanitize={flag} here")
+    extra = [f"-fsanitize={flag}", "-fno-omit-frame-pointer"]
+    if "undefined" in flag:
+        extra.append("-fno-sanitize-recover=undefined")
+    exe = _build(os.path.join(CSRC, "server.cu"), str(tmp_path / "server_host_san"), extra)
+    env = dict(os.environ, TSAN_OPTIONS="halt_on_error=1 exitcode=66", ASAN_OPTIONS="detect_leaks=1")
     for scenario in SCENARIOS:
         r = subprocess.run([exe, scenario], capture_output=True, text=True, timeout=300, env=env)
         assert r.returncode == 0 and r.stdout.strip() == "ok", f"{scenario}:\n{r.stdout}{r.stderr[-4000:]}"
@@ -124,10 +134,7 @@ def test_planted_race_is_caught(tmp_path):
     lock (other workers read it under the lock) must be reported."""
     if shutil.which("g++") is None or _cuda_include() is None:
         pytest.skip("needs g++ and the CUDA runtime headers")
-    probe = tmp_path / "probe.cpp"
-    probe.write_text("int main() { return 0; }\n")
-    if subprocess.run(["g++", "-fsanitize=thread", str(probe), "-o", str(tmp_path / "probe")],
-                      capture_output=True).returncode != 0:
+    if not _sanitizer_usable(tmp_path, "thread"):
         pytest.skip("g++ cannot build with -fsanitize=thread here")
     src = open(os.path.join(CSRC, "server.cu")).read()
     old = "    const int64_t t = now_ns();\n    std::lock_guard<std::mutex> lk(mu);\n    for (int i = 0; i < 64; ++i) {"
