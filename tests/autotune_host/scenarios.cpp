@@ -6,6 +6,7 @@
 #include <stdlib.h>
 
 #include <algorithm>
+#include <memory>
 #include <set>
 #include <string>
 #include <vector>
@@ -27,10 +28,13 @@ namespace {
 constexpr int64_t kN = 1000, kNonzero = 900;
 std::vector<int32_t> orig((size_t)kN);  // internal id -> caller id
 
+std::vector<std::unique_ptr<Graph>> owned;  // freed at exit
+
 Graph *make_graph()
 {
     for (int64_t i = 0; i < kN; ++i) orig[(size_t)i] = (int32_t)((i * 7919) % kN);
-    Graph *g = new Graph();
+    owned.push_back(std::make_unique<Graph>());
+    Graph *g = owned.back().get();
     g->n = kN;
     g->m = 16 * kN;
     g->n_nonzero = kNonzero;

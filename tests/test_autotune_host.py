@@ -31,8 +31,8 @@ def _cuda_include():
     return None
 
 
-def _build(src, out):
-    cmd = ["g++", "-std=c++17", "-O1", "-pthread", f"-I{CSRC}", f"-I{HOST}", f"-I{_cuda_include()}",
+def _build(src, out, extra=()):
+    cmd = ["g++", "-std=c++17", "-O1", "-g", "-pthread", *extra, f"-I{CSRC}", f"-I{HOST}", f"-I{_cuda_include()}",
            "-x", "c++", src, "-x", "none",
            os.path.join(HOST, "fake_runtime.cpp"), os.path.join(HOST, "scenarios.cpp"), "-o", out]
     r = subprocess.run(cmd, capture_output=True, text=True)
@@ -52,6 +52,22 @@ def autotune_host(tmp_path_factory):
 def test_scenario(autotune_host, scenario):
     r = subprocess.run([autotune_host, scenario], capture_output=True, text=True, timeout=120)
     assert r.returncode == 0 and r.stdout.strip() == "ok", r.stdout + r.stderr
+
+
+def test_scenarios_under_address_and_ub_sanitizers(tmp_path):
+    """Every scenario again, built with AddressSanitizer and UBSan."""
+    if shutil.which("g++") is None or _cuda_include() is None:
+        pytest.skip("needs g++ and the CUDA runtime headers")
+    probe = tmp_path / "probe.cpp"
+    probe.write_text("int main() { return 0; }\n")
+    flags = ["-fsanitize=address,undefined", "-fno-sanitize-recover=undefined", "-fno-omit-frame-pointer"]
+    if subprocess.run(["g++", *flags, str(probe), "-o", str(tmp_path / "probe")], capture_output=True).returncode:
+        pytest.skip("g++ cannot build with the sanitizers here")
+    exe = _build(os.path.join(CSRC, "autotune.cu"), str(tmp_path / "autotune_san"), flags)
+    for scenario in SCENARIOS:
+        r = subprocess.run([exe, scenario], capture_output=True, text=True, timeout=120,
+                           env=dict(os.environ, ASAN_OPTIONS="detect_leaks=1"))
+        assert r.returncode == 0 and r.stdout.strip() == "ok", f"{scenario}:\n{r.stdout}{r.stderr[-4000:]}"
 
 
 # (name, text in autotune.cu, replacement, scenario that must then fail)
