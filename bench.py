@@ -25,6 +25,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -117,7 +118,9 @@ class ClockSampler:
     def __init__(self, uuid=None):
         self.uuid = uuid
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        # raw samples: GBBFS_CLOCKS_DIR if set (to keep them), else the temp dir
+        d = os.environ.get("GBBFS_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(d, f"gbbfs_clocks_{os.getpid()}_{id(self)}.csv")
 
     def __enter__(self):
         try:
