@@ -260,6 +260,8 @@ int bfs_run_batch(bfs_graph *g, const int32_t *roots, int32_t k, uint8_t *level_
 /* ---- serving ------------------------------------------------------------ */
 
 /*
+ * Serving (not in the paper; each query is the search of Sec. 3, run by the
+ * batched layer step of bfs_run_batch).
  * A request loop over resident graphs with continuous batching: queries on
  * one graph are packed into the lanes of bit-parallel batches as they
  * arrive; a lane freed by a finished query is given to the next waiting one
@@ -298,7 +300,8 @@ int bfs_poll(bfs_server *s, uint64_t ticket);
 /* Block until every submitted query has completed (or failed). */
 int bfs_server_drain(bfs_server *s);
 
-/* Monitoring counters of one graph of the server, written to out[0..6]:
+/* Monitoring counters (not in the paper) of one graph of the server,
+ * written to out[0..6]:
  *   out[0] queries waiting for a lane     out[1] lanes running
  *   out[2] rounds its worker has run      out[3] the batch's iteration after
  *                                                the last round (-1 = none)
