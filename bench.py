@@ -393,6 +393,11 @@ def batched_measurement(args, gb, torch, dev):
 _KEEP_ALIVE = []  # objects of a serving run that did not finish
 
 
+# deadline of one serving run: a base plus a share per query
+SERVING_WAIT_S = 120.0
+SERVING_WAIT_PER_QUERY_S = 0.002
+
+
 class ServingStuck(Exception):
     pass
 
@@ -412,19 +417,32 @@ def wait_tickets(poll, tickets, limit_s, sleep_s=0.0002):
         time.sleep(sleep_s)
 
 
+class ServingFailed(Exception):
+    """A serving attempt that stopped, with each graph's queue and worker state."""
+
+    def __init__(self, msg, graphs):
+        super().__init__(msg)
+        self.graphs = graphs
+
+
 def serving_measurement(args, gb, torch, dev):
     """Eight resident Kronecker graphs (scales 12..23; edgefactor 16 from
     scale 16, 8 below), requests choosing a graph with probability
     proportional to 1/scale and a uniform source of degree >= 1, Poisson
     arrivals.  Saturated throughput first (all requests at once), then rate
     points at 0.5/0.7/0.9 of it; latency = completion - submission, from the
-    library's own ticket times.  Plain path: bfs_run one query at a time."""
+    library's own ticket times.  Plain path: bfs_run one query at a time.
+    An attempt that stops (a query unfinished past its deadline, or a failed
+    query) is reported with its diagnostics and run once more on a fresh
+    server with freshly uploaded graphs."""
     import graphgen
+    import threading
     scales = [int(x) for x in args.serving_scales.split(",")]
-    graphs, roots = [], []
+    workload = "kronecker_scales_" + "_".join(map(str, scales)) + "_poisson"
+    csrs, roots = [], []
     for s_ in scales:
         ro, col = graphgen.kronecker(s_, 16 if s_ >= 16 else 8, args.seed + s_)
-        graphs.append((len(ro) - 1, gb.Graph(ro, col)))
+        csrs.append((ro, col))
         roots.append(graphgen.pick_roots(ro, 4096, args.seed + 100 + s_, distinct=False))
     w = np.array([1.0 / s_ for s_ in scales])
     w /= w.sum()
@@ -434,88 +452,104 @@ def serving_measurement(args, gb, torch, dev):
         gi = rng.choice(len(scales), size=k, p=w)
         return [(int(g_), int(roots[g_][rng.integers(0, len(roots[g_]))])) for g_ in gi]
 
-    pools = [[] for _ in scales]
+    def upload():
+        return [(len(ro) - 1, gb.Graph(ro, col)) for ro, col in csrs]
 
-    def buf(gi):
-        if pools[gi]:
-            return pools[gi].pop()
-        return torch.empty(graphs[gi][0], dtype=torch.uint8).pin_memory().numpy()
+    def attempt(graphs):
+        """One full serving measurement on a new server; returns (sat, points)."""
+        server = gb.Server()
+        ids = [server.add_graph(g) for _, g in graphs]
+        pools = [[] for _ in scales]  # recycled pinned result buffers of this attempt
 
-    server = gb.Server()
-    ids = [server.add_graph(g) for _, g in graphs]
+        def buf(gi):
+            if pools[gi]:
+                return pools[gi].pop()
+            return torch.empty(graphs[gi][0], dtype=torch.uint8).pin_memory().numpy()
 
+        def run(reqs, rate):
+            """Submit reqs at Poisson times (rate None = all at once); returns
+            (elapsed_s, latencies_s)."""
+            import collections
+            gaps = rng.exponential(1.0 / rate, size=len(reqs)) if rate else np.zeros(len(reqs))
+            inflight = collections.deque()
+            tickets = []
+            t0 = time.perf_counter()
+            t_next = t0
+            for (gi, r), gap in zip(reqs, gaps):
+                t_next += gap
+                # recycle finished buffers (oldest first, a few per arrival)
+                for _ in range(4):
+                    if inflight and server.poll(inflight[0][0]):
+                        t, g_, b = inflight.popleft()
+                        pools[g_].append(b)
+                    else:
+                        break
+                while time.perf_counter() < t_next:
+                    pass
+                b = buf(gi)
+                t = server.submit(ids[gi], r, b)
+                tickets.append(t)
+                inflight.append((t, gi, b))
+            wait_tickets(server.poll, tickets, SERVING_WAIT_S + len(reqs) * SERVING_WAIT_PER_QUERY_S)
+            elapsed = time.perf_counter() - t0
+            for t, g_, b in inflight:
+                pools[g_].append(b)
+            server._keep.clear()
+            lat = []
+            for t in tickets:
+                a, b2 = server.times(t)
+                lat.append((b2 - a) * 1e-9)
+            return elapsed, np.array(lat)
 
-    def run(reqs, rate):
-        """Submit reqs at Poisson times (rate None = all at once); returns
-        (elapsed_s, latencies_s)."""
-        import collections
-        gaps = rng.exponential(1.0 / rate, size=len(reqs)) if rate else np.zeros(len(reqs))
-        inflight = collections.deque()
-        tickets = []
-        t0 = time.perf_counter()
-        t_next = t0
-        for (gi, r), gap in zip(reqs, gaps):
-            t_next += gap
-            # recycle finished buffers (oldest first, a few per arrival)
-            for _ in range(4):
-                if inflight and server.poll(inflight[0][0]):
-                    t, g_, b = inflight.popleft()
-                    pools[g_].append(b)
-                else:
-                    break
-            while time.perf_counter() < t_next:
-                pass
-            b = buf(gi)
-            t = server.submit(ids[gi], r, b)
-            tickets.append(t)
-            inflight.append((t, gi, b))
-        wait_tickets(server.poll, tickets, 120.0 + len(reqs) / 500.0)
-        elapsed = time.perf_counter() - t0
-        for t, g_, b in inflight:
-            pools[g_].append(b)
-        server._keep.clear()
-        lat = []
-        for t in tickets:
-            a, b2 = server.times(t)
-            lat.append((b2 - a) * 1e-9)
-        return elapsed, np.array(lat)
+        try:
+            run(draw(2000), None)  # warm-up: workspaces, kernels
+            n_sat = min(20000, args.serving_requests)
+            el, lat = run(draw(n_sat), None)
+            sat = n_sat / el
+            points = []
+            for frac in (0.5, 0.7, 0.9):
+                k = args.serving_requests if frac == 0.7 else max(1000, args.serving_requests // 5)
+                el, lat = run(draw(k), frac * sat)
+                points.append({"rate_fraction_of_saturation": frac, "offered_qps": frac * sat, "requests": k,
+                               "queries_per_s": k / el, "p50_ms": float(np.percentile(lat, 50) * 1e3),
+                               "p99_ms": float(np.percentile(lat, 99) * 1e3)})
+        except (ServingStuck, gb.BfsError) as e:
+            # each graph's queue and worker state, then a bounded attempt to
+            # close; the server and its graphs stay alive (closing them under
+            # a stuck worker could block the process)
+            stats = []
 
-    try:
-        run(draw(2000), None)  # warm-up: workspaces, kernels
-        n_sat = min(20000, args.serving_requests)
-        el, lat = run(draw(n_sat), None)
-        sat = n_sat / el
-        points = []
-        for frac in (0.5, 0.7, 0.9):
-            k = args.serving_requests if frac == 0.7 else max(1000, args.serving_requests // 5)
-            el, lat = run(draw(k), frac * sat)
-            points.append({"rate_fraction_of_saturation": frac, "offered_qps": frac * sat, "requests": k,
-                           "queries_per_s": k / el, "p50_ms": float(np.percentile(lat, 50) * 1e3),
-                           "p99_ms": float(np.percentile(lat, 99) * 1e3)})
-    except (ServingStuck, gb.BfsError) as e:
-        # report instead of hanging, with each graph's queue and worker state;
-        # the server and its graphs are left alive (closing them under a stuck
-        # worker could block the process)
-        import threading
-        stats = []
+            def snapshot():
+                for i, s_ in enumerate(scales):
+                    try:
+                        stats.append(dict(scale=s_, **server.graph_stats(ids[i])))
+                    except Exception as e2:  # noqa: BLE001
+                        stats.append({"scale": s_, "error": str(e2)})
 
-        def snapshot():
-            for i, s_ in enumerate(scales):
-                try:
-                    stats.append(dict(scale=s_, **server.graph_stats(ids[i])))
-                except Exception as e2:  # noqa: BLE001
-                    stats.append({"scale": s_, "error": str(e2)})
+            th = threading.Thread(target=snapshot, daemon=True)
+            th.start()
+            th.join(10.0)
+            closer = threading.Thread(target=server.close, daemon=True)
+            closer.start()
+            closer.join(30.0)
+            _KEEP_ALIVE.append((server, graphs))
+            raise ServingFailed(f"serving measurement stopped: {e}", stats) from e
+        server.close()
+        return sat, points
 
-        th = threading.Thread(target=snapshot, daemon=True)
-        th.start()
-        th.join(10.0)
-        closer = threading.Thread(target=server.close, daemon=True)
-        closer.start()
-        closer.join(30.0)
-        _KEEP_ALIVE.append((server, graphs))
-        return {"workload": "kronecker_scales_" + "_".join(map(str, scales)) + "_poisson",
-                "error": f"serving measurement stopped: {e}", "graphs": stats}
-    server.close()
+    stalls = []
+    graphs = upload()
+    for _ in range(2):
+        try:
+            sat, points = attempt(graphs)
+            break
+        except ServingFailed as f:
+            stalls.append({"error": str(f), "graphs": f.graphs})
+            graphs = upload()  # the stopped server keeps the old ones
+    else:
+        for _, g in graphs:
+            g.close()
+        return {"workload": workload, "error": "serving measurement stopped twice", "stalls": stalls}
     # plain path: bfs_run one query at a time (levels to pinned host memory)
     plain_reqs = draw(2000)
     outs = {}
@@ -533,15 +567,18 @@ def serving_measurement(args, gb, torch, dev):
     for _, g in graphs:
         g.close()
     head = points[1]
-    return {"workload": "kronecker_scales_" + "_".join(map(str, scales)) + "_poisson",
-            "requests": head["requests"], "saturated_queries_per_s": sat,
-            "queries_per_s": head["queries_per_s"], "p50_ms": head["p50_ms"], "p99_ms": head["p99_ms"],
-            "offered_qps": head["offered_qps"], "sweep": points,
-            "plain_queries_per_s": len(plain_reqs) / plain_el,
-            "plain_p50_ms": float(np.percentile(plat, 50) * 1e3), "plain_p99_ms": float(np.percentile(plat, 99) * 1e3),
-            "how": "bfs_submit/bfs_poll (64-lane continuous batching, uint8 levels to pinned host buffers); "
-                   "latency from the library's ticket times; plain = bfs_run + sync per query, "
-                   "int32 levels to pinned host memory, back to back"}
+    out = {"workload": workload,
+           "requests": head["requests"], "saturated_queries_per_s": sat,
+           "queries_per_s": head["queries_per_s"], "p50_ms": head["p50_ms"], "p99_ms": head["p99_ms"],
+           "offered_qps": head["offered_qps"], "sweep": points,
+           "plain_queries_per_s": len(plain_reqs) / plain_el,
+           "plain_p50_ms": float(np.percentile(plat, 50) * 1e3), "plain_p99_ms": float(np.percentile(plat, 99) * 1e3),
+           "how": "bfs_submit/bfs_poll (64-lane continuous batching, uint8 levels to pinned host buffers); "
+                  "latency from the library's ticket times; plain = bfs_run + sync per query, "
+                  "int32 levels to pinned host memory, back to back"}
+    if stalls:
+        out["stalls_before_this_attempt"] = stalls
+    return out
 
 
 def run_ours(args):

@@ -78,3 +78,136 @@ def test_profiled_traffic_only_for_the_profiled_kernel(tmp_path, monkeypatch):
         "traffic_bytes_per_launch: 123\nsource_sha256_16: 0000000000000000\n")
     monkeypatch.setattr(bench, "ROOT", str(root))
     assert bench.profiled_traffic(args, {"mode": 0, "block": 512}) is None
+
+
+# ---- the serving measurement's control flow, on a stand-in library --------
+
+class _FakeBfsError(Exception):
+    def __init__(self, status, msg=""):
+        super().__init__(msg)
+        self.status = status
+
+
+class _FakeGraph:
+    def __init__(self, ro, col):
+        self.n = len(ro) - 1
+        self.handle = object()
+        self.closed = False
+
+    def close(self):
+        self.closed = True
+
+
+def _fake_gb(stall_servers, fail_servers=()):
+    """A stand-in for the library: servers numbered from 0; those listed in
+    stall_servers never complete a query, those in fail_servers report every
+    query as failed."""
+    import time as _t
+    import types
+    state = {"servers": 0}
+
+    class Server:
+        def __init__(self):
+            self.no = state["servers"]
+            state["servers"] += 1
+            self.stall = self.no in stall_servers
+            self.fail = self.no in fail_servers
+            self.graphs = []
+            self._keep = {}
+            self.t = {}
+            self.closed = False
+
+        def add_graph(self, g):
+            self.graphs.append(g)
+            return len(self.graphs) - 1
+
+        def submit(self, gid, root, buf):
+            t = len(self.t) + 1
+            self.t[t] = _t.monotonic_ns()
+            return t
+
+        def poll(self, t):
+            if self.fail:
+                raise _FakeBfsError(-6, "a device-side wait ran out")
+            return not self.stall
+
+        def times(self, t):
+            return self.t[t], self.t[t] + 1000
+
+        def graph_stats(self, gid):
+            return {"waiting": 1, "running": 0, "phase": "waiting for work"}
+
+        def close(self):
+            self.closed = True
+
+    return types.SimpleNamespace(Graph=_FakeGraph, Server=Server, BfsError=_FakeBfsError,
+                                 bfs_run=lambda *a: None), state
+
+
+def _fake_torch():
+    import types
+    import numpy as np
+
+    class T:
+        def __init__(self, n, dtype):
+            self.a = np.zeros(n, dtype)
+
+        def pin_memory(self):
+            return self
+
+        def numpy(self):
+            return self.a
+
+    class Stream:
+        def synchronize(self):
+            pass
+
+    cuda = types.SimpleNamespace(current_stream=lambda dev=None: Stream())
+    return types.SimpleNamespace(empty=lambda n, dtype=None: T(n, dtype), uint8=np.uint8, int32=np.int32, cuda=cuda)
+
+
+def _serving_args():
+    import argparse
+    return argparse.Namespace(serving_scales="6,7", seed=1, serving_requests=1000)
+
+
+@pytest.fixture
+def short_deadline(monkeypatch):
+    monkeypatch.setattr(bench, "SERVING_WAIT_S", 0.2)
+    monkeypatch.setattr(bench, "SERVING_WAIT_PER_QUERY_S", 0.0)
+    monkeypatch.setattr(bench, "_KEEP_ALIVE", [])
+
+
+def test_serving_measurement_normal_run(short_deadline):
+    pytest.importorskip("graphgen")
+    gb, state = _fake_gb(stall_servers=())
+    out = bench.serving_measurement(_serving_args(), gb, _fake_torch(), None)
+    assert "error" not in out and "stalls_before_this_attempt" not in out
+    assert out["queries_per_s"] > 0 and len(out["sweep"]) == 3 and state["servers"] == 1
+
+
+def test_serving_measurement_retries_once_after_a_stall(short_deadline):
+    pytest.importorskip("graphgen")
+    gb, state = _fake_gb(stall_servers=(0,))
+    out = bench.serving_measurement(_serving_args(), gb, _fake_torch(), None)
+    assert "error" not in out and out["queries_per_s"] > 0
+    (stall,) = out["stalls_before_this_attempt"]
+    assert "unfinished" in stall["error"] and len(stall["graphs"]) == 2
+    assert state["servers"] == 2 and len(bench._KEEP_ALIVE) == 1
+
+
+def test_serving_measurement_reports_two_stalls(short_deadline):
+    pytest.importorskip("graphgen")
+    gb, state = _fake_gb(stall_servers=(0, 1))
+    out = bench.serving_measurement(_serving_args(), gb, _fake_torch(), None)
+    assert out["error"] == "serving measurement stopped twice" and len(out["stalls"]) == 2
+    assert state["servers"] == 2
+
+
+def test_serving_measurement_retries_after_failed_queries(short_deadline):
+    pytest.importorskip("graphgen")
+    gb, state = _fake_gb(stall_servers=(), fail_servers=(0,))
+    out = bench.serving_measurement(_serving_args(), gb, _fake_torch(), None)
+    assert "error" not in out and out["queries_per_s"] > 0
+    (stall,) = out["stalls_before_this_attempt"]
+    assert "device-side wait" in stall["error"] and state["servers"] == 2
