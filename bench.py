@@ -393,6 +393,17 @@ def batched_measurement(args, gb, torch, dev):
 _KEEP_ALIVE = []  # objects of a serving run that did not finish
 
 
+def guarded(name, fn):
+    """Run one of the measurements beside the headline; an exception becomes
+    an error entry, so that the line with the headline is still printed."""
+    try:
+        return fn()
+    except Exception as e:  # noqa: BLE001
+        import traceback
+        traceback.print_exc(file=sys.stderr)
+        return {"error": f"{name}: {type(e).__name__}: {e}"}
+
+
 # deadline of one serving run: a base plus a share per query
 SERVING_WAIT_S = 120.0
 SERVING_WAIT_PER_QUERY_S = 0.002
@@ -699,22 +710,25 @@ def run_ours(args):
     options = {k: g.get_option(k) for k in gb.OPTION_NAMES}
     ablation = None
     if not args.no_ablation and rank == 0:
-        ablation = ablation_measurement(g, gb, torch, roots, mcc, checks, level, parent, flush, stream)
-        for v in ablation.values():
-            v["vs_mode0_atomic"] = v["hm_gteps"] / hm
+        def ablate():
+            out = ablation_measurement(g, gb, torch, roots, mcc, checks, level, parent, flush, stream)
+            for v in out.values():
+                v["vs_mode0_atomic"] = v["hm_gteps"] / hm
+            return out
+        ablation = guarded("ablation", ablate)
     batched = None
     if not args.no_batched and rank == 0:
-        batched = batched_measurement(args, gb, torch, dev)
-        batched["uneven_mix"] = uneven_mix_measurement(args, gb, torch, dev, (ro, g))
+        batched = guarded("batched", lambda: batched_measurement(args, gb, torch, dev))
+        batched["uneven_mix"] = guarded("uneven_mix", lambda: uneven_mix_measurement(args, gb, torch, dev, (ro, g)))
     serving = None
     if not args.no_serving and rank == 0:
         with ClockSampler(uuid) as sclocks:
-            serving = serving_measurement(args, gb, torch, dev)
+            serving = guarded("serving", lambda: serving_measurement(args, gb, torch, dev))
         serving["clocks"] = sclocks.summary()
     if rank == 0:
         cpu = None
         if not args.no_cpu_baseline:
-            cpu = cpu_baseline(ro, col, roots, args.cpu_sample_roots)
+            cpu = guarded("cpu_baseline", lambda: cpu_baseline(ro, col, roots, args.cpu_sample_roots))
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
@@ -729,7 +743,7 @@ def run_ours(args):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_kind": peak_kind,
                          "traffic": profiled_traffic(args, options),
-                         "kernel": "td_warp_kernel" if options.get("mode") == 0 else "td_kernel",
+                         "kernel": "td_kernel" if options.get("mode") == 1 else f"td_warp_kernel (mode {options.get('mode')})",
                          "algorithmic_bytes_per_launch": mean_bytes,
                          "mean_launch_s": mean_t},
             "cpu_baseline": cpu,

@@ -211,3 +211,13 @@ def test_serving_measurement_retries_after_failed_queries(short_deadline):
     assert "error" not in out and out["queries_per_s"] > 0
     (stall,) = out["stalls_before_this_attempt"]
     assert "device-side wait" in stall["error"] and state["servers"] == 2
+
+
+def test_guarded_turns_an_exception_into_an_entry():
+    assert bench.guarded("x", lambda: {"a": 1}) == {"a": 1}
+
+    def boom():
+        raise RuntimeError("device lost")
+
+    out = bench.guarded("batched", boom)
+    assert out == {"error": "batched: RuntimeError: device lost"}
