@@ -424,7 +424,7 @@ def wait_tickets(poll, tickets, limit_s, sleep_s=0.0002):
             i += 1
             continue
         if time.perf_counter() > deadline:
-            raise ServingStuck(f"{len(tickets) - i} of {len(tickets)} queries unfinished after {limit_s:.0f} s")
+            raise ServingStuck(f"{len(tickets) - i} of {len(tickets)} queries unfinished after {limit_s:.1f} s")
         time.sleep(sleep_s)
 
 
