@@ -310,13 +310,16 @@ def ablation_measurement(g, gb, torch, roots, mcc, checks, level, parent, flush,
     return out
 
 
+UNEVEN_MIX_SCALES = (12, 14, 16, 18, 20, 22)
+
+
 def uneven_mix_measurement(args, gb, torch, dev, main_graph):
     """256 seeded sources spread round-robin over six resident Kronecker
     graphs of scales 12, 14, 16, 18, 20 and 22 (43/43/43/43/42/42), each
     graph's share run by one bfs_run_batch (one persistent launch sequence);
     host wall clock around the six calls, best of 3."""
     import graphgen
-    scales = [12, 14, 16, 18, 20, 22]
+    scales = list(UNEVEN_MIX_SCALES)
     counts = [len(range(i, 256, len(scales))) for i in range(len(scales))]
     parts = []
     for s_, k in zip(scales, counts):
@@ -341,7 +344,7 @@ def uneven_mix_measurement(args, gb, torch, dev, main_graph):
     for g, own, _, _ in parts:
         if own:
             g.close()
-    return {"workload": "kronecker_scales_12_14_16_18_20_22_256sources", "sources_per_graph": counts,
+    return {"workload": "kronecker_scales_" + "_".join(map(str, scales)) + "_256sources", "sources_per_graph": counts,
             "queries_per_s": 256 / best, "s_per_256": best}
 
 
