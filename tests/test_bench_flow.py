@@ -14,7 +14,9 @@ import sys
 
 import pytest
 
-HARNESS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "bench_flow", "run_with_stand_ins.py")
+HERE = os.path.dirname(os.path.abspath(__file__))
+HARNESS = os.path.join(HERE, "bench_flow", "run_with_stand_ins.py")
+BENCH = os.path.join(os.path.dirname(HERE), "bench.py")
 
 
 def _run(*stalling):
@@ -66,3 +68,17 @@ def test_flow_with_two_stalled_serving_attempts():
     _check_contract(line)
     assert line["serving"]["error"] == "serving measurement stopped twice"
     assert len(line["serving"]["stalls"]) == 2
+
+
+def test_reference_arm_line():
+    """--impl reference (the oracle on the host cores) on a small graph."""
+    r = subprocess.run([sys.executable, BENCH, "--impl", "reference", "--scale", "10",
+                        "--steps", "2", "--warmup", "3"], capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-4000:]
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["value"] > 0 and line["unit"] == "GTEPS"
+    assert line["steps"] == 2 and line["warmup"] == 3 and line["higher_is_better"] is True
+    assert line["config"]["workload"] == "kronecker_scale10_ef16_64roots"
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
+    assert line["e2e"] == {"value": line["value"], "unit": "GTEPS", "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
