@@ -8,11 +8,12 @@ point is that the flow completes and the line has its keys.
 
     python run_with_stand_ins.py [stalling server numbers ...]
 
-prints the bench's JSON line, then one line "exit: <how the bench ended>".
+prints the bench's JSON line (rank 0 only), then one line "exit: <how the
+bench ended>".  Under torch.distributed.run each rank runs it, and the ranks
+meet over gloo.
 """
 import contextlib
 import io
-import json
 import os
 import sys
 import time
@@ -152,6 +153,8 @@ with contextlib.redirect_stdout(buf):
         how = f"returned {bench.main(['--scale', '10', '--steps', '1', '--warmup', '3', '--batched-scale', '10', '--batched-sources', '64', '--serving-requests', '2000', '--serving-scales', '6,7', '--cpu-sample-roots', '4'])}"
     except _Exited as e:
         how = f"direct exit {e.args[0]}"
-print(buf.getvalue().strip().splitlines()[-1])
+lines = buf.getvalue().strip().splitlines()
+if lines:  # ranks other than 0 print no line
+    print(lines[-1])
 print(f"exit: {how}")
 sys.stdout.flush()

@@ -89,3 +89,21 @@ def test_reference_arm_other_ranks_do_no_work():
     r = subprocess.run([sys.executable, BENCH, "--impl", "reference", "--scale", "10", "--gpus", "2",
                         "--steps", "1", "--warmup", "3"], capture_output=True, text=True, timeout=600, env=env)
     assert r.returncode == 0 and r.stdout.strip() == ""
+
+
+def test_flow_with_two_ranks_over_gloo(tmp_path):
+    """Two replicas (ranks over gloo, as under torchrun): rank 0 prints one
+    line whose value is the sum over the ranks, both ranks finish."""
+    import socket
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    r = subprocess.run([sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+                        "--master-addr", "127.0.0.1", "--master-port", str(port), HARNESS],
+                       capture_output=True, text=True, timeout=900, cwd=str(tmp_path))
+    assert r.returncode == 0, r.stdout[-2000:] + r.stderr[-4000:]
+    out = [ln for ln in r.stdout.splitlines() if ln.strip()]
+    lines = [json.loads(ln) for ln in out if ln.startswith("{")]
+    assert len(lines) == 1 and sum(ln.startswith("exit:") for ln in out) == 2
+    line = lines[0]
+    assert line["n_gpus"] == 2 and line["value"] > 0 and line["config"]["parallelism"] == "replicas"
