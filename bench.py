@@ -222,7 +222,8 @@ def cpu_baseline(ro, col, roots, k):
         teps.append(mcc / s)
     return {"value": harmonic_mean(teps) / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{len(sample)} of the {len(roots)} roots, same graph, steady clock around each search",
-            "host_cores_available": os.cpu_count(), "seconds": sum(secs)}
+            "host_cores_available": os.cpu_count(), "seconds": sum(secs),
+            "queries_per_s": len(sample) / sum(secs)}
 
 
 def run_reference(args):
