@@ -109,10 +109,13 @@ typedef enum {
 
 /* ---- library ------------------------------------------------------------ */
 
-/* ABI version of this header (increments on incompatible change). */
+/* ABI version of this header (library plumbing, not in the paper;
+ * increments on an incompatible change). */
 int bfs_abi_version(void);
 
-/* Message and code of the most recent failure on this host thread. */
+/* Message and code of the most recent failure on this host thread (library
+ * plumbing, not in the paper).  The message stays valid until the thread's
+ * next library call. */
 const char *bfs_last_error(void);
 int bfs_last_status(void);
 
@@ -136,14 +139,21 @@ int bfs_last_status(void);
 bfs_graph *bfs_graph_create(const int32_t *row_offsets, const int32_t *col_idx,
                             int64_t n, int64_t m);
 
-/* Free the graph and its workspaces after all its work has finished.
- * NULL is accepted.  Returns BFS_OK or BFS_ERR_CUDA. */
+/* Free the graph of bfs_graph_create (the CSR of Sec. 3.3.1) and its
+ * workspaces, after waiting for its last run.  NULL is accepted.  Returns
+ * BFS_OK or BFS_ERR_CUDA. */
 int bfs_graph_destroy(bfs_graph *g);
 
+/* n and m of the graph as given to bfs_graph_create (Sec. 3.3.1: the
+ * vertices and the CSR entries), or -1 for NULL. */
 int64_t bfs_graph_num_vertices(const bfs_graph *g);
 int64_t bfs_graph_num_edges(const bfs_graph *g);
 
-/* Set / read a tunable.  Invalid values give BFS_ERR_INVALID_ARG. */
+/* Set / read a tunable (bfs_option; not in the paper, whose tunables are
+ * Xeon Phi thread counts and affinities, Sec. 5).  Options change the time
+ * of a search, never its result.  Invalid values give BFS_ERR_INVALID_ARG
+ * and leave the option unchanged; get returns the value, or a negative
+ * bfs_status for a NULL graph or an unknown option. */
 int bfs_graph_set_option(bfs_graph *g, int option, int64_t value);
 int64_t bfs_graph_get_option(const bfs_graph *g, int option);
 
@@ -168,8 +178,8 @@ int bfs_run(bfs_graph *g, int32_t root, int32_t *level_out, int32_t *parent_out,
             void *stream);
 
 /*
- * Single-source search that allocates nothing (the paper has no counterpart:
- * this is a deployment variant of bfs_run).  For callers that cannot
+ * Single-source search that allocates nothing (not in the paper: a
+ * deployment variant of bfs_run, whose search is the top-down BFS of Alg. 2).  For callers that cannot
  * allocate GPU memory at the moment they search -- a process whose device
  * memory is owned by another allocator or fixed budget, a latency-critical
  * path that must not block in cudaMalloc/cudaFree, or code running where
@@ -196,8 +206,9 @@ int bfs_run(bfs_graph *g, int32_t root, int32_t *level_out, int32_t *parent_out,
 int bfs_run_noalloc(const int32_t *row_offsets, const int32_t *col_idx, int64_t n, int64_t m,
                     int32_t root, int32_t *level_out, int32_t *parent_out, void *stream);
 
-/* Wait for the graph's last run and return its device-side status
- * (BFS_OK, BFS_ERR_TIMEOUT or BFS_ERR_CUDA); clears the status word. */
+/* Wait for the graph's last run (any bfs_run of Alg. 1-3) and return its
+ * device-side status (BFS_OK, BFS_ERR_TIMEOUT or BFS_ERR_CUDA); clears the
+ * status word. */
 int bfs_graph_status(bfs_graph *g);
 
 /*
@@ -212,9 +223,10 @@ int bfs_graph_status(bfs_graph *g);
 int bfs_graph_layer_stats(bfs_graph *g, int64_t *vertices, int64_t *edges,
                           int64_t *traversed, int32_t max_layers);
 
-/* Device time at the end of each layer of the last bfs_run, ns since the
- * kernel started (recorded with BFS_OPT_LAYER_STATS = 1).  Returns the
- * number of layers or a negative bfs_status.  Synchronous. */
+/* Device time at the end of each layer (Sec. 3: layer L_d) of the last
+ * bfs_run, ns since the kernel started (recorded with BFS_OPT_LAYER_STATS =
+ * 1).  t_end_ns: host int64[max_layers].  Returns the number of layers or a
+ * negative bfs_status.  Synchronous. */
 int bfs_graph_layer_times(bfs_graph *g, int64_t *t_end_ns, int32_t max_layers);
 
 /*
@@ -278,26 +290,40 @@ int bfs_run_batch(bfs_graph *g, const int32_t *roots, int32_t k, uint8_t *level_
  * other graphs keep running.
  */
 bfs_server *bfs_server_create(int64_t hbm_budget_bytes);
+
+/* Serving, not in the paper.  Stop the workers (each finishes its current
+ * round), free the workspaces
+ * and the server.  Queries still queued are dropped: drain first to keep
+ * them.  NULL is accepted.  Returns BFS_OK. */
 int bfs_server_destroy(bfs_server *s);
 
-/* Register a graph (not owned: keep it alive until bfs_server_destroy).
+/* Serving, not in the paper.  Register a graph (not owned: keep it alive
+ * until bfs_server_destroy).
  * From then on the server owns the graph's batch workspace: do not call
  * bfs_run_batch on it while it is registered (bfs_run stays available).
  * Returns a graph id >= 0 or a negative bfs_status. */
 int bfs_server_add_graph(bfs_server *s, bfs_graph *g);
 
-/* Queue one BFS query.  level_out: host uint8[n] of that graph, written as in
- * bfs_run_batch (0xFF = unreached); it must stay valid until bfs_poll
- * reports completion.  *ticket receives the query's id.  Returns
- * BFS_ERR_BUSY if the graph's workspace can never fit the HBM budget. */
+/* Queue one BFS query: the search of Sec. 3 from `root` on graph graph_id,
+ * levels only.  level_out: host uint8[n] of that graph (caller-owned),
+ * written as in bfs_run_batch (0xFF = unreached); it must stay valid until
+ * bfs_poll reports completion or failure.  *ticket receives the query's id
+ * (>= 1).  Returns BFS_ERR_INVALID_ARG (NULL pointer, unknown graph, root
+ * outside [0, n)), BFS_ERR_BUSY if the graph's workspace can never fit the
+ * HBM budget, or the server's error once it has stopped after one. */
 int bfs_submit(bfs_server *s, int graph_id, int32_t root, uint8_t *level_out,
                uint64_t *ticket);
 
-/* BFS_OK when the query is complete (level_out filled), BFS_NOT_READY while
- * it runs, or a negative bfs_status.  Never blocks. */
+/* Serving, not in the paper.  BFS_OK when the query is complete (level_out
+ * filled), BFS_NOT_READY while
+ * it waits or runs, or the negative bfs_status it failed with
+ * (BFS_ERR_INVALID_ARG for an unknown ticket).  Never blocks. */
 int bfs_poll(bfs_server *s, uint64_t ticket);
 
-/* Block until every submitted query has completed (or failed). */
+/* Serving, not in the paper.  Block until every submitted query has
+ * completed or failed.  Returns
+ * BFS_OK, or the error that stopped the server (queries that failed alone,
+ * e.g. with BFS_ERR_BUSY, are reported by bfs_poll only). */
 int bfs_server_drain(bfs_server *s);
 
 /* Monitoring counters (not in the paper) of one graph of the server,
@@ -315,7 +341,10 @@ int bfs_server_drain(bfs_server *s);
  * BFS_ERR_INVALID_ARG (NULL pointer, unknown graph id). */
 int bfs_server_graph_stats(bfs_server *s, int graph_id, int64_t *out);
 
-/* Submission and completion times of a query, ns on a monotonic clock. */
+/* Serving, not in the paper.  Submission and completion times of a query,
+ * ns on a monotonic clock
+ * (latency = t_done - t_submit; t_done is 0 while it runs).  Returns BFS_OK
+ * or BFS_ERR_INVALID_ARG. */
 int bfs_ticket_times(bfs_server *s, uint64_t ticket, int64_t *t_submit_ns,
                      int64_t *t_done_ns);
 

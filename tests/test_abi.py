@@ -76,3 +76,20 @@ def test_missing_library_fails_loudly(tmp_path, monkeypatch):
     monkeypatch.setattr(gb, "_lib", None)
     with pytest.raises(RuntimeError, match="no CPU fallback"):
         gb.load(str(tmp_path / "nope.so"))
+
+
+def test_every_declaration_states_its_provenance():
+    """Each entry point's comment (the nearest one above it) cites the passage
+    of the paper that defines the operation, or says that it is not in the
+    paper."""
+    import re
+    src = open(HEADER).read()
+    cites = ("Sec.", "Alg.", "Table", "Listing", "not in the paper")
+    missing = []
+    for m in re.finditer(r"^[A-Za-z_][\w \*]*?\b(bfs_\w+)\s*\(", src, re.M):
+        head = src[:m.start()]
+        last = head.rfind("*/")
+        comment = head[head.rfind("/*", 0, last):last] if last >= 0 else ""
+        if not any(c in comment for c in cites):
+            missing.append(m.group(1))
+    assert not missing, f"declarations without a cited passage: {missing}"
