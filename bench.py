@@ -286,6 +286,7 @@ def ablation_measurement(g, gb, torch, roots, mcc, checks, level, parent, flush,
         for r in roots[:4]:
             gb.bfs_run(g.handle, int(r), level, parent, stream)
         torch.cuda.synchronize()
+        g.status()  # a failing mode stops here, before its timed searches
         evs = []
         for r in roots:
             flush.fill_(1)
@@ -374,6 +375,7 @@ def batched_measurement(args, gb, torch, dev):
     stream = torch.cuda.current_stream(dev)
     for r in roots[:8]:
         gb.bfs_run(g.handle, int(r), level, None, stream)
+    gb.bfs_graph_status(g.handle)  # a failing search stops here, before 1,024 of them are queued
     flush.fill_(1)
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
@@ -384,6 +386,7 @@ def batched_measurement(args, gb, torch, dev):
     e1.record(stream)
     torch.cuda.synchronize()
     t_plain = e0.elapsed_time(e1) * 1e-3
+    gb.bfs_graph_status(g.handle)
     g.close()
     return {"workload": f"kronecker_scale{args.batched_scale}_ef{args.edgefactor}_{len(roots)}sources",
             "batch_width": tuned["batch_width"], "batch_block": tuned["batch_block"],
@@ -565,20 +568,27 @@ def serving_measurement(args, gb, torch, dev):
         for _, g in graphs:
             g.close()
         return {"workload": workload, "error": "serving measurement stopped twice", "stalls": stalls}
-    # plain path: bfs_run one query at a time (levels to pinned host memory)
+    # plain path: bfs_run one query at a time (levels to pinned host memory).
+    # Each search's device status is read after its timed span: a search that
+    # fails (a bounded device wait that ran out) stops the plain path at once
+    # and is reported, instead of being repeated silently.
     plain_reqs = draw(2000)
     outs = {}
     for gi, (n_, g) in enumerate(graphs):
         outs[gi] = torch.empty(n_, dtype=torch.int32).pin_memory()
     stream = torch.cuda.current_stream(dev)
-    plat = []
-    t0 = time.perf_counter()
-    for gi, r in plain_reqs:
+    plat, plain_error = [], None
+    for i, (gi, r) in enumerate(plain_reqs):
         a = time.perf_counter()
         gb.bfs_run(graphs[gi][1].handle, r, outs[gi], None, stream)
         stream.synchronize()
         plat.append(time.perf_counter() - a)
-    plain_el = time.perf_counter() - t0
+        try:
+            graphs[gi][1].status()
+        except gb.BfsError as e:
+            plain_error = (f"plain bfs_run {i} (scale-{scales[gi]} graph, root {r}) failed after "
+                           f"{plat[-1]:.3f} s: {e}")
+            break
     for _, g in graphs:
         g.close()
     head = points[1]
@@ -586,13 +596,16 @@ def serving_measurement(args, gb, torch, dev):
            "requests": head["requests"], "saturated_queries_per_s": sat,
            "queries_per_s": head["queries_per_s"], "p50_ms": head["p50_ms"], "p99_ms": head["p99_ms"],
            "offered_qps": head["offered_qps"], "sweep": points,
-           "plain_queries_per_s": len(plain_reqs) / plain_el,
-           "plain_p50_ms": float(np.percentile(plat, 50) * 1e3), "plain_p99_ms": float(np.percentile(plat, 99) * 1e3),
+           "plain_queries_per_s": None if plain_error else len(plat) / sum(plat),
+           "plain_p50_ms": None if plain_error else float(np.percentile(plat, 50) * 1e3),
+           "plain_p99_ms": None if plain_error else float(np.percentile(plat, 99) * 1e3),
            "how": "bfs_submit/bfs_poll (64-lane continuous batching, uint8 levels to pinned host buffers); "
                   "latency from the library's ticket times; plain = bfs_run + sync per query, "
                   "int32 levels to pinned host memory, back to back"}
     if stalls:
         out["stalls_before_this_attempt"] = stalls
+    if plain_error:
+        out["plain_error"] = plain_error
     return out
 
 
@@ -625,6 +638,7 @@ def run_ours(args):
     mcc, bmin, checks = {}, {}, {}
     for r in roots:
         g.run(int(r), level, parent)
+        g.status()  # raises at once if a search fails (outside any timed region)
         reached = level >= 0
         dsum = int(deg_d[reached].sum().item())
         nr = int(reached.sum().item())
@@ -704,6 +718,7 @@ def run_ours(args):
             gb.bfs_run(g.handle, int(r), lvh, pah, stream)
             stream.synchronize()
             e2e_teps.append(mcc[int(r)] / (time.perf_counter() - t0))
+            g.status()  # after the timed span
         e2e = {"value": harmonic_mean(e2e_teps) / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": 4 * len(roots), "d2h_bytes_per_step": 8 * n * len(roots),
                "how": "host wall clock around bfs_run with pinned host level/parent outputs + stream sync, per root"}

@@ -124,6 +124,7 @@ class _Graph:
 lib.Graph = _Graph
 lib.bfs_run = lambda h, root, level, parent, stream: _search(_handles[h], root, level, parent)
 lib.bfs_run_batch = lambda h, roots, out: out.zero_()
+lib.bfs_graph_status = lambda h: 0
 stub_gb, _ = test_bench_host._fake_gb(stall_servers=tuple(int(x) for x in sys.argv[1:]))
 lib.Server = stub_gb.Server
 sys.modules["paper_1604_02844_gb300"] = lib

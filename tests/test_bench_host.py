@@ -89,10 +89,17 @@ class _FakeBfsError(Exception):
 
 
 class _FakeGraph:
+    fail_status = False  # every search reports a device timeout
+
     def __init__(self, ro, col):
         self.n = len(ro) - 1
         self.handle = object()
         self.closed = False
+
+    def status(self):
+        if _FakeGraph.fail_status:
+            raise _FakeBfsError(-6, "a device-side wait ran out")
+        return 0
 
     def close(self):
         self.closed = True
@@ -221,3 +228,12 @@ def test_guarded_turns_an_exception_into_an_entry():
 
     out = bench.guarded("batched", boom)
     assert out == {"error": "batched: RuntimeError: device lost"}
+
+
+def test_serving_measurement_stops_the_plain_path_at_a_failed_search(short_deadline, monkeypatch):
+    pytest.importorskip("graphgen")
+    monkeypatch.setattr(_FakeGraph, "fail_status", True)
+    gb, state = _fake_gb(stall_servers=())
+    out = bench.serving_measurement(_serving_args(), gb, _fake_torch(), None)
+    assert out["queries_per_s"] > 0  # the serving numbers are kept
+    assert out["plain_queries_per_s"] is None and "plain bfs_run 0 " in out["plain_error"]
