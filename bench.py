@@ -414,6 +414,7 @@ def guarded(name, fn):
 # deadline of one serving run: a base plus a share per query
 SERVING_WAIT_S = 120.0
 SERVING_WAIT_PER_QUERY_S = 0.002
+SERVER_CLOSE_WAIT_S = 60.0  # longest wait for bfs_server_destroy
 
 
 class ServingStuck(Exception):
@@ -549,13 +550,19 @@ def serving_measurement(args, gb, torch, dev):
             th.join(10.0)
             closer = threading.Thread(target=server.close, daemon=True)
             closer.start()
-            closer.join(30.0)
+            closer.join(SERVER_CLOSE_WAIT_S)
             _KEEP_ALIVE.append((server, graphs))
             raise ServingFailed(f"serving measurement stopped: {e}", stats) from e
-        server.close()
+        # closing joins the server's workers: bounded too
+        closer = threading.Thread(target=server.close, daemon=True)
+        closer.start()
+        closer.join(SERVER_CLOSE_WAIT_S)
+        if closer.is_alive():
+            close_errors.append(f"bfs_server_destroy did not return within {SERVER_CLOSE_WAIT_S:.1f} s")
+            _KEEP_ALIVE.append((server, graphs))
         return sat, points
 
-    stalls = []
+    stalls, close_errors = [], []
     graphs = upload()
     for _ in range(2):
         try:
@@ -606,6 +613,8 @@ def serving_measurement(args, gb, torch, dev):
         out["stalls_before_this_attempt"] = stalls
     if plain_error:
         out["plain_error"] = plain_error
+    if close_errors:
+        out["close_error"] = close_errors[0]
     return out
 
 

@@ -105,7 +105,7 @@ class _FakeGraph:
         self.closed = True
 
 
-def _fake_gb(stall_servers, fail_servers=()):
+def _fake_gb(stall_servers, fail_servers=(), hang_close=False):
     """A stand-in for the library: servers numbered from 0; those listed in
     stall_servers never complete a query, those in fail_servers report every
     query as failed."""
@@ -145,6 +145,8 @@ def _fake_gb(stall_servers, fail_servers=()):
             return {"waiting": 1, "running": 0, "phase": "waiting for work"}
 
         def close(self):
+            if hang_close:
+                _t.sleep(3.0)
             self.closed = True
 
     return types.SimpleNamespace(Graph=_FakeGraph, Server=Server, BfsError=_FakeBfsError,
@@ -182,6 +184,7 @@ def _serving_args():
 def short_deadline(monkeypatch):
     monkeypatch.setattr(bench, "SERVING_WAIT_S", 0.2)
     monkeypatch.setattr(bench, "SERVING_WAIT_PER_QUERY_S", 0.0)
+    monkeypatch.setattr(bench, "SERVER_CLOSE_WAIT_S", 0.2)
     monkeypatch.setattr(bench, "_KEEP_ALIVE", [])
 
 
@@ -237,3 +240,11 @@ def test_serving_measurement_stops_the_plain_path_at_a_failed_search(short_deadl
     out = bench.serving_measurement(_serving_args(), gb, _fake_torch(), None)
     assert out["queries_per_s"] > 0  # the serving numbers are kept
     assert out["plain_queries_per_s"] is None and "plain bfs_run 0 " in out["plain_error"]
+
+
+def test_serving_measurement_bounds_the_server_close(short_deadline):
+    pytest.importorskip("graphgen")
+    gb, state = _fake_gb(stall_servers=(), hang_close=True)
+    out = bench.serving_measurement(_serving_args(), gb, _fake_torch(), None)
+    assert out["queries_per_s"] > 0 and "did not return" in out["close_error"]
+    assert len(bench._KEEP_ALIVE) == 1
