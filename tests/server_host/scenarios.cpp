@@ -221,36 +221,50 @@ void device_oom_fail()
     CHECK(b.result_ok(again));
 }
 
-// A query that waits longer than the room limit (0.2 s in this build) for
+// Poll the monitoring counters of graph gi until pred holds (at most 10 s).
+template <class Pred>
+bool await_stats(const Bench &b, int gi, Pred pred)
+{
+    const auto t0 = std::chrono::steady_clock::now();
+    int64_t st[7];
+    while (std::chrono::steady_clock::now() - t0 < std::chrono::seconds(10)) {
+        CHECK(bfs_server_graph_stats(b.s, gi, st) == BFS_OK);
+        if (pred(st)) return true;
+        std::this_thread::sleep_for(std::chrono::milliseconds(1));
+    }
+    return false;
+}
+
+// A query that waits longer than the room limit (1.5 s in this build) for
 // its graph's workspace fails with BFS_ERR_BUSY; later queries are served.
 void room_limit()
 {
     Bench b({3000, 2000}, kOneWorkspace);
     fake::deep_root = 11;
-    fake::deep_depth = 240;  // 60 rounds of 4 iterations
+    fake::deep_depth = 240;      // 60 rounds of 4 iterations
     fake::slow_graph_n = 3000;
-    fake::slow_step_us = 8000;  // about 0.5 s in all
+    fake::slow_step_us = 40000;  // about 2.4 s in all, longer than the room limit
     Query deep;
     deep.gi = 0;
     deep.root = 11;
     CHECK(b.submit(deep) == BFS_OK);
-    std::this_thread::sleep_for(std::chrono::milliseconds(30));  // its workspace is taken
+    // the deep query holds the one workspace the budget allows
+    CHECK(await_stats(b, 0, [](const int64_t *st) { return st[1] == 1 && st[4] == 1; }));
     Query starved;
     starved.gi = 1;
     starved.root = 5;
     CHECK(b.submit(starved) == BFS_OK);
-    std::this_thread::sleep_for(std::chrono::milliseconds(50));
+    // its graph's worker waits for room, the query queued
+    CHECK(await_stats(b, 1, [](const int64_t *st) { return st[6] == 6; }));
     {
-        int64_t st[7];  // the starved graph's worker is waiting for room, its query queued
+        int64_t st[7];
         CHECK(bfs_server_graph_stats(b.s, 1, st) == BFS_OK);
-        CHECK(st[0] == 1 && st[1] == 0 && st[4] == 0 && (st[6] == 6 || st[6] == 1));
-        CHECK(bfs_server_graph_stats(b.s, 0, st) == BFS_OK);  // the busy one holds its workspace
-        CHECK(st[1] == 1 && st[4] == 1);
+        CHECK(st[0] == 1 && st[1] == 0 && st[4] == 0);
     }
     CHECK(b.wait(starved) == BFS_ERR_BUSY);
     int64_t t0 = 0, t1 = 0;
     CHECK(bfs_ticket_times(b.s, starved.ticket, &t0, &t1) == BFS_OK);
-    CHECK(t1 - t0 >= 190'000'000);
+    CHECK(t1 - t0 >= 1'450'000'000);
     CHECK(b.wait(deep) == BFS_OK);
     CHECK(b.result_ok(deep));
     Query later;

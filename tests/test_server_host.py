@@ -16,7 +16,7 @@ loop through its C ABI and check that:
 - the host backstop ends a lane that never finishes;
 - the pull-phase hold is kept.
 
-The loop's wait for room is shortened to 0.2 s in this build. A stress
+The loop's wait for room is shortened to 1.5 s in this build. A stress
 scenario mixes eight graphs, bursts of queries, steps of random length, the
 hold and a budget for three workspaces. Every scenario also runs under
 ThreadSanitizer, and under AddressSanitizer with UBSan. A last test plants mistakes in a copy of server.cu and
@@ -45,7 +45,7 @@ def _cuda_include():
 
 def _build(server_src, out, extra=()):
     inc = _cuda_include()
-    cmd = ["g++", "-std=c++17", "-O1", "-g", "-pthread", *extra, "-DGBBFS_ROOM_WAIT_NS=200000000",
+    cmd = ["g++", "-std=c++17", "-O1", "-g", "-pthread", *extra, "-DGBBFS_ROOM_WAIT_NS=1500000000",
            f"-I{CSRC}", f"-I{HOST}", f"-I{inc}",
            "-x", "c++", server_src, "-x", "none",
            os.path.join(HOST, "fake_backend.cpp"), os.path.join(HOST, "scenarios.cpp"), "-o", out]
