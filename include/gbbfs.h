@@ -125,7 +125,9 @@ int bfs_last_status(void);
  * Upload a CSR graph (Sec. 3.3.1) to the current CUDA device.
  *   row_offsets : n+1 int32 entries; host or device memory (detected)
  *   col_idx     : m int32 entries; host or device memory; may be NULL if m == 0
- *   n, m        : 1 <= n <= INT32_MAX - 1, 0 <= m <= INT32_MAX
+ *   n, m        : 1 <= n <= 2^31 - 2^24, 0 <= m <= 2^31 - 2^24 (indices are
+ *                 32-bit on the device; the margin keeps every grid-stride
+ *                 loop's last step from overflowing), else BFS_ERR_INVALID_ARG
  * The library copies both arrays into device memory it owns; the caller
  * keeps ownership of its arrays.  The copy is validated on the device:
  * row_offsets[0] == 0, non-decreasing, row_offsets[n] == m, and every

@@ -156,8 +156,12 @@ int bfs_last_status(void) { return t_status; }
 bfs_graph *bfs_graph_create(const int32_t *row_offsets, const int32_t *col_idx, int64_t n, int64_t m)
 {
     clear_error();
-    if (!row_offsets || n < 1 || n > 2147483646LL || m < 0 || m > 2147483647LL || (m > 0 && !col_idx)) {
-        set_error(BFS_ERR_INVALID_ARG, "bfs_graph_create: need row_offsets, 1 <= n < INT32_MAX, 0 <= m <= INT32_MAX, col_idx when m > 0");
+    // Vertex and edge indices are 32-bit in the kernels, whose grid-stride
+    // loops step up to about 2^18 past the last index: keep 2^24 of headroom.
+    constexpr int64_t kMaxIndex = (int64_t(1) << 31) - (int64_t(1) << 24);
+    if (!row_offsets || n < 1 || n > kMaxIndex || m < 0 || m > kMaxIndex || (m > 0 && !col_idx)) {
+        set_error(BFS_ERR_INVALID_ARG, "bfs_graph_create: need row_offsets, 1 <= n <= 2^31 - 2^24, "
+                                       "0 <= m <= 2^31 - 2^24, col_idx when m > 0");
         return nullptr;
     }
     Graph *g = new (std::nothrow) Graph();

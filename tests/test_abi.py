@@ -63,6 +63,12 @@ def test_host_side_argument_errors(lib):
     assert not lib.bfs_graph_create(ro.ctypes.data, None, 2, 2)
     assert lib.bfs_last_status() == gb.BFS_ERR_INVALID_ARG
     assert not lib.bfs_graph_create(None, col.ctypes.data, 2, 2)
+    # sizes past the 32-bit index headroom (2^31 - 2^24), also before any access
+    top = (1 << 31) - (1 << 24)
+    assert not lib.bfs_graph_create(ro.ctypes.data, col.ctypes.data, top + 1, 2)
+    assert lib.bfs_last_status() == gb.BFS_ERR_INVALID_ARG
+    assert not lib.bfs_graph_create(ro.ctypes.data, col.ctypes.data, 2, top + 1)
+    assert lib.bfs_last_status() == gb.BFS_ERR_INVALID_ARG
     assert lib.bfs_run(None, 0, None, None, None) == gb.BFS_ERR_INVALID_ARG
     assert lib.bfs_graph_status(None) == gb.BFS_ERR_INVALID_ARG
     assert lib.bfs_run_batch(None, None, 0, None) == gb.BFS_ERR_INVALID_ARG
