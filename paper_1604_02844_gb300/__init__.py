@@ -375,9 +375,14 @@ class Server:
     def poll(self, ticket: int) -> bool:
         return bfs_poll(self.handle, ticket) == BFS_OK
 
-    def wait(self, ticket: int, sleep_s: float = 0.0) -> None:
+    def wait(self, ticket: int, sleep_s: float = 0.0, timeout_s: float | None = None) -> None:
+        """Poll until the query completes (raises BfsError if it failed, and
+        TimeoutError if timeout_s passes first)."""
         import time
+        deadline = None if timeout_s is None else time.monotonic() + timeout_s
         while not self.poll(ticket):
+            if deadline is not None and time.monotonic() > deadline:
+                raise TimeoutError(f"query {ticket} still running after {timeout_s} s")
             if sleep_s:
                 time.sleep(sleep_s)
 

@@ -99,3 +99,29 @@ def test_every_declaration_states_its_provenance():
         if not any(c in comment for c in cites):
             missing.append(m.group(1))
     assert not missing, f"declarations without a cited passage: {missing}"
+
+
+def test_server_wait_timeout_and_failure(monkeypatch):
+    """Server.wait on a stand-in poll: returns when done, raises TimeoutError
+    past its limit, and passes a failed query's error on."""
+    s = gb.Server.__new__(gb.Server)  # no native server: poll is replaced below
+    s.handle, s._keep = None, {}
+    calls = {"n": 0}
+
+    def done_after_three(handle, ticket):
+        calls["n"] += 1
+        return gb.BFS_OK if calls["n"] >= 3 else gb.BFS_NOT_READY
+
+    monkeypatch.setattr(gb, "bfs_poll", done_after_three)
+    s.wait(1)
+    assert calls["n"] == 3
+    monkeypatch.setattr(gb, "bfs_poll", lambda h, t: gb.BFS_NOT_READY)
+    with pytest.raises(TimeoutError):
+        s.wait(2, sleep_s=0.001, timeout_s=0.05)
+
+    def failed(handle, ticket):
+        raise gb.BfsError(gb.BFS_ERR_TIMEOUT, "a device-side wait ran out")
+
+    monkeypatch.setattr(gb, "bfs_poll", failed)
+    with pytest.raises(gb.BfsError):
+        s.wait(3)
