@@ -361,9 +361,12 @@ class Server:
     def __init__(self, hbm_budget_bytes: int = 0):
         self.handle = bfs_server_create(hbm_budget_bytes)
         self._keep = {}
+        self._graphs = []  # registered graphs outlive the server (it frees their batch workspaces)
 
     def add_graph(self, graph: "Graph") -> int:
-        return bfs_server_add_graph(self.handle, graph.handle)
+        gid = bfs_server_add_graph(self.handle, graph.handle)
+        self._graphs.append(graph)
+        return gid
 
     def submit(self, graph_id: int, root: int, level_out: np.ndarray) -> int:
         if not (isinstance(level_out, np.ndarray) and level_out.dtype == np.uint8 and level_out.flags["C_CONTIGUOUS"]):
@@ -400,6 +403,12 @@ class Server:
         if self.handle:
             bfs_server_destroy(self.handle)
             self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
     def __enter__(self):
         return self
