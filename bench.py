@@ -411,10 +411,33 @@ def guarded(name, fn):
         return {"error": f"{name}: {type(e).__name__}: {e}"}
 
 
+def bounded(name, fn, limit_s, setup=None):
+    """guarded(), on a thread of its own with a deadline: a measurement that
+    does not finish in limit_s is reported and left running (its objects
+    stay referenced), and the bench goes on.  setup() runs first on that
+    thread (e.g. to select its CUDA device)."""
+    import threading
+    box = {}
+
+    def target():
+        if setup is not None:
+            setup()
+        box["v"] = guarded(name, fn)
+
+    th = threading.Thread(target=target, daemon=True)
+    th.start()
+    th.join(limit_s)
+    if th.is_alive():
+        _KEEP_ALIVE.append(th)
+        return {"error": f"{name}: did not finish within {limit_s:.0f} s"}
+    return box["v"]
+
+
 # deadline of one serving run: a base plus a share per query
 SERVING_WAIT_S = 120.0
 SERVING_WAIT_PER_QUERY_S = 0.002
 SERVER_CLOSE_WAIT_S = 60.0  # longest wait for bfs_server_destroy
+SERVING_TOTAL_S = 1500.0    # the whole serving measurement, retry included
 
 
 class ServingStuck(Exception):
@@ -596,8 +619,12 @@ def serving_measurement(args, gb, torch, dev):
             plain_error = (f"plain bfs_run {i} (scale-{scales[gi]} graph, root {r}) failed after "
                            f"{plat[-1]:.3f} s: {e}")
             break
-    for _, g in graphs:
-        g.close()
+    closer = threading.Thread(target=lambda: [g.close() for _, g in graphs], daemon=True)
+    closer.start()
+    closer.join(SERVER_CLOSE_WAIT_S)
+    if closer.is_alive():
+        close_errors.append(f"bfs_graph_destroy did not return within {SERVER_CLOSE_WAIT_S:.1f} s")
+        _KEEP_ALIVE.append(graphs)
     head = points[1]
     out = {"workload": workload,
            "requests": head["requests"], "saturated_queries_per_s": sat,
@@ -751,7 +778,8 @@ def run_ours(args):
     serving = None
     if not args.no_serving and rank == 0:
         with ClockSampler(uuid) as sclocks:
-            serving = guarded("serving", lambda: serving_measurement(args, gb, torch, dev))
+            serving = bounded("serving", lambda: serving_measurement(args, gb, torch, dev), SERVING_TOTAL_S,
+                              setup=lambda: torch.cuda.set_device(dev))
         serving["clocks"] = sclocks.summary()
     if rank == 0:
         cpu = None

@@ -248,3 +248,14 @@ def test_serving_measurement_bounds_the_server_close(short_deadline):
     out = bench.serving_measurement(_serving_args(), gb, _fake_torch(), None)
     assert out["queries_per_s"] > 0 and "did not return" in out["close_error"]
     assert len(bench._KEEP_ALIVE) == 1
+
+
+def test_bounded_reports_a_measurement_that_does_not_finish(monkeypatch):
+    import time as _t
+    monkeypatch.setattr(bench, "_KEEP_ALIVE", [])
+    assert bench.bounded("quick", lambda: {"ok": 1}, 5.0) == {"ok": 1}
+    seen = []
+    out = bench.bounded("slow", lambda: _t.sleep(2.0), 0.1, setup=lambda: seen.append("setup"))
+    assert out == {"error": "slow: did not finish within 0 s"} and seen == ["setup"]
+    assert len(bench._KEEP_ALIVE) == 1
+    assert bench.bounded("boom", lambda: 1 / 0, 5.0)["error"].startswith("boom: ZeroDivisionError")
