@@ -23,7 +23,7 @@ def csr_from_edges(n, edges, directed):
 
 
 def load_golden(path):
-    spec = {"edges": [], "levels": None, "bitmap": None}
+    spec = {"edges": [], "levels": None, "bitmap": None, "profile": None}
     section = None
     with open(path) as f:
         for raw in f:
@@ -34,7 +34,7 @@ def load_golden(path):
             if tok[0] in ("n", "directed", "root"):
                 spec[tok[0]] = int(tok[1])
                 section = None
-            elif tok[0] in ("edges", "levels", "bitmap"):
+            elif tok[0] in ("edges", "levels", "bitmap", "profile"):
                 section = tok[0]
             elif section == "edges":
                 spec["edges"].append((int(tok[0]), int(tok[1])))
@@ -42,10 +42,15 @@ def load_golden(path):
                 spec["levels"] = (spec["levels"] or []) + [int(t) for t in tok]
             elif section == "bitmap":
                 spec["bitmap"] = (spec["bitmap"] or []) + [int(t, 16) for t in tok]
+            elif section == "profile":
+                assert len(tok) == 3, path
+                spec["profile"] = (spec["profile"] or []) + [[int(t) for t in tok]]
     assert len(spec["levels"]) == spec["n"], path
     ro, col = csr_from_edges(spec["n"], spec["edges"], spec["directed"])
     spec["row_offsets"], spec["col_idx"] = ro, col
     spec["levels"] = np.array(spec["levels"], np.int32)
+    if spec["profile"] is not None:
+        spec["profile"] = np.array(spec["profile"], np.int64)
     spec["name"] = os.path.basename(path)
     return spec
 

@@ -10,8 +10,11 @@ The oracle is checked against things other than itself:
     seeded Kronecker and Erdos-Renyi graphs;
   * the validator (Sec. 5.3 soft check) accepts independent correct trees and
     rejects each kind of planted mistake;
+  * hand-worked per-layer profiles (Table 1 columns: vertices, edges
+    scanned, traversed) of five fixtures;
   * mutants of oracle.c (dropped term, wrong index, stack instead of queue,
-    wrong root level, wrong parent, lenient validator) each fail some pin.
+    wrong root level, wrong parent, lenient validator, edges counted in the
+    wrong layer) each fail some pin.
 """
 import os
 import random
@@ -95,6 +98,10 @@ def pin_failures(orc):
             bad.append("golden:" + c["name"])
         elif not independent_parent_check(c["row_offsets"], c["col_idx"], c["root"], lv, pa):
             bad.append("golden-parent:" + c["name"])
+        if c["profile"] is not None:  # hand-worked Table 1 columns, from the fixture's own levels
+            v, e, t = orc.layer_profile(c["row_offsets"], c["levels"])
+            if not np.array_equal(np.stack([v, e, t], axis=1), c["profile"]):
+                bad.append("golden-profile:" + c["name"])
     for name, ro, col, expect, r in closed_form_cases():
         lv, pa = orc.bfs(ro, col, r)
         if not np.array_equal(lv, expect):
@@ -283,6 +290,15 @@ def test_batch_depth_overflow():
     assert out[0].max() == 150
 
 
+def test_golden_layer_profiles():
+    """Hand-worked Table 1 columns (tests/golden, 'profile' sections)."""
+    cases = [c for c in golden_cases() if c["profile"] is not None]
+    assert len(cases) >= 5
+    for c in cases:
+        v, e, t = oracle.layer_profile(c["row_offsets"], c["levels"])
+        np.testing.assert_array_equal(np.stack([v, e, t], axis=1), c["profile"], err_msg=c["name"])
+
+
 def test_layer_profile_table1_invariants():
     ro, col = graphgen.kronecker(16, 16, 1)
     for r in graphgen.pick_roots(ro, 4, 2):
@@ -325,6 +341,15 @@ MUTANTS = [
     ("validator skips edge check", "if (parent[v] == u) found[v] = 1;", "found[v] = 1;"),
     ("validator drops rule 5", "if ((level[v] >= 0) != (ref_level[v] >= 0))", "if (0)"),
     ("validator drops root check", "if (parent[root] != root || level[root] != 0)", "if (0)"),
+    ("profile edges counted at d+1", "edges[d] += row_offsets[v + 1] - row_offsets[v];",
+     "if (d + 1 < max_layers) edges[d + 1] += row_offsets[v + 1] - row_offsets[v];"),
+    ("profile edges only for d > 0", "edges[d] += row_offsets[v + 1] - row_offsets[v];",
+     "if (d > 0) edges[d] += row_offsets[v + 1] - row_offsets[v];"),
+    ("profile edges of unreached vertices", "if (d < 0) continue;\n        if (d >= max_layers)",
+     "if (d < 0) { edges[0] += row_offsets[v + 1] - row_offsets[v]; continue; }\n        if (d >= max_layers)"),
+    ("profile edges counted once per vertex", "edges[d] += row_offsets[v + 1] - row_offsets[v];",
+     "edges[d] += 1;"),
+    ("profile traversed at d", "if (d > 0) traversed[d - 1] += 1;", "traversed[d] += 1;"),
 ]
 
 
