@@ -14,6 +14,7 @@ import pytest
 
 import graphgen
 import oracle
+from parity_pool import big_graph, check_roots
 from fixtures import (binary_tree, csr_from_edges, cycle_graph, golden_cases, grid_graph,
                       hypercube_graph, path_graph, star_graph)
 
@@ -255,18 +256,23 @@ def test_option_errors_and_timeout_recovery():
         check_root(g, ro, col, r)
 
 
-@pytest.mark.parametrize("scale", [20, 22])
-def test_kronecker_full_size_sampled_roots(scale):
-    ro, col = graphgen.kronecker(scale, 16, 1)
-    roots = graphgen.pick_roots(ro, 64, 1)
-    with gb.Graph(ro, col, mode=HYB) as g:
-        for r in roots[[0, 17, 63]]:
-            check_root(g, ro, col, r)
+def _gpu_run(g):
+    def run(r):
+        level, parent = g.run(int(r))
+        torch.cuda.synchronize()
+        assert g.status() == gb.BFS_OK, gb.last_error()
+        return level.cpu().numpy(), parent.cpu().numpy()
+    return run
 
 
-@pytest.mark.parametrize("kind", ["kronecker", "erdos_renyi"])
-def test_scale24_sampled_roots(kind):
-    ro, col = getattr(graphgen, kind)(24, 16, 1)
-    roots = graphgen.pick_roots(ro, 64, 1)
+@pytest.mark.parametrize("kind,scale,nroots", [("kronecker", 20, 64), ("kronecker", 22, 64),
+                                                 ("kronecker", 24, 64), ("erdos_renyi", 24, 64)])
+def test_full_size_every_root(kind, scale, nroots):
+    """Mode 3 (direction-optimising): the benchmark's graphs and roots (64 seeded roots of degree
+    >= 1, paper Sec. 5.3) in the benchmark's launch configuration; every
+    root's levels equal the oracle's and its parents pass the validation."""
+    ro, col = big_graph(kind, scale)
+    roots = graphgen.pick_roots(ro, 64, 1)[:nroots]
     with gb.Graph(ro, col, mode=HYB) as g:
-        check_root(g, ro, col, roots[0])
+        fails = check_roots(_gpu_run(g), ro, col, roots)
+    assert fails == [], fails[:5]
