@@ -1,6 +1,6 @@
 """Benchmark: single-source top-down BFS GTEPS on a seeded Kronecker graph.
 
-Workload (default): Kronecker (R-MAT A/B/C/D = .57/.19/.19/.05) scale 22,
+Workload (default): Kronecker (R-MAT A/B/C/D = .57/.19/.19/.05) scale 24,
 edgefactor 16, permuted, symmetrised, self-loops and repeats removed; 64
 seeded roots of degree >= 1 (paper Sec. 5.2-5.3: 64 BFS runs from distinct
 roots, TEPS per run, harmonic mean).  One step = one BFS from each of the 64
@@ -44,13 +44,18 @@ def parse_args(argv=None):
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--scale", type=int, default=22)
+    ap.add_argument("--scale", type=int, default=24)
     ap.add_argument("--graph", choices=["kronecker", "erdos_renyi"], default="kronecker",
                     help="erdos_renyi: the low-skew contrast graph with the same n and tuple count")
     ap.add_argument("--edgefactor", type=int, default=16)
     ap.add_argument("--roots", type=int, default=64)
     ap.add_argument("--seed", type=int, default=1)
-    ap.add_argument("--cpu-sample-roots", type=int, default=32)
+    ap.add_argument("--cpu-sample-roots", type=int, default=None,
+                    help="roots of the CPU-baseline sample (default: about 20 s of oracle work)")
+    ap.add_argument("--other-workloads", default="erdos_renyi:24,kronecker:22,kronecker:16",
+                    help="graph:scale list measured beside the headline (64 roots each), or 'none'")
+    ap.add_argument("--no-layer-profile", action="store_true",
+                    help="skip the per-layer breakdown of the headline searches")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--option", action="append", default=[],
@@ -65,8 +70,6 @@ def parse_args(argv=None):
                     help="skip the serving-loop measurement")
     ap.add_argument("--serving-requests", type=int, default=100000)
     ap.add_argument("--serving-scales", default="12,14,15,17,18,20,21,23")
-    ap.add_argument("--profile-layers", action="store_true",
-                    help="print the per-layer counters and device times of one search to stderr")
     return ap.parse_args(argv)
 
 
@@ -208,6 +211,19 @@ def build_workload(args, rank):
     return ro, col, roots
 
 
+def oracle_seconds_per_root(scale, edgefactor):
+    """Rough single-core oracle time of one search (0.6 s at scale 22, ef 16
+    on the GPU host), used only to size the bounded CPU samples."""
+    return 0.6 * 2.0 ** (scale - 22) * edgefactor / 16.0
+
+
+def cpu_sample_size(args, target_s=20.0):
+    if args.cpu_sample_roots is not None:
+        return args.cpu_sample_roots
+    est = oracle_seconds_per_root(args.scale, args.edgefactor)
+    return int(max(2, min(32, round(target_s / est))))
+
+
 def cpu_baseline(ro, col, roots, k):
     """The oracle (single-threaded C queue BFS) on the host cores, on a
     bounded sample of the roots."""
@@ -242,11 +258,12 @@ def run_reference(args):
     _, label = connected_components(sp.csr_matrix((np.ones(len(col), np.int8), col, ro), shape=(n, n)),
                                     directed=False)
     comp_edges = np.bincount(label, weights=deg) / 2.0
-    per_step = max(1, min(16, args.cpu_sample_roots, len(roots)))  # timed steps: a bounded sample
+    # timed steps: a bounded sample of about 6 s of oracle work each
+    per_step = max(1, min(16, cpu_sample_size(args, 6.0), len(roots)))
     teps, step_ms = [], []
     pos = 0
     for step in range(args.warmup + args.steps):
-        k = 2 if step < args.warmup else per_step  # warm-up steps: a token sample
+        k = 1 if step < args.warmup else per_step  # warm-up steps: a token sample
         sample = [int(roots[(pos + i) % len(roots)]) for i in range(k)]
         pos += k
         secs = oracle.time_bfs(ro, col, sample)
@@ -310,6 +327,141 @@ def ablation_measurement(g, gb, torch, roots, mcc, checks, level, parent, flush,
             "levels_match_atomic_path": bool(same)}
     g.set_option("mode", base_mode)
     return out
+
+
+def bookkeeping(g, gb, roots, level, parent, deg_d, n):
+    """Per-root edge counts for TEPS (m_cc), algorithmic bytes and a level
+    checksum, outside any timed region; a failing search raises at once."""
+    mcc, bmin, checks = {}, {}, {}
+    for r in roots:
+        g.run(int(r), level, parent)
+        g.status()
+        reached = level >= 0
+        dsum = int(deg_d[reached].sum().item())
+        nr = int(reached.sum().item())
+        mcc[int(r)] = dsum / 2.0
+        bmin[int(r)] = algorithmic_bytes(dsum, nr, n)
+        checks[int(r)] = (nr, int(level[reached].sum().item()))
+    return mcc, bmin, checks
+
+
+def timed_pass(gb, torch, g, roots, level, parent, flush, stream):
+    """One search per root, CUDA events on the search's stream around each,
+    the L2 flushed before each (outside the events).  Returns (root, e0, e1)."""
+    evs = []
+    for r in roots:
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        gb.bfs_run(g.handle, int(r), level, parent, stream)
+        e1.record(stream)
+        evs.append((int(r), e0, e1))
+    return evs
+
+
+def layer_profile(g, torch, roots, level, parent, n, grid_warps):
+    """Per-layer breakdown of the searches from every root (layer counters
+    and the device time at the end of each layer, BFS_OPT_LAYER_STATS on;
+    outside the timed region, the counters add a few atomics per warp and
+    layer).  Per layer index d, summed over the roots: frontier vertices,
+    adjacency entries scanned, new vertices, time, algorithmic bytes
+    (4 B per entry + 16 B per frontier vertex + 8 B level/parent per new
+    vertex; layer 0 also carries the initialisation, 8.25 B per vertex) and
+    their rate.  A layer is light when its entries fill fewer work items
+    (384 entries each) than the grid has warps."""
+    g.set_option("layer_stats", 1)
+    per = {}
+    light_t = total_t = 0.0
+    floor = []
+    try:
+        for r in roots:
+            g.run(int(r), level, parent)
+            torch.cuda.synchronize()
+            v, e, t = g.layer_stats()
+            ts = g.layer_times()
+            prev = 0
+            for d in range(len(v)):
+                dt = (int(ts[d]) - prev) * 1e-9
+                prev = int(ts[d])
+                b = 4.0 * int(e[d]) + 16.0 * int(v[d]) + 8.0 * int(t[d]) + (8.25 * n if d == 0 else 0.0)
+                a = per.setdefault(d, {"d": d, "roots": 0, "vertices": 0, "edges": 0, "new": 0,
+                                       "time_s": 0.0, "bytes": 0.0})
+                a["roots"] += 1
+                a["vertices"] += int(v[d])
+                a["edges"] += int(e[d])
+                a["new"] += int(t[d])
+                a["time_s"] += dt
+                a["bytes"] += b
+                total_t += dt
+                if int(e[d]) < 384 * grid_warps:
+                    light_t += dt
+                if int(v[d]) <= 2 and int(e[d]) <= 64 and d > 0:
+                    floor.append(dt)
+    finally:
+        g.set_option("layer_stats", 0)
+    layers = []
+    for d in sorted(per):
+        a = per[d]
+        k = len(roots)
+        layers.append({"d": d, "roots": a["roots"], "vertices_mean": a["vertices"] / k,
+                       "edges_mean": a["edges"] / k, "new_mean": a["new"] / k,
+                       "time_us_mean": 1e6 * a["time_s"] / k,
+                       "time_share": a["time_s"] / total_t if total_t else None,
+                       "edges_share": None, "bytes_mean": a["bytes"] / k,
+                       "gbs": a["bytes"] / a["time_s"] / 1e9 if a["time_s"] > 0 else None})
+    etot = sum(x["edges_mean"] for x in layers) or 1.0
+    for x in layers:
+        x["edges_share"] = x["edges_mean"] / etot
+    fl = statistics.median(floor) if floor else None
+    return {"roots": len(roots), "grid_warps": grid_warps, "layers": layers,
+            "search_us_mean": 1e6 * total_t / len(roots),
+            "light_layer_time_share": light_t / total_t if total_t else None,
+            "tiny_layer_us_median": 1e6 * fl if fl else None,
+            "tiny_layer_time_share_est": (fl * sum(x["roots"] for x in layers) / total_t) if fl and total_t else None,
+            "how": "BFS_OPT_LAYER_STATS counters and per-layer globaltimer stamps of one search per root; "
+                   "light = fewer 384-entry items than grid warps; tiny = <= 2 frontier vertices and <= 64 "
+                   "entries, whose time is the per-layer floor (grid barrier + one item chain); "
+                   "tiny_layer_time_share_est = that floor times the layers run / the search time"}
+
+
+def other_workload(args, gb, torch, dev, graph, scale, peak, flush, stream, reps=2):
+    """The headline measurement on another graph (64 seeded roots, one
+    warm-up pass, `reps` timed passes): harmonic-mean GTEPS, TEPS spread,
+    the HBM fraction and the mean launch time."""
+    import graphgen
+    ro, col = getattr(graphgen, graph)(scale, args.edgefactor, args.seed)
+    roots = graphgen.pick_roots(ro, args.roots, args.seed)
+    n = len(ro) - 1
+    g = gb.Graph(ro, col)
+    try:
+        for kv in args.option:
+            k, v = kv.split("=")
+            g.set_option(k, int(v))
+        level = torch.empty(n, dtype=torch.int32, device=dev)
+        parent = torch.empty(n, dtype=torch.int32, device=dev)
+        deg_d = torch.from_numpy(np.diff(ro).astype(np.int64)).to(dev)
+        mcc, bmin, _ = bookkeeping(g, gb, roots, level, parent, deg_d, n)
+        timed_pass(gb, torch, g, roots, level, parent, flush, stream)
+        torch.cuda.synchronize()
+        runs = []
+        for _ in range(reps):
+            evs = timed_pass(gb, torch, g, roots, level, parent, flush, stream)
+            torch.cuda.synchronize()
+            runs += [(r, e0.elapsed_time(e1) * 1e-3) for r, e0, e1 in evs]
+        g.status()
+    finally:
+        g.close()
+    teps = [mcc[r] / t for r, t in runs]
+    mean_t = statistics.mean(t for _, t in runs)
+    mean_b = statistics.mean(bmin[r] for r, _ in runs)
+    return {"workload": workload_name(scale, args.edgefactor, args.roots, graph), "n": n, "m_directed": len(col),
+            "hm_gteps": harmonic_mean(teps) / 1e9,
+            "teps_stats": {"min": min(teps) / 1e9, "median": statistics.median(teps) / 1e9,
+                           "max": max(teps) / 1e9, "runs": len(teps)},
+            "roofline": {"bound": "hbm", "achieved": mean_b / mean_t / 1e9, "peak": peak, "unit": "GB/s",
+                         "frac": mean_b / mean_t / 1e9 / peak, "algorithmic_bytes_per_launch": mean_b},
+            "mean_launch_us": 1e6 * mean_t}
 
 
 UNEVEN_MIX_SCALES = (12, 14, 16, 18, 20, 22)
@@ -581,15 +733,18 @@ def serving_measurement(args, gb, torch, dev):
         closer.start()
         closer.join(SERVER_CLOSE_WAIT_S)
         if closer.is_alive():
+            # a worker may still run on these graphs: they are neither
+            # searched nor freed from here on
             close_errors.append(f"bfs_server_destroy did not return within {SERVER_CLOSE_WAIT_S:.1f} s")
             _KEEP_ALIVE.append((server, graphs))
-        return sat, points
+            return sat, points, False
+        return sat, points, True
 
     stalls, close_errors = [], []
     graphs = upload()
     for _ in range(2):
         try:
-            sat, points = attempt(graphs)
+            sat, points, closed = attempt(graphs)
             break
         except ServingFailed as f:
             stalls.append({"error": str(f), "graphs": f.graphs})
@@ -602,12 +757,16 @@ def serving_measurement(args, gb, torch, dev):
     # Each search's device status is read after its timed span: a search that
     # fails (a bounded device wait that ran out) stops the plain path at once
     # and is reported, instead of being repeated silently.
-    plain_reqs = draw(2000)
+    plain_reqs = draw(2000) if closed else []
+    if not closed:
+        plain_error = "plain path skipped: the server did not close, its graphs stay allocated"
     outs = {}
     for gi, (n_, g) in enumerate(graphs):
         outs[gi] = torch.empty(n_, dtype=torch.int32).pin_memory()
     stream = torch.cuda.current_stream(dev)
-    plat, plain_error = [], None
+    plat = []
+    if closed:
+        plain_error = None
     for i, (gi, r) in enumerate(plain_reqs):
         a = time.perf_counter()
         gb.bfs_run(graphs[gi][1].handle, r, outs[gi], None, stream)
@@ -619,7 +778,7 @@ def serving_measurement(args, gb, torch, dev):
             plain_error = (f"plain bfs_run {i} (scale-{scales[gi]} graph, root {r}) failed after "
                            f"{plat[-1]:.3f} s: {e}")
             break
-    closer = threading.Thread(target=lambda: [g.close() for _, g in graphs], daemon=True)
+    closer = threading.Thread(target=lambda: [g.close() for _, g in graphs] if closed else None, daemon=True)
     closer.start()
     closer.join(SERVER_CLOSE_WAIT_S)
     if closer.is_alive():
@@ -671,42 +830,12 @@ def run_ours(args):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
 
     # per-root edge counts (bookkeeping for TEPS, outside any timed region)
-    mcc, bmin, checks = {}, {}, {}
-    for r in roots:
-        g.run(int(r), level, parent)
-        g.status()  # raises at once if a search fails (outside any timed region)
-        reached = level >= 0
-        dsum = int(deg_d[reached].sum().item())
-        nr = int(reached.sum().item())
-        mcc[int(r)] = dsum / 2.0
-        bmin[int(r)] = algorithmic_bytes(dsum, nr, n)
-        checks[int(r)] = (nr, int(level[reached].sum().item()))
+    mcc, bmin, checks = bookkeeping(g, gb, roots, level, parent, deg_d, n)
     torch.cuda.synchronize()
     assert g.status() == gb.BFS_OK, gb.last_error()
 
-    if args.profile_layers and rank == 0:
-        g.set_option("layer_stats", 1)
-        for r in roots[:2]:
-            g.run(int(r), level, parent)
-            torch.cuda.synchronize()
-            v, e, t = g.layer_stats()
-            ts = g.layer_times()
-            print(json.dumps({"root": int(r), "layers": [
-                {"d": d, "vertices": int(v[d]), "edges": int(e[d]), "new": int(t[d]),
-                 "t_end_us": round(ts[d] / 1e3, 2)} for d in range(len(v))]}), file=sys.stderr)
-        g.set_option("layer_stats", 0)
-
     def one_step(record):
-        evs = []
-        for r in roots:
-            flush.fill_(1)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            gb.bfs_run(g.handle, int(r), level, parent, stream)
-            e1.record(stream)
-            evs.append((int(r), e0, e1))
-        return evs
+        return timed_pass(gb, torch, g, roots, level, parent, flush, stream)
 
     for _ in range(args.warmup):
         one_step(False)
@@ -763,6 +892,22 @@ def run_ours(args):
     value, step_ms = combine_replicas(dist, world, hm, total_dev, args.steps)
 
     options = {k: g.get_option(k) for k in gb.OPTION_NAMES}
+    layers = None
+    if not args.no_layer_profile and rank == 0:
+        def grid_warps():
+            try:
+                return torch.cuda.get_device_properties(dev).multi_processor_count * (options.get("block", 512) // 32)
+            except Exception:  # noqa: BLE001
+                return 152 * 16
+        layers = guarded("layer_profile", lambda: layer_profile(g, torch, roots, level, parent, n, grid_warps()))
+    others = None
+    if args.other_workloads != "none" and rank == 0:
+        others = {}
+        for item in args.other_workloads.split(","):
+            gname, sc = item.split(":")
+            key = workload_name(int(sc), args.edgefactor, args.roots, gname)
+            others[key] = guarded(key, lambda: other_workload(args, gb, torch, dev, gname, int(sc), peak,
+                                                               flush, stream))
     ablation = None
     if not args.no_ablation and rank == 0:
         def ablate():
@@ -784,7 +929,7 @@ def run_ours(args):
     if rank == 0:
         cpu = None
         if not args.no_cpu_baseline:
-            cpu = guarded("cpu_baseline", lambda: cpu_baseline(ro, col, roots, args.cpu_sample_roots))
+            cpu = guarded("cpu_baseline", lambda: cpu_baseline(ro, col, roots, cpu_sample_size(args)))
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
@@ -804,6 +949,8 @@ def run_ours(args):
                          "mean_launch_s": mean_t},
             "cpu_baseline": cpu,
             "e2e": e2e,
+            "layer_profile": layers,
+            "other_workloads": others,
             "ablation": ablation,
             "batched": batched,
             "serving": serving,

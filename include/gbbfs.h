@@ -143,7 +143,9 @@ bfs_graph *bfs_graph_create(const int32_t *row_offsets, const int32_t *col_idx,
 
 /* Free the graph of bfs_graph_create (the CSR of Sec. 3.3.1) and its
  * workspaces, after waiting for its last run.  NULL is accepted.  Returns
- * BFS_OK or BFS_ERR_CUDA. */
+ * BFS_OK or BFS_ERR_CUDA; BFS_ERR_BUSY (nothing freed) while the graph is
+ * registered with a server that has not been destroyed, whose worker may
+ * still search it. */
 int bfs_graph_destroy(bfs_graph *g);
 
 /* n and m of the graph as given to bfs_graph_create (Sec. 3.3.1: the
@@ -181,7 +183,7 @@ int bfs_run(bfs_graph *g, int32_t root, int32_t *level_out, int32_t *parent_out,
 
 /*
  * Single-source search that allocates nothing (not in the paper: a
- * deployment variant of bfs_run, whose search is the top-down BFS of Alg. 2).  For callers that cannot
+ * deployment variant of bfs_run).  For callers that cannot
  * allocate GPU memory at the moment they search -- a process whose device
  * memory is owned by another allocator or fixed budget, a latency-critical
  * path that must not block in cudaMalloc/cudaFree, or code running where
@@ -202,6 +204,10 @@ int bfs_run(bfs_graph *g, int32_t root, int32_t *level_out, int32_t *parent_out,
  * the array on that device; make it before any stream capture.  Every call
  * shares the one array: calls from several host threads are serialised, and
  * searches that overlap on the GPU through other means would race on it.
+ * The set-up is kept for the life of the process: after cudaDeviceReset on
+ * a device, this entry point must not be called on that device again until
+ * the library is reloaded (its cached address would belong to the destroyed
+ * context).
  */
 #define BFS_NOALLOC_MAX_VERTICES 131072
 #define BFS_NOALLOC_MAX_EDGES 4194304

@@ -252,6 +252,7 @@ int bfs_graph_destroy(bfs_graph *gh)
 {
     if (!gh) return BFS_OK;
     Graph *g = reinterpret_cast<Graph *>(gh);
+    if (const int busy = graph_release_check(g)) return busy;
     cudaError_t e = cudaSuccess;
     if (g->ran) e = cudaEventSynchronize(g->ws_event);
     free_graph(g);

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <mutex>
 #include <string>
 
@@ -48,8 +49,6 @@ struct Ctrl {
     unsigned status;                 // ST_* bits
     unsigned layers;                 // layers of the last search
 };
-using TdCtrl = Ctrl;
-using UnitCtrl = Ctrl;
 
 enum { MODE_WARP = 0, MODE_BINNED = 1, MODE_RESTORE = 2, MODE_HYBRID = 3 };
 
@@ -114,7 +113,18 @@ struct Graph {
 
     Options opt;
     std::mutex mu;
+    std::atomic<int> servers{0};  // live servers this graph is registered with
 };
+
+// A graph registered with a live server is still in use by the server's
+// worker thread: bfs_graph_destroy refuses it until the server is destroyed.
+inline int graph_release_check(const Graph *g)
+{
+    if (g->servers.load() > 0)
+        return set_error(BFS_ERR_BUSY, "bfs_graph_destroy: the graph is registered with a live server; "
+                                       "destroy the server first");
+    return BFS_OK;
+}
 
 // implemented in topdown.cu (degree-binned mode; its queues are allocated
 // on first use by graph.cu)

@@ -17,7 +17,10 @@
 // array is sized for them, about 7 MB, and every GPU that loads the library
 // holds it until the process exits).  The first call on a device sets the
 // array up (its device address, the identity maps); make that first call
-// before any stream capture.  All calls share the one array, which keeps
+// before any stream capture.  The set-up is cached for the life of the
+// process, so cudaDeviceReset on a device leaves a stale address behind:
+// after a reset this entry point must not be called on that device until
+// the library is reloaded.  All calls share the one array, which keeps
 // the previous call's contents: the control block is returned to zero by
 // the kernel itself at the end of every search and the bitmap and frontier
 // are rewritten by each search, but two calls that overlap on the GPU (on

@@ -411,6 +411,7 @@ int bfs_server_destroy(bfs_server *sh)
             ms_free(gs->g);
             cudaFree(gs->d_stage);
         }
+        gs->g->servers.fetch_sub(1);  // the graph may be destroyed again
     }
     delete s;
     return BFS_OK;
@@ -432,6 +433,7 @@ int bfs_server_add_graph(bfs_server *sh, bfs_graph *gh)
     }
     auto gs = std::make_unique<GraphState>();
     gs->g = g;
+    g->servers.fetch_add(1);  // bfs_graph_destroy refuses it until this server is destroyed
     GraphState *raw = gs.get();
     s->graphs.push_back(std::move(gs));
     raw->worker = std::thread([s, raw] { s->run(*raw); });

@@ -51,7 +51,7 @@ struct TdParams {
     uint32_t *bitmap;
     int32_t *qu[2], *qb[2], *ql[2];  // small-item queue [buffer]
     int32_t *bu[2], *bb[2], *bl[2];  // large-item queue [buffer]
-    TdCtrl *ctrl;
+    Ctrl *ctrl;
     int64_t *stats;  // [kMaxStatLayers][4] or null
     int32_t n;
     int32_t root;
@@ -96,7 +96,7 @@ __device__ __forceinline__ unsigned lanemask_lt()
 
 // Bounded grid barrier (all CTAs are co-resident: cooperative launch).
 // Returns false if this or another CTA gave up waiting.
-__device__ bool grid_sync(TdCtrl *c, unsigned nblocks, uint64_t timeout_ns, int *s_ok)
+__device__ bool grid_sync(Ctrl *c, unsigned nblocks, uint64_t timeout_ns, int *s_ok)
 {
     __threadfence();
     __syncthreads();
@@ -271,7 +271,7 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) td_kernel(TdParams p)
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned G = gridDim.x;
-    TdCtrl *c = p.ctrl;
+    Ctrl *c = p.ctrl;
     const OutBuf ob{s_ou, s_ob, s_ol, &s_ocnt, &s_gbase};
     const uint64_t t_start = globaltimer();
 

@@ -88,6 +88,7 @@ _handles = {}
 
 def _search(g, root, level, parent):
     lv, pa = oracle.bfs(g.ro, g.col, int(root))
+    g.last_level = lv
     level.copy_(real.from_numpy(lv))
     if parent is not None:
         parent.copy_(real.from_numpy(pa))
@@ -113,6 +114,13 @@ class _Graph:
 
     def status(self):
         return 0
+
+    def layer_stats(self):
+        return oracle.layer_profile(self.ro, self.last_level)
+
+    def layer_times(self):
+        v, _, _ = self.layer_stats()
+        return np.cumsum(np.full(len(v), 1000, np.int64))
 
     def autotune(self, what, samples=0):
         return dict(self.opts)
@@ -151,7 +159,7 @@ buf = io.StringIO()
 how = None
 with contextlib.redirect_stdout(buf):
     try:
-        how = f"returned {bench.main(['--scale', '10', '--steps', '1', '--warmup', '3', '--batched-scale', '10', '--batched-sources', '64', '--serving-requests', '2000', '--serving-scales', '6,7', '--cpu-sample-roots', '4'])}"
+        how = f"returned {bench.main(['--scale', '10', '--steps', '1', '--warmup', '3', '--batched-scale', '10', '--batched-sources', '64', '--serving-requests', '2000', '--serving-scales', '6,7', '--cpu-sample-roots', '4', '--other-workloads', 'erdos_renyi:9,kronecker:8'])}"
     except _Exited as e:
         how = f"direct exit {e.args[0]}"
 lines = buf.getvalue().strip().splitlines()

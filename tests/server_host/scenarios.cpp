@@ -381,6 +381,29 @@ void stress()
     CHECK(fake::injections_during_pull.load() == 0);
 }
 
+// A graph registered with a live server may not be released (its worker may
+// still search it): graph_release_check, the guard of bfs_graph_destroy,
+// refuses it with BFS_ERR_BUSY until every server holding it is destroyed.
+void registration()
+{
+    Graph *g = make_graph(1000, 16000);
+    CHECK(gbbfs::graph_release_check(g) == BFS_OK);
+    bfs_server *a = bfs_server_create(0), *b = bfs_server_create(0);
+    CHECK(a && b);
+    CHECK(bfs_server_add_graph(a, reinterpret_cast<bfs_graph *>(g)) == 0);
+    CHECK(bfs_server_add_graph(b, reinterpret_cast<bfs_graph *>(g)) == 0);
+    CHECK(bfs_server_add_graph(a, reinterpret_cast<bfs_graph *>(g)) == BFS_ERR_INVALID_ARG);  // twice
+    CHECK(gbbfs::graph_release_check(g) == BFS_ERR_BUSY);
+    Query q;
+    std::vector<uint8_t> buf((size_t)g->n, 0xAB);
+    CHECK(bfs_submit(a, 0, 5, buf.data(), &q.ticket) == BFS_OK);
+    CHECK(bfs_server_destroy(a) == BFS_OK);
+    CHECK(gbbfs::graph_release_check(g) == BFS_ERR_BUSY);  // still held by b
+    CHECK(bfs_server_destroy(b) == BFS_OK);
+    CHECK(gbbfs::graph_release_check(g) == BFS_OK);
+    delete g;
+}
+
 }  // namespace
 
 int main(int argc, char **argv)
@@ -401,6 +424,7 @@ int main(int argc, char **argv)
     else if (s == "kernel_depth") kernel_depth();
     else if (s == "pull_hold") pull_hold();
     else if (s == "stress") stress();
+    else if (s == "registration") registration();
     else {
         fprintf(stderr, "unknown scenario %s\n", s.c_str());
         return 2;

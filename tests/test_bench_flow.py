@@ -46,6 +46,14 @@ def _check_contract(line):
     assert set(line["clocks"]) >= {"sm_mhz", "sm_max_mhz", "reasons"}
     assert len(line["ablation"]) == 3 and all("error" not in v for v in line["ablation"].values())
     assert line["batched"]["queries_per_s"] > 0 and line["batched"]["uneven_mix"]["queries_per_s"] > 0
+    lp = line["layer_profile"]
+    assert "error" not in lp and lp["roots"] == 64 and lp["layers"][0]["d"] == 0
+    assert sum(x["edges_share"] for x in lp["layers"]) == pytest.approx(1.0)
+    others = line["other_workloads"]
+    assert set(others) == {"erdos_renyi_scale9_ef16_64roots", "kronecker_scale8_ef16_64roots"}
+    for v in others.values():
+        assert "error" not in v and v["hm_gteps"] > 0 and 0 < v["roofline"]["frac"]
+        assert v["teps_stats"]["runs"] == 128 and v["mean_launch_us"] > 0
 
 
 def test_flow_without_stalls():

@@ -245,9 +245,15 @@ def test_serving_measurement_stops_the_plain_path_at_a_failed_search(short_deadl
 def test_serving_measurement_bounds_the_server_close(short_deadline):
     pytest.importorskip("graphgen")
     gb, state = _fake_gb(stall_servers=(), hang_close=True)
+    searched = []
+    gb.bfs_run = lambda *a: searched.append(a)
     out = bench.serving_measurement(_serving_args(), gb, _fake_torch(), None)
     assert out["queries_per_s"] > 0 and "did not return" in out["close_error"]
     assert len(bench._KEEP_ALIVE) == 1
+    # the server's workers may still use its graphs: none is searched or freed
+    (server, graphs), = bench._KEEP_ALIVE
+    assert graphs and not any(g.closed for _, g in graphs)
+    assert searched == [] and out["plain_queries_per_s"] is None and "skipped" in out["plain_error"]
 
 
 def test_bounded_reports_a_measurement_that_does_not_finish(monkeypatch):

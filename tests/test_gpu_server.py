@@ -173,3 +173,25 @@ def test_graph_stats_after_drain(resident):
                 assert st["rounds"] > 0 and st["iter"] > 0 and st["has_workspace"], st
         with pytest.raises(gb.BfsError):
             s.graph_stats(len(ids))
+
+
+def test_registered_graph_cannot_be_destroyed_under_a_live_server():
+    """A server's worker may search its graphs until the server is
+    destroyed: bfs_graph_destroy refuses a registered graph with
+    BFS_ERR_BUSY (nothing freed, the graph stays usable) and succeeds once
+    the server is gone."""
+    ro, col = graphgen.kronecker(12, 16, 71)
+    r = int(graphgen.pick_roots(ro, 1, 71)[0])
+    n = len(ro) - 1
+    g = gb.Graph(ro, col)
+    s = gb.Server()
+    gid = s.add_graph(g)
+    with pytest.raises(gb.BfsError) as ei:
+        g.close()
+    assert ei.value.status == gb.BFS_ERR_BUSY and g.handle
+    buf = np.empty(n, np.uint8)
+    s.wait(s.submit(gid, r, buf), timeout_s=60)
+    np.testing.assert_array_equal(buf, oracle.bfs_batch(ro, col, np.array([r], np.int32))[0])
+    s.close()
+    g.close()
+    assert g.handle is None

@@ -5,8 +5,8 @@ they search (their device memory belongs to another allocator or a fixed
 budget, or they run on a path that must not block in cudaMalloc/cudaFree).
 It searches the caller's device CSR with scratch state kept in a fixed array
 inside the library.  Its results must equal those of the ordinary entry
-point: levels bit for bit, and parents that pass the same validation (the
-parent choice is not unique).
+point and of the oracle: levels bit for bit, and parents that pass the
+oracle's validation (the parent choice is not unique).
 
 The file name sorts last so that a run stopping at the first failure has
 already run every other test.
@@ -52,8 +52,12 @@ def test_noalloc_matches_bfs_run_on_two_calls_in_a_row():
             lv, pa = lv.cpu().numpy(), pa.cpu().numpy()
             ref_lv, ref_pa = ref_lv.cpu().numpy(), ref_pa.cpu().numpy()
             np.testing.assert_array_equal(lv, ref_lv)
-            assert oracle.validate(ro, col, int(r), lv, pa, ref_lv)[0] == 0
-            assert oracle.validate(ro, col, int(r), ref_lv, ref_pa, ref_lv)[0] == 0
+            # both against the oracle: levels bit for bit, parents validated
+            # with the oracle's levels as the reached-set reference
+            or_lv = oracle.bfs(ro, col, int(r), want_parent=False)[0]
+            np.testing.assert_array_equal(lv, or_lv)
+            assert oracle.validate(ro, col, int(r), lv, pa, or_lv)[0] == 0
+            assert oracle.validate(ro, col, int(r), ref_lv, ref_pa, or_lv)[0] == 0
     finally:
         g.close()
 
