@@ -356,6 +356,26 @@ int bfs_server_graph_stats(bfs_server *s, int graph_id, int64_t *out);
 int bfs_ticket_times(bfs_server *s, uint64_t ticket, int64_t *t_submit_ns,
                      int64_t *t_done_ns);
 
+/* Serving, not in the paper.  The path of one query through the server:
+ *   t_submit_ns, t_admit_ns, t_done_ns : submission, admission into a lane
+ *       of the graph's running bit-parallel search, completion (ns on the
+ *       monotonic clock of bfs_ticket_times; 0 while not reached).  Queue
+ *       wait = t_admit - t_submit; time in the search (iterations plus the
+ *       result copy) = t_done - t_admit.
+ *   join_iter, done_iter : the search's iteration counter when the lane was
+ *       filled and at the end of the round that found the query finished
+ *       (-1 while not reached); a query whose lanes_busy_at_join > 0 joined
+ *       a search already running for other queries (continuous batching).
+ *   graph_id, lane : where it ran (lane -1 until admitted).
+ * `out` is caller-owned.  Returns BFS_OK or BFS_ERR_INVALID_ARG (NULL
+ * argument, unknown ticket). */
+typedef struct bfs_ticket_record {
+    int64_t t_submit_ns, t_admit_ns, t_done_ns;
+    int64_t join_iter, done_iter;
+    int32_t graph_id, lane, lanes_busy_at_join, reserved;
+} bfs_ticket_record;
+int bfs_ticket_info(bfs_server *s, uint64_t ticket, bfs_ticket_record *out);
+
 #ifdef __cplusplus
 }
 #endif

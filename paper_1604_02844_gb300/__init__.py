@@ -88,7 +88,15 @@ SIGNATURES = {
     "bfs_server_drain": (_INT, [_P]),
     "bfs_ticket_times": (_INT, [_P, _U64, ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
     "bfs_server_graph_stats": (_INT, [_P, _INT, ctypes.POINTER(_I64)]),
+    "bfs_ticket_info": (_INT, [_P, _U64, _P]),
 }
+
+
+class TicketInfo(ctypes.Structure):
+    """Layout of bfs_ticket_record (include/gbbfs.h)."""
+    _fields_ = [("t_submit_ns", _I64), ("t_admit_ns", _I64), ("t_done_ns", _I64),
+                ("join_iter", _I64), ("done_iter", _I64),
+                ("graph_id", _I32), ("lane", _I32), ("lanes_busy_at_join", _I32), ("reserved", _I32)]
 
 
 class BfsError(RuntimeError):
@@ -283,6 +291,14 @@ def bfs_ticket_times(s, ticket: int):
     return a.value, b.value
 
 
+def bfs_ticket_info(s, ticket: int) -> dict:
+    """The path of one query: submission, admission, completion times and
+    the search iterations at which its lane joined and finished."""
+    info = TicketInfo()
+    _check(load().bfs_ticket_info(s, int(ticket), ctypes.byref(info)))
+    return {k: getattr(info, k) for k, _ in TicketInfo._fields_ if k != "reserved"}
+
+
 # ---- convenience wrappers -------------------------------------------------
 
 class Graph:
@@ -394,6 +410,9 @@ class Server:
 
     def times(self, ticket: int):
         return bfs_ticket_times(self.handle, ticket)
+
+    def info(self, ticket: int) -> dict:
+        return bfs_ticket_info(self.handle, ticket)
 
     def graph_stats(self, graph_id: int) -> dict:
         """Monitoring snapshot of one graph's queue and worker."""

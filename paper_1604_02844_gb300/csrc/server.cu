@@ -48,7 +48,10 @@ struct Request {
     int graph = 0;
     int32_t root = 0;
     uint8_t *out = nullptr;
-    int64_t t_submit = 0, t_done = 0;
+    int64_t t_submit = 0, t_admit = 0, t_done = 0;
+    int lane = -1;
+    int lanes_busy = 0;                 // lanes of the running search when this one joined
+    int64_t join_iter = -1, done_iter = -1;  // search iterations at joining and at the round that finished it
     std::atomic<int> status{BFS_NOT_READY};
 };
 
@@ -230,6 +233,7 @@ int Server::finish(GraphState &gs, unsigned long long mask)
         if (!((mask >> i) & 1ull)) continue;
         Request &r = *reqs[gs.lane_ticket[i] - 1];
         r.t_done = t;
+        r.done_iter = gs.have_last ? (int64_t)gs.last.iter : -1;
         r.status.store(BFS_OK);
         gs.lane_ticket[i] = 0;
         --outstanding;
@@ -274,13 +278,20 @@ int Server::round(GraphState &gs)
         }
         gs.room_wait_since = 0;
         const bool hold = gs.running && gs.have_last && pull_phase(gs.g, gs.last, gs.running);
+        const int busy = __builtin_popcountll(gs.running);
+        const int64_t t_admit = now_ns();
         while (!hold && !gs.waiting.empty() && (gs.running | add) != ~0ull) {
             const int lane = __builtin_ctzll(~(gs.running | add));
             const uint64_t t = gs.waiting.front();
             gs.waiting.pop_front();
             gs.lane_ticket[lane] = t;
             gs.lane_iter0[lane] = gs.have_last ? gs.last.iter : 0u;
-            src[lane] = reqs[t - 1]->root;
+            Request &r = *reqs[t - 1];
+            src[lane] = r.root;
+            r.t_admit = t_admit;
+            r.lane = lane;
+            r.lanes_busy = busy;
+            r.join_iter = (int64_t)gs.lane_iter0[lane];
             add |= 1ull << lane;
         }
         gs.running |= add;
@@ -518,6 +529,25 @@ int bfs_ticket_times(bfs_server *sh, uint64_t ticket, int64_t *t_submit_ns, int6
     Request &r = *s->reqs[ticket - 1];
     *t_submit_ns = r.t_submit;
     *t_done_ns = r.t_done;
+    return BFS_OK;
+}
+
+int bfs_ticket_info(bfs_server *sh, uint64_t ticket, bfs_ticket_record *out)
+{
+    if (!sh || !out) return set_error(BFS_ERR_INVALID_ARG, "bfs_ticket_info: NULL argument");
+    Server *s = reinterpret_cast<Server *>(sh);
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (ticket == 0 || ticket > s->reqs.size()) return set_error(BFS_ERR_INVALID_ARG, "bfs_ticket_info: unknown ticket");
+    const Request &r = *s->reqs[ticket - 1];
+    out->t_submit_ns = r.t_submit;
+    out->t_admit_ns = r.t_admit;
+    out->t_done_ns = r.t_done;
+    out->join_iter = r.join_iter;
+    out->done_iter = r.done_iter;
+    out->graph_id = r.graph;
+    out->lane = r.lane;
+    out->lanes_busy_at_join = r.lanes_busy;
+    out->reserved = 0;
     return BFS_OK;
 }
 

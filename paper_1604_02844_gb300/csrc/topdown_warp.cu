@@ -65,6 +65,7 @@ constexpr int MAXI = 2 * W;  // edges of one work item are < MAXI
 constexpr int OBW = 128;     // out-buffer entries per warp
 constexpr int UA = 12;       // pass A: visited-word loads per lane in flight
 constexpr int UB = 2;        // pass B: claims per lane in flight
+constexpr int CB = 64;       // modes 0, 3: deferred claims per warp (two per lane per round)
 constexpr int VW = 4;        // bottom-up: visited words per warp in flight
 
 enum { KM_ATOMIC = 0, KM_RESTORE = 1, KM_HYBRID = 2 };  // kernel variants
@@ -99,9 +100,14 @@ struct WParams {
     uint64_t timeout_ns;
 };
 
-struct WarpSmem {
-    int32_t stage[2][MAXI];  // staged adjacency; pass A compacts candidates in place
-    uint16_t ce[MAXI];       // candidate -> edge index inside the item
+struct alignas(16) WarpSmem {
+    int32_t stage[2][MAXI];  // staged adjacency, padded with the root's id to a multiple of 128 entries
+    union {
+        uint16_t ce[MAXI];   // mode 2: candidate -> edge index inside the item (compacted in place)
+        struct {
+            int32_t v[CB], u[CB];
+        } cand;              // modes 0, 3: candidates whose claim is deferred (vertex, source)
+    };
     int32_t off[2][33];      // item entries: prefix of lengths
     int32_t iu[2][32];       // item entries: vertex
     int32_t wv[OBW], wu[OBW];           // claimed vertices and their sources (internal ids)
@@ -193,7 +199,7 @@ __device__ __forceinline__ Item load_item(const WParams &p, int qi, const Desc &
 // the longest short list; a search over the flattened lists costs more
 // instructions than it saves).  Commits one group per lane.  Returns the
 // item's edge count (uniform).
-__device__ __forceinline__ int stage_item(WarpSmem &ws, const WParams &p, const Item &it_in, int buf)
+__device__ __forceinline__ int stage_item(WarpSmem &ws, const WParams &p, const Item &it_in, int buf, int rint)
 {
     const int lane = threadIdx.x & 31;
     Item it = it_in;
@@ -237,6 +243,10 @@ __device__ __forceinline__ int stage_item(WarpSmem &ws, const WParams &p, const 
         for (int k = 0; k < maxl; ++k)
             if (k < sl) cp_async4(&ws.stage[buf][off + k], p.col + it.b + k);
     }
+    // pad to a multiple of 128 entries with the root, whose visited bit is
+    // set from the start: the padding never becomes a candidate
+    const int pend = (et + 127) & ~127;
+    for (int k = et + lane; k < pend; k += 32) ws.stage[buf][k] = rint;
     cp_async_commit();
     return et;
 }
@@ -446,10 +456,9 @@ __device__ __forceinline__ void warp_flush(WarpSmem &ws, const WParams &p, int s
     __syncwarp();
 }
 
-// Passes A and B over the staged item in stage[buf] with `et` edges.
-template <int KM>
-__device__ __forceinline__ void process_item(WarpSmem &ws, const WParams &p, int buf, int et, int cnt,
-                                             int next_level, int set_out, int qo, int &ocnt, unsigned &my_new)
+// Mode 2 (Alg. 3): passes A and B over the staged item in stage[buf] with
+// `et` edges.
+__device__ __forceinline__ void process_item_rst(WarpSmem &ws, const WParams &p, int buf, int et, int cnt)
 {
     const int lane = threadIdx.x & 31;
     const unsigned lt = lanemask_lt();
@@ -464,22 +473,16 @@ __device__ __forceinline__ void process_item(WarpSmem &ws, const WParams &p, int
             const int e = base + k * 32 + lane;
             v[k] = e < et ? stg[e] : -1;
         }
-        if (KM == KM_RESTORE) {  // Alg. 3: not in vis and not in out; both words share one 8-byte load
-            // (a stale out word only sends v on to pass B)
+        // Alg. 3: not in vis and not in out; both words share one 8-byte load
+        // (a stale out word only sends v on to pass B)
 #pragma unroll
-            for (int k = 0; k < UA; ++k) {
-                if (v[k] >= 0) {
-                    const uint2 x = __ldca(p.vo + ((unsigned)v[k] >> 5));
-                    w[k] = x.x | x.y;
-                } else {
-                    w[k] = 0xffffffffu;
-                }
+        for (int k = 0; k < UA; ++k) {
+            if (v[k] >= 0) {
+                const uint2 x = __ldca(p.vo + ((unsigned)v[k] >> 5));
+                w[k] = x.x | x.y;
+            } else {
+                w[k] = 0xffffffffu;
             }
-        } else {
-            // L1-cached read: bits are only ever set during a search, so a
-            // stale word can only send an already visited vertex on to the atomicOr
-#pragma unroll
-            for (int k = 0; k < UA; ++k) w[k] = v[k] >= 0 ? __ldca(p.bitmap + ((unsigned)v[k] >> 5)) : 0xffffffffu;
         }
         __syncwarp();
 #pragma unroll
@@ -495,7 +498,7 @@ __device__ __forceinline__ void process_item(WarpSmem &ws, const WParams &p, int
         }
     }
     __syncwarp();
-    if constexpr (KM == KM_RESTORE) {
+    {
         // pass B of Alg. 3: plain read-modify-write of the out word, then
         // P[v] = u - n.  Lanes whose vertices share a word combine their bits
         // and the lowest of them writes the word once (rows are sorted, so
@@ -537,51 +540,140 @@ __device__ __forceinline__ void process_item(WarpSmem &ws, const WParams &p, int
             }
         }
         __syncwarp();
-    } else {
-    // pass B: claim with atomicOr; each winner is queued with its source
-    for (int c0 = 0; c0 < nc; c0 += 32 * UB) {
-        // room for a whole batch of winners, flushed outside the claim loop
-        if (ocnt > OBW - 32 * UB) {
-            warp_flush<KM == KM_HYBRID ? (FL_LP | FL_CNT) : FL_LP>(ws, p, set_out, qo, ocnt, next_level);
-            ocnt = 0;
-        }
-        int v[UB], e[UB];
-        bool win[UB];
+    }
+}
+
+// ---- modes 0 and 3: pass A with deferred claims ----------------------------
+//
+// Pass A reads the staged item 128 entries at a time (one 16-byte shared
+// load per lane and 4 entries), tests each entry's visited word and keeps a
+// per-lane bit mask of the candidates (entries whose bit was clear).  The
+// candidates, with their sources, go to the warp's deferred-claim buffer;
+// the buffer is claimed (pass B: atomicOr, two per lane in flight) only when
+// it cannot take the next candidates and at the end of the layer, so one
+// atomic round trip serves the candidates of several items.  A candidate
+// whose bit another warp sets in the meantime simply loses its atomicOr.
+
+// Claim the deferred candidates cand.v/u[0..nb) and queue the winners.
+template <int KM>
+__device__ __forceinline__ void claim_deferred(WarpSmem &ws, const WParams &p, int &nb, int set_out, int qo,
+                                               int &ocnt, int next_level, unsigned &my_new)
+{
+    constexpr int FL = KM == KM_HYBRID ? (FL_LP | FL_CNT) : FL_LP;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = lanemask_lt();
+    if (ocnt > OBW - CB) {  // room for every winner of this round
+        warp_flush<FL>(ws, p, set_out, qo, ocnt, next_level);
+        ocnt = 0;
+    }
+    __syncwarp();  // the buffer was filled by other lanes
+    const int v0 = lane < nb ? ws.cand.v[lane] : -1;
+    const int v1 = lane + 32 < nb ? ws.cand.v[lane + 32] : -1;
+    const int u0 = lane < nb ? ws.cand.u[lane] : 0;
+    const int u1 = lane + 32 < nb ? ws.cand.u[lane + 32] : 0;
+    bool w0 = false, w1 = false;
+    if (v0 >= 0) {
+        const unsigned bit = 1u << (v0 & 31);
+        w0 = !(atomicOr(p.bitmap + ((unsigned)v0 >> 5), bit) & bit);
+    }
+    if (v1 >= 0) {
+        const unsigned bit = 1u << (v1 & 31);
+        w1 = !(atomicOr(p.bitmap + ((unsigned)v1 >> 5), bit) & bit);
+    }
+    const unsigned m0 = __ballot_sync(FULL, w0), m1 = __ballot_sync(FULL, w1);
+    if (w0) {
+        const int pos = ocnt + __popc(m0 & lt);
+        ws.wv[pos] = v0;
+        ws.wu[pos] = u0;
+        ++my_new;
+    }
+    if (w1) {
+        const int pos = ocnt + __popc(m0) + __popc(m1 & lt);
+        ws.wv[pos] = v1;
+        ws.wu[pos] = u1;
+        ++my_new;
+    }
+    ocnt += __popc(m0) + __popc(m1);
+    nb = 0;
+    __syncwarp();  // the buffer is read before it is refilled
+}
+
+// Pass A over the staged item in stage[buf] (et entries, cnt entries of the
+// item; padded to a multiple of 128 with the root): candidates go to the
+// deferred-claim buffer (nb entries held).
+template <int KM>
+__device__ __forceinline__ void process_item_def(WarpSmem &ws, const WParams &p, int buf, int et, int cnt, int rint,
+                                                 int next_level, int set_out, int qo, int &ocnt, int &nb,
+                                                 unsigned &my_new)
+{
+    const int lane = threadIdx.x & 31;
+    const int32_t *stg = ws.stage[buf];
+    const int4 *stg4 = reinterpret_cast<const int4 *>(stg);
+    const int u_first = ws.iu[buf][0];
+    for (int base = 0; base < et; base += 32 * UA) {
+        int v[UA];
 #pragma unroll
-        for (int k = 0; k < UB; ++k) {
-            const int i = c0 + k * 32 + lane;
-            v[k] = i < nc ? stg[i] : -1;
-            e[k] = i < nc ? (int)ws.ce[i] : 0;
+        for (int c = 0; c < UA / 4; ++c) {
+            int4 q = make_int4(rint, rint, rint, rint);
+            if (base + 128 * c < et) q = stg4[(base + 128 * c) / 4 + lane];
+            v[4 * c + 0] = q.x;
+            v[4 * c + 1] = q.y;
+            v[4 * c + 2] = q.z;
+            v[4 * c + 3] = q.w;
         }
+        // L1-cached read: bits are only ever set during a search, so a stale
+        // word can only send an already visited vertex on to the atomicOr
+        unsigned w[UA];
 #pragma unroll
-        for (int k = 0; k < UB; ++k) {
-            win[k] = false;
-            if (v[k] >= 0) {
-                const unsigned bit = 1u << (v[k] & 31);
-                win[k] = !(atomicOr(p.bitmap + ((unsigned)v[k] >> 5), bit) & bit);
+        for (int k = 0; k < UA; ++k) w[k] = __ldca(p.bitmap + ((unsigned)v[k] >> 5));
+        unsigned cm = 0;  // bit k: entry k of this lane is a candidate
+#pragma unroll
+        for (int k = 0; k < UA; ++k) cm |= (~__funnelshift_r(w[k], w[k], (unsigned)v[k]) & 1u) << k;
+        // at most two candidates per lane per round into the buffer
+        while (__any_sync(FULL, cm != 0u)) {
+            int k1 = -1, k2 = -1;
+            if (cm) {
+                k1 = __ffs(cm) - 1;
+                cm &= cm - 1;
             }
-        }
+            if (cm) {
+                k2 = __ffs(cm) - 1;
+                cm &= cm - 1;
+            }
+            const int t = (k1 >= 0) + (k2 >= 0);
+            int inc = t;
 #pragma unroll
-        for (int k = 0; k < UB; ++k) {
-            const unsigned m = __ballot_sync(FULL, win[k]);
-            if (!m) continue;
-            if (win[k]) {
-                int lo = 0, hi = cnt;  // source entry: largest j with off[j] <= e
-                while (hi - lo > 1) {
-                    const int mid = (lo + hi) >> 1;
-                    if (ws.off[buf][mid] <= e[k]) lo = mid;
-                    else hi = mid;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(FULL, inc, o);
+                if (lane >= o) inc += y;
+            }
+            const int total = __shfl_sync(FULL, inc, 31);
+            if (nb + total > CB) claim_deferred<KM>(ws, p, nb, set_out, qo, ocnt, next_level, my_new);
+            int pos = nb + inc - t;
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const int k = j == 0 ? k1 : k2;
+                if (k >= 0) {
+                    const int e = base + 128 * (k >> 2) + 4 * lane + (k & 3);  // entry inside the item
+                    int u = u_first;
+                    if (cnt > 1) {  // source entry: largest j with off[j] <= e
+                        int lo = 0, hi = cnt;
+                        while (hi - lo > 1) {
+                            const int mid = (lo + hi) >> 1;
+                            if (ws.off[buf][mid] <= e) lo = mid;
+                            else hi = mid;
+                        }
+                        u = ws.iu[buf][lo];
+                    }
+                    ws.cand.v[pos] = stg[e];
+                    ws.cand.u[pos] = u;
+                    ++pos;
                 }
-                const int pos = ocnt + __popc(m & lt);
-                ws.wv[pos] = v[k];
-                ws.wu[pos] = ws.iu[buf][lo];
-                ++my_new;
             }
-            ocnt += __popc(m);
+            nb += total;
         }
     }
     __syncwarp();
-    }
 }
 
 // ---- direction-optimising mode (KM_HYBRID) ---------------------------------
@@ -795,10 +887,11 @@ __global__ void __launch_bounds__(WPB * 32, (24 / WPB) > 0 ? (24 / WPB) : 1) td_
     Ctrl *c = p.ctrl;
     const uint64_t t_start = globaltimer();
 
+    const int rint = __ldg(p.perm + p.root);  // the root in internal numbering
+
     // ---- initialisation (Alg. 1: P = infinity except P[s] = s; vis = {s}) --
     {
         const int64_t stride = (int64_t)G * WPB * 32;
-        const int rint = __ldg(p.perm + p.root);  // the root in internal numbering
         for (int64_t i = (int64_t)blockIdx.x * WPB * 32 + tid; i < p.n; i += stride) {
             const bool is_root = (i == p.root);
             p.level[i] = is_root ? 0 : -1;
@@ -932,7 +1025,7 @@ __global__ void __launch_bounds__(WPB * 32, (24 / WPB) > 0 ? (24 / WPB) : 1) td_
                 c->hub_count[set_rst] = 0;
             }
         }
-        int ocnt = 0;
+        int ocnt = 0, nb = 0;  // winners to flush; deferred candidates
         unsigned td_new = 0;
 
         // software pipeline over this warp's items gw, gw+GW, ...
@@ -940,7 +1033,7 @@ __global__ void __launch_bounds__(WPB * 32, (24 / WPB) > 0 ? (24 / WPB) : 1) td_
         Desc d0 = load_desc(p, qi, nH, n_items, id, split);
         Item cur = load_item(p, qi, d0, id < n_items, split);
         int buf = 0;
-        int et_cur = (id < n_items) ? stage_item(ws, p, cur, buf) : 0;
+        int et_cur = (id < n_items) ? stage_item(ws, p, cur, buf, rint) : 0;
         int cnt_cur = cur.cnt;
         if (KM != KM_HYBRID && p.stats && id < n_items && lane == 0)
             my_vertices += (d0.c < 0) ? (cur.b == __ldg(p.ro + cur.u) ? 1 : 0) : (unsigned)cur.cnt;
@@ -951,7 +1044,7 @@ __global__ void __launch_bounds__(WPB * 32, (24 / WPB) > 0 ? (24 / WPB) : 1) td_
             const unsigned id1 = id + GW, id2 = id + 2 * GW;
             int et_nxt = 0;
             if (id1 < n_items) {
-                et_nxt = stage_item(ws, p, nxt, buf ^ 1);
+                et_nxt = stage_item(ws, p, nxt, buf ^ 1, rint);
                 if (KM != KM_HYBRID && p.stats && lane == 0)
                     my_vertices += (d1.c < 0) ? (nxt.b == __ldg(p.ro + nxt.u) ? 1 : 0) : (unsigned)nxt.cnt;
             } else {
@@ -963,7 +1056,10 @@ __global__ void __launch_bounds__(WPB * 32, (24 / WPB) > 0 ? (24 / WPB) : 1) td_
             asm volatile("cp.async.wait_group 1;" ::: "memory");
             __syncwarp();
             if (lane == 0) my_edges += (unsigned long long)et_cur;
-            process_item<KM>(ws, p, buf, et_cur, cnt_cur, next_level, set_out, qo, ocnt, td_new);
+            if constexpr (KM == KM_RESTORE)
+                process_item_rst(ws, p, buf, et_cur, cnt_cur);
+            else
+                process_item_def<KM>(ws, p, buf, et_cur, cnt_cur, rint, next_level, set_out, qo, ocnt, nb, td_new);
             buf ^= 1;
             id = id1;
             et_cur = et_nxt;
@@ -974,6 +1070,8 @@ __global__ void __launch_bounds__(WPB * 32, (24 / WPB) > 0 ? (24 / WPB) : 1) td_
         }
         cp_async_wait_all();
         __syncwarp();
+        if constexpr (KM != KM_RESTORE)
+            if (nb > 0) claim_deferred<KM>(ws, p, nb, set_out, qo, ocnt, next_level, td_new);
         if (ocnt > 0) warp_flush<KM == KM_HYBRID ? (FL_LP | FL_CNT) : FL_LP>(ws, p, set_out, qo, ocnt, next_level);
 
         if (KM == KM_RESTORE) {

@@ -381,6 +381,41 @@ void stress()
     CHECK(fake::injections_during_pull.load() == 0);
 }
 
+// A query submitted while another query's search runs joins that search
+// (continuous batching): its record shows the lanes already busy and the
+// iteration at which it joined; times and iterations are ordered.
+void join_record()
+{
+    fake::deep_root = 7;
+    fake::deep_depth = 200;
+    fake::slow_graph_n = 1000;  // 2 ms per round: the long search runs about 0.1 s
+    fake::slow_step_us = 2000;
+    Bench b({1000}, 0);
+    Query lq, q;
+    lq.root = 7;
+    q.root = 3;
+    CHECK(b.submit(lq) == BFS_OK);
+    int64_t st[7] = {};
+    for (int i = 0; i < 20000; ++i) {  // until the long search has run a few rounds
+        CHECK(bfs_server_graph_stats(b.s, 0, st) == BFS_OK);
+        if (st[3] >= 8) break;
+        std::this_thread::sleep_for(std::chrono::microseconds(100));
+    }
+    CHECK(st[3] >= 8);
+    CHECK(b.submit(q) == BFS_OK);
+    CHECK(b.wait(q) == BFS_OK);
+    CHECK(b.result_ok(q));
+    bfs_ticket_record r{}, l{};
+    CHECK(bfs_ticket_info(b.s, q.ticket, &r) == BFS_OK);
+    CHECK(r.lanes_busy_at_join == 1 && r.join_iter >= 8 && r.done_iter > r.join_iter);
+    CHECK(r.t_submit_ns > 0 && r.t_admit_ns >= r.t_submit_ns && r.t_done_ns >= r.t_admit_ns);
+    CHECK(bfs_server_drain(b.s) == BFS_OK);
+    CHECK(b.result_ok(lq));
+    CHECK(bfs_ticket_info(b.s, lq.ticket, &l) == BFS_OK);
+    CHECK(l.lanes_busy_at_join == 0 && l.join_iter == 0 && l.lane != r.lane && l.done_iter >= 200);
+    CHECK(bfs_ticket_info(b.s, 0, &l) == BFS_ERR_INVALID_ARG);
+}
+
 // A graph registered with a live server may not be released (its worker may
 // still search it): graph_release_check, the guard of bfs_graph_destroy,
 // refuses it with BFS_ERR_BUSY until every server holding it is destroyed.
@@ -425,6 +460,7 @@ int main(int argc, char **argv)
     else if (s == "pull_hold") pull_hold();
     else if (s == "stress") stress();
     else if (s == "registration") registration();
+    else if (s == "join_record") join_record();
     else {
         fprintf(stderr, "unknown scenario %s\n", s.c_str());
         return 2;

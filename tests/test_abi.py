@@ -125,3 +125,20 @@ def test_server_wait_timeout_and_failure(monkeypatch):
     monkeypatch.setattr(gb, "bfs_poll", failed)
     with pytest.raises(gb.BfsError):
         s.wait(3)
+
+
+def test_ticket_info_layout_matches_the_header(tmp_path):
+    """The binding's bfs_ticket_record structure has the C layout (size and
+    field offsets printed by a program compiled against the header)."""
+    import ctypes
+    src = tmp_path / "layout.c"
+    src.write_text('#include <stddef.h>\n#include <stdio.h>\n#include "gbbfs.h"\n'
+                   "int main(void) { printf(\"%zu\", sizeof(bfs_ticket_record));\n"
+                   + "".join(f'  printf(" %zu", offsetof(bfs_ticket_record, {f}));\n'
+                             for f, _ in gb.TicketInfo._fields_)
+                   + "  return 0; }\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    assert got[0] == ctypes.sizeof(gb.TicketInfo)
+    assert got[1:] == [getattr(gb.TicketInfo, f).offset for f, _ in gb.TicketInfo._fields_]

@@ -15,7 +15,9 @@ loop through its C ABI and check that:
 - device timeouts and depth overflows fail the queries instead of hanging;
 - the host backstop ends a lane that never finishes;
 - the pull-phase hold is kept;
-- a graph registered with a live server cannot be released.
+- a graph registered with a live server cannot be released;
+- a query submitted during another's search joins it, and its record
+  (bfs_ticket_info) says so.
 
 The loop's wait for room is shortened to 1.5 s in this build. A stress
 scenario mixes eight graphs, bursts of queries, steps of random length, the
@@ -34,7 +36,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(ROOT, "paper_1604_02844_gb300", "csrc")
 HOST = os.path.join(HERE, "server_host")
 SCENARIOS = ["mixed", "tight_budget", "device_oom_wait", "device_oom_fail", "room_limit", "timeout",
-             "depth_backstop", "kernel_depth", "pull_hold", "stress", "registration"]
+             "depth_backstop", "kernel_depth", "pull_hold", "stress", "registration",
+             "join_record"]
 
 
 def _cuda_include():
