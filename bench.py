@@ -590,6 +590,7 @@ SERVING_WAIT_S = 120.0
 SERVING_WAIT_PER_QUERY_S = 0.002
 SERVER_CLOSE_WAIT_S = 60.0  # longest wait for bfs_server_destroy
 SERVING_TOTAL_S = 1500.0    # the whole serving measurement, retry included
+SERVING_SWEEP = (0.3, 0.4, 0.5, 0.6, 0.7, 0.8, 0.9, 1.0)  # offered rates, fractions of the burst rate
 
 
 class ServingStuck(Exception):
@@ -617,6 +618,49 @@ class ServingFailed(Exception):
     def __init__(self, msg, graphs):
         super().__init__(msg)
         self.graphs = graphs
+
+
+def serving_stats(recs, scales):
+    """Latency split of one serving run from the library's ticket records
+    (bfs_ticket_info): end to end, queue wait (submission to admission into
+    a lane) and time in the search (admission to completion: iterations plus
+    the result copy), overall and per graph scale; how many queries joined a
+    search that was already running for others (continuous batching); and
+    the served rate over the steady part of the arrival window (completions
+    between 25 % and 100 % of it, per second)."""
+    sub = np.array([r["t_submit_ns"] for r in recs], np.float64)
+    adm = np.array([r["t_admit_ns"] for r in recs], np.float64)
+    done = np.array([r["t_done_ns"] for r in recs], np.float64)
+    gid = np.array([r["graph_id"] for r in recs])
+    busy = np.array([r["lanes_busy_at_join"] for r in recs])
+    iters = np.array([r["done_iter"] - r["join_iter"] for r in recs], np.float64)
+    lat, wait, ins = (done - sub) * 1e-6, (adm - sub) * 1e-6, (done - adm) * 1e-6
+
+    def pct(x, q):
+        return float(np.percentile(x, q)) if len(x) else None
+
+    t_a = sub.min() + 0.25 * (sub.max() - sub.min())
+    t_b = sub.max()
+    served = float(((done >= t_a) & (done <= t_b)).sum() / ((t_b - t_a) * 1e-9)) if t_b > t_a else None
+    per = {}
+    for g in sorted(set(gid.tolist())):
+        m = gid == g
+        per[str(scales[g])] = {"requests": int(m.sum()), "p50_ms": pct(lat[m], 50), "p99_ms": pct(lat[m], 99),
+                               "queue_wait_p99_ms": pct(wait[m], 99), "in_search_p50_ms": pct(ins[m], 50),
+                               "in_search_p99_ms": pct(ins[m], 99), "iterations_p50": pct(iters[m], 50)}
+    return {"p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99),
+            "queue_wait_p50_ms": pct(wait, 50), "queue_wait_p99_ms": pct(wait, 99),
+            "in_search_p50_ms": pct(ins, 50), "in_search_p99_ms": pct(ins, 99),
+            "joined_running_search": float((busy > 0).mean()) if len(busy) else None,
+            "steady_served_qps": served, "per_scale": per}
+
+
+def find_knee(points, tol=0.05):
+    """The sustainable rate: the highest offered rate whose steady served
+    rate is within tol of it (None if no point is)."""
+    ok = [p["offered_qps"] for p in points
+          if p.get("steady_served_qps") and p["steady_served_qps"] >= (1.0 - tol) * p["offered_qps"]]
+    return max(ok) if ok else None
 
 
 def serving_measurement(args, gb, torch, dev):
@@ -689,24 +733,22 @@ def serving_measurement(args, gb, torch, dev):
             for t, g_, b in inflight:
                 pools[g_].append(b)
             server._keep.clear()
-            lat = []
-            for t in tickets:
-                a, b2 = server.times(t)
-                lat.append((b2 - a) * 1e-9)
-            return elapsed, np.array(lat)
+            return elapsed, [server.info(t) for t in tickets]
+
+        def point(k, rate, **extra):
+            el, recs = run(draw(k), rate)
+            return dict(extra, offered_qps=rate, requests=k, queries_per_s=k / el, **serving_stats(recs, scales))
 
         try:
             run(draw(2000), None)  # warm-up: workspaces, kernels
             n_sat = min(20000, args.serving_requests)
-            el, lat = run(draw(n_sat), None)
+            el, _ = run(draw(n_sat), None)
             sat = n_sat / el
-            points = []
-            for frac in (0.5, 0.7, 0.9):
-                k = args.serving_requests if frac == 0.7 else max(1000, args.serving_requests // 5)
-                el, lat = run(draw(k), frac * sat)
-                points.append({"rate_fraction_of_saturation": frac, "offered_qps": frac * sat, "requests": k,
-                               "queries_per_s": k / el, "p50_ms": float(np.percentile(lat, 50) * 1e3),
-                               "p99_ms": float(np.percentile(lat, 99) * 1e3)})
+            # rate sweep (fractions of the burst rate) to find the sustainable rate
+            points = [point(max(2000, args.serving_requests // 10), f * sat, rate_fraction_of_burst=f)
+                      for f in SERVING_SWEEP]
+            knee = find_knee(points) or SERVING_SWEEP[0] * sat
+            head = point(args.serving_requests, 0.7 * knee, rate_fraction_of_knee=0.7)
         except (ServingStuck, gb.BfsError) as e:
             # each graph's queue and worker state, then a bounded attempt to
             # close; the server and its graphs stay alive (closing them under
@@ -737,14 +779,14 @@ def serving_measurement(args, gb, torch, dev):
             # searched nor freed from here on
             close_errors.append(f"bfs_server_destroy did not return within {SERVER_CLOSE_WAIT_S:.1f} s")
             _KEEP_ALIVE.append((server, graphs))
-            return sat, points, False
-        return sat, points, True
+            return sat, points, knee, head, False
+        return sat, points, knee, head, True
 
     stalls, close_errors = [], []
     graphs = upload()
     for _ in range(2):
         try:
-            sat, points, closed = attempt(graphs)
+            sat, points, knee, head, closed = attempt(graphs)
             break
         except ServingFailed as f:
             stalls.append({"error": str(f), "graphs": f.graphs})
@@ -784,17 +826,18 @@ def serving_measurement(args, gb, torch, dev):
     if closer.is_alive():
         close_errors.append(f"bfs_graph_destroy did not return within {SERVER_CLOSE_WAIT_S:.1f} s")
         _KEEP_ALIVE.append(graphs)
-    head = points[1]
     out = {"workload": workload,
-           "requests": head["requests"], "saturated_queries_per_s": sat,
+           "requests": head["requests"], "burst_queries_per_s": sat, "sustainable_qps": knee,
            "queries_per_s": head["queries_per_s"], "p50_ms": head["p50_ms"], "p99_ms": head["p99_ms"],
-           "offered_qps": head["offered_qps"], "sweep": points,
+           "offered_qps": head["offered_qps"], "headline": head, "sweep": points,
            "plain_queries_per_s": None if plain_error else len(plat) / sum(plat),
            "plain_p50_ms": None if plain_error else float(np.percentile(plat, 50) * 1e3),
            "plain_p99_ms": None if plain_error else float(np.percentile(plat, 99) * 1e3),
            "how": "bfs_submit/bfs_poll (64-lane continuous batching, uint8 levels to pinned host buffers); "
-                  "latency from the library's ticket times; plain = bfs_run + sync per query, "
-                  "int32 levels to pinned host memory, back to back"}
+                  "latency and its split from the library's ticket records (bfs_ticket_info); sustainable "
+                  "rate = highest swept offered rate whose steady served rate is within 5 %; headline at "
+                  "0.7 x that rate; plain = bfs_run + sync per query, int32 levels to pinned host memory, "
+                  "back to back"}
     if stalls:
         out["stalls_before_this_attempt"] = stalls
     if plain_error:

@@ -355,6 +355,7 @@ int64_t bfs_graph_get_option(const bfs_graph *gh, int option)
 
 int bfs_run(bfs_graph *gh, int32_t root, int32_t *level_out, int32_t *parent_out, void *stream)
 {
+    const NvtxRange nvtx("bfs_run");
     clear_error();
     if (!gh) return set_error(BFS_ERR_INVALID_ARG, "bfs_run: NULL graph");
     Graph *g = reinterpret_cast<Graph *>(gh);
@@ -478,6 +479,7 @@ int bfs_graph_visited_bitmap(bfs_graph *gh, uint32_t *words_out, int64_t nwords)
 
 int bfs_run_batch(bfs_graph *gh, const int32_t *roots, int32_t k, uint8_t *level_out)
 {
+    const NvtxRange nvtx("bfs_run_batch");
     clear_error();
     if (!gh) return set_error(BFS_ERR_INVALID_ARG, "bfs_run_batch: NULL graph");
     if (k < 0 || (k > 0 && (!roots || !level_out))) return set_error(BFS_ERR_INVALID_ARG, "bfs_run_batch: bad argument");

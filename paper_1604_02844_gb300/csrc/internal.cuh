@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <atomic>
 #include <mutex>
 #include <string>
@@ -114,6 +116,16 @@ struct Graph {
     Options opt;
     std::mutex mu;
     std::atomic<int> servers{0};  // live servers this graph is registered with
+};
+
+// A named host-side range for profilers (NVTX, header-only; costs nothing
+// when no tool is attached).  The searches are persistent kernels, so a
+// range covers one launch; per-layer times come from the device counters.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
 };
 
 // A graph registered with a live server is still in use by the server's

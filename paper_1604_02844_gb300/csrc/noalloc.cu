@@ -102,6 +102,7 @@ using namespace gbbfs;
 extern "C" int bfs_run_noalloc(const int32_t *row_offsets, const int32_t *col_idx, int64_t n, int64_t m, int32_t root,
                                int32_t *level_out, int32_t *parent_out, void *stream)
 {
+    const NvtxRange nvtx("bfs_run_noalloc");
     clear_error();
     if (n < 1 || n > kMaxN || m < 0 || m > kMaxM)
         return set_error(BFS_ERR_INVALID_ARG,

@@ -258,6 +258,7 @@ static bool pull_phase(const Graph *g, const MsCtrl &st, unsigned long long runn
 // batch is in its pull phase), a few iterations, finished lanes out.
 int Server::round(GraphState &gs)
 {
+    const NvtxRange nvtx("bfs_server round");
     unsigned long long add = 0, running;
     int32_t src[64] = {0};
     int active = 1;
@@ -391,6 +392,7 @@ bfs_server *bfs_server_create(int64_t hbm_budget_bytes)
         set_error(BFS_ERR_INVALID_ARG, "bfs_server_create: negative budget");
         return nullptr;
     }
+    nvtxInitialize(nullptr);  // once, before any worker thread names a range
     Server *s = new (std::nothrow) Server();
     if (!s) {
         set_error(BFS_ERR_OOM, "bfs_server_create: host allocation");

@@ -122,6 +122,7 @@ def _fake_gb(stall_servers, fail_servers=(), hang_close=False):
             self.graphs = []
             self._keep = {}
             self.t = {}
+            self.gid = {}
             self.closed = False
 
         def add_graph(self, g):
@@ -131,6 +132,7 @@ def _fake_gb(stall_servers, fail_servers=(), hang_close=False):
         def submit(self, gid, root, buf):
             t = len(self.t) + 1
             self.t[t] = _t.monotonic_ns()
+            self.gid[t] = gid
             return t
 
         def poll(self, t):
@@ -140,6 +142,11 @@ def _fake_gb(stall_servers, fail_servers=(), hang_close=False):
 
         def times(self, t):
             return self.t[t], self.t[t] + 1000
+
+        def info(self, t):
+            return {"t_submit_ns": self.t[t], "t_admit_ns": self.t[t] + 400, "t_done_ns": self.t[t] + 1000,
+                    "join_iter": 2, "done_iter": 5, "graph_id": self.gid[t], "lane": 0,
+                    "lanes_busy_at_join": t % 2}
 
         def graph_stats(self, gid):
             return {"waiting": 1, "running": 0, "phase": "waiting for work"}
@@ -193,7 +200,37 @@ def test_serving_measurement_normal_run(short_deadline):
     gb, state = _fake_gb(stall_servers=())
     out = bench.serving_measurement(_serving_args(), gb, _fake_torch(), None)
     assert "error" not in out and "stalls_before_this_attempt" not in out
-    assert out["queries_per_s"] > 0 and len(out["sweep"]) == 3 and state["servers"] == 1
+    assert out["queries_per_s"] > 0 and len(out["sweep"]) == len(bench.SERVING_SWEEP) and state["servers"] == 1
+    assert out["sustainable_qps"] > 0 and out["offered_qps"] == pytest.approx(0.7 * out["sustainable_qps"])
+    head = out["headline"]
+    assert set(head["per_scale"]) == {"6", "7"} and head["queue_wait_p99_ms"] == pytest.approx(4e-4)
+    assert head["in_search_p50_ms"] == pytest.approx(6e-4) and 0.4 < head["joined_running_search"] < 0.6
+
+
+def test_serving_stats_hand_count():
+    # four queries on two graphs (scales 10 and 20); times in ns
+    recs = [dict(t_submit_ns=0, t_admit_ns=1_000_000, t_done_ns=3_000_000, graph_id=0, lanes_busy_at_join=0,
+                 join_iter=0, done_iter=4),
+            dict(t_submit_ns=1_000_000, t_admit_ns=1_000_000, t_done_ns=2_000_000, graph_id=1, lanes_busy_at_join=3,
+                 join_iter=2, done_iter=5),
+            dict(t_submit_ns=2_000_000, t_admit_ns=4_000_000, t_done_ns=5_000_000, graph_id=0, lanes_busy_at_join=1,
+                 join_iter=4, done_iter=6),
+            dict(t_submit_ns=4_000_000, t_admit_ns=4_000_000, t_done_ns=10_000_000, graph_id=1, lanes_busy_at_join=0,
+                 join_iter=0, done_iter=8)]
+    st = bench.serving_stats(recs, [10, 20])
+    assert st["p50_ms"] == pytest.approx(3.0)          # latencies 3, 1, 3, 6 ms
+    assert st["queue_wait_p50_ms"] == pytest.approx(0.5)  # waits 1, 0, 2, 0 ms
+    assert st["joined_running_search"] == 0.5
+    # steady window: submissions span 0..4 ms, window 1..4 ms; completions in it: 2, 3 ms
+    assert st["steady_served_qps"] == pytest.approx(2 / 3e-3)
+    assert st["per_scale"]["10"]["requests"] == 2 and st["per_scale"]["20"]["iterations_p50"] == pytest.approx(5.5)  # 3 and 8
+
+
+def test_find_knee():
+    pts = [{"offered_qps": 100, "steady_served_qps": 99}, {"offered_qps": 200, "steady_served_qps": 192},
+           {"offered_qps": 300, "steady_served_qps": 240}]
+    assert bench.find_knee(pts) == 200
+    assert bench.find_knee([{"offered_qps": 100, "steady_served_qps": 50}]) is None
 
 
 def test_serving_measurement_retries_once_after_a_stall(short_deadline):

@@ -195,3 +195,55 @@ def test_registered_graph_cannot_be_destroyed_under_a_live_server():
     s.close()
     g.close()
     assert g.handle is None
+
+
+def test_continuous_batching_queries_join_a_running_search():
+    """Continuous batching on the device: while a deep search (a 200-vertex
+    path hanging off a Kronecker scale-14 graph, searched from the path's
+    far end) is running, further queries on the same graph are admitted into
+    free lanes of that search.  Their ticket records show that they joined a
+    running search (lanes busy, join iteration > 0, admission before the deep
+    query finished), and every result equals the oracle's and the same query
+    run alone."""
+    kro, kcol = graphgen.kronecker(14, 16, 81)
+    nk = len(kro) - 1
+    src = np.repeat(np.arange(nk, dtype=np.int32), np.diff(kro))
+    hub = int(np.argmax(np.diff(kro)))
+    path = np.arange(nk, nk + 200, dtype=np.int32)
+    ps = np.concatenate([src, path[:-1], [path[0]]]).astype(np.int32)
+    pd = np.concatenate([kcol, path[1:], [hub]]).astype(np.int32)
+    ro, col = graphgen.csr_from_tuples(nk + 200, ps, pd)
+    n = len(ro) - 1
+    deep = int(path[-1])
+    others = [int(r) for r in graphgen.pick_roots(kro, 24, 82)]
+    with gb.Graph(ro, col) as g:
+        with gb.Server() as s:
+            gid = s.add_graph(g)
+            bufs = {deep: np.empty(n, np.uint8)}
+            t_deep = s.submit(gid, deep, bufs[deep])
+            t0 = time.monotonic()
+            while s.graph_stats(gid)["iter"] < 20 and time.monotonic() - t0 < 30:
+                time.sleep(0.0005)
+            assert s.graph_stats(gid)["iter"] >= 20 and not s.poll(t_deep)
+            tickets = {}
+            for r in others:
+                bufs[r] = np.empty(n, np.uint8)
+                tickets[r] = s.submit(gid, r, bufs[r])
+            s.wait(t_deep, timeout_s=60)
+            for t in tickets.values():
+                s.wait(t, timeout_s=60)
+            deep_rec = s.info(t_deep)
+            joined = [s.info(t) for t in tickets.values()]
+            assert deep_rec["join_iter"] == 0 and deep_rec["done_iter"] >= 200
+            overlap = [r for r in joined if r["lanes_busy_at_join"] > 0 and r["join_iter"] >= 20
+                       and r["t_admit_ns"] < deep_rec["t_done_ns"]]
+            assert len(overlap) == len(others), joined[:3]
+            assert len({r["lane"] for r in joined} | {deep_rec["lane"]}) == len(others) + 1
+            # the same queries alone (one at a time on the same server)
+            for r in [deep] + others[:6]:
+                alone = np.empty(n, np.uint8)
+                s.wait(s.submit(gid, r, alone), timeout_s=60)
+                np.testing.assert_array_equal(alone, bufs[r], err_msg=f"root {r}: alone vs mixed")
+    ref = oracle.bfs_batch(ro, col, np.array([deep] + others, np.int32))
+    for i, r in enumerate([deep] + others):
+        np.testing.assert_array_equal(bufs[r], ref[i], err_msg=f"root {r}")
