@@ -502,6 +502,26 @@ def uneven_mix_measurement(args, gb, torch, dev, main_graph):
             "queries_per_s": 256 / best, "s_per_256": best}
 
 
+def batched_algorithmic_bytes(torch, levels, deg, dev):
+    """Minimum DRAM bytes of the bit-parallel search of levels (uint8
+    [k][n], 0xFF unreached), groups of 64 consecutive sources: per iteration
+    i, every vertex in some lane's frontier reads its adjacency (4 B per
+    entry), its frontier word (8 B) and its seen/next words (16 B); every
+    vertex first reached by some lane in that iteration writes its 64-lane
+    level row (64 B)."""
+    w = torch.from_numpy(4 * deg + 24).to(dev)
+    total = 0
+    for b0 in range(0, levels.shape[0], 64):
+        lv = levels[b0:b0 + 64]
+        reached = lv != 255
+        depth = int(lv[reached].max().item()) if bool(reached.any()) else -1
+        for i in range(depth + 1):
+            total += int(w[(lv == i).any(0)].sum().item())
+            if i < depth:
+                total += 64 * int((lv == i + 1).any(0).sum().item())
+    return float(total)
+
+
 def batched_measurement(args, gb, torch, dev):
     """1,024 seeded sources on a Kronecker graph (scale 20, ef 16) through
     bfs_run_batch (64 sources per bit-parallel batch), against the plain path
@@ -523,6 +543,7 @@ def batched_measurement(args, gb, torch, dev):
         gb.bfs_run_batch(g.handle, roots, out)
         times.append(time.perf_counter() - t0)
     t_batch = min(times)
+    bytes_alg = batched_algorithmic_bytes(torch, out, np.diff(ro).astype(np.int64), dev)
     level = torch.empty(n, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream(dev)
     for r in roots[:8]:
@@ -545,6 +566,14 @@ def batched_measurement(args, gb, torch, dev):
             "tuned_by": "bfs_graph_autotune(BFS_TUNE_BATCH)", "queries_per_s": len(roots) / t_batch,
             "plain_queries_per_s": len(roots) / t_plain, "speedup_vs_plain": t_plain / t_batch,
             "s_per_1024_batched": t_batch, "s_per_1024_plain": t_plain,
+            "roofline": {"bound": "hbm", "achieved": bytes_alg / t_batch / 1e9, "peak": measured_peaks()[0],
+                         "unit": "GB/s", "frac": bytes_alg / t_batch / 1e9 / measured_peaks()[0],
+                         "peak_kind": measured_peaks()[1], "kernel": "ms_kernel (bfs_run_batch)",
+                         "algorithmic_bytes": bytes_alg,
+                         "how": "push-formulation bytes per group of 64 consecutive sources, per iteration i: "
+                                "sum over vertices in some lane's frontier (4 B/entry + 8 B frontier word + 16 B "
+                                "seen/next) + 64 B level row per vertex first reached by some lane, from the "
+                                "call's level rows, outside the timed region; over the call's host wall time"},
             "how": "host wall clock around the synchronous bfs_run_batch (device output, best of 3); "
                    "plain = CUDA events around back-to-back bfs_run (levels only) on one stream"}
 

@@ -302,3 +302,17 @@ def test_bounded_reports_a_measurement_that_does_not_finish(monkeypatch):
     assert out == {"error": "slow: did not finish within 0 s"} and seen == ["setup"]
     assert len(bench._KEEP_ALIVE) == 1
     assert bench.bounded("boom", lambda: 1 / 0, 5.0)["error"].startswith("boom: ZeroDivisionError")
+
+
+def test_batched_algorithmic_bytes_hand_count():
+    """Path 0-1-2, sources 0 and 2 in one group: iteration 0 reads vertices
+    0 and 2 (4 B/entry + 24 B each: 28 + 28) and writes the row of vertex 1
+    (64); iteration 1 reads vertex 1 (8 + 24) and writes rows 0 and 2 (128);
+    iteration 2 reads vertices 0 and 2 (56)."""
+    torch = pytest.importorskip("torch")
+    import numpy as np
+    lv = torch.tensor([[0, 1, 2], [2, 1, 0]], dtype=torch.uint8)
+    assert bench.batched_algorithmic_bytes(torch, lv, np.array([1, 2, 1]), "cpu") == 56 + 64 + 32 + 128 + 56
+    # an unreached vertex (0xFF) costs nothing
+    lv2 = torch.tensor([[0, 1, 255]], dtype=torch.uint8)
+    assert bench.batched_algorithmic_bytes(torch, lv2, np.array([1, 1, 0]), "cpu") == 28 + 64 + 28
