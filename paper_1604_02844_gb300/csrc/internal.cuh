@@ -112,6 +112,7 @@ struct Graph {
 
     // batched (bit-parallel) workspace, allocated on first use
     void *batch_ws = nullptr;
+    int stream_priority = 0;  // of the batched workspace's stream (set by a server)
 
     Options opt;
     std::mutex mu;

@@ -456,7 +456,13 @@ __global__ void __launch_bounds__(MS_WPB * 32) ms_kernel(MsParams p)
         }
         __syncthreads();
         const unsigned nF = s_nF;
-        if (nF == 0) break;
+        if (nF == 0) {
+            // no frontier entry left: lanes whose last vertices have no
+            // out-edges may still carry an alive bit, but none of them can
+            // progress, so every lane is finished
+            if (blockIdx.x == 0 && tid == 0) c->alive[par] = 0ull;
+            break;
+        }
         if (blockIdx.x == 0 && tid == 0) {
             // parity par^1: last read before the previous barrier, next used
             // after the coming one
@@ -476,11 +482,14 @@ __global__ void __launch_bounds__(MS_WPB * 32) ms_kernel(MsParams p)
         __syncthreads();
         const bool pull = p.symmetric && s_minage >= 2 && (long long)ld_relaxed64(&c->fedges[par]) * 16 > p.m &&
                           (double)ld_relaxed64(&c->seen_pairs) >= 0.3 * (double)__popcll(live) * (double)p.n_nonzero;
-        if (!pull) {
-            ms_expand(p, par, nF, s_tbuf[threadIdx.x >> 5]);
-            ok = grid_sync(&c->bar_count, &c->bar_gen, &c->status, G, p.timeout_ns, &s_ok);
-            if (!ok) break;
-        }
+        if (!pull) ms_expand(p, par, nF, s_tbuf[threadIdx.x >> 5]);
+        // On both paths: block 0's reset of the parity par^1 counters above
+        // happens before any CTA appends to them (ms_update after a push
+        // expansion, ms_pull directly).  Without this barrier a pull step of a
+        // CTA running ahead of block 0 could have its frontier appends wiped,
+        // leaving lanes alive with an empty frontier.
+        ok = grid_sync(&c->bar_count, &c->bar_gen, &c->status, G, p.timeout_ns, &s_ok);
+        if (!ok) break;
         // this iteration's level byte per lane, packed four to a word
         if (tid < 16) {
             uint32_t w = 0;
@@ -648,7 +657,8 @@ int ms_alloc(Graph *g, MsWs **out)
     if ((e = cudaMalloc(&w->lane_row, 64 * 4)) != cudaSuccess) return bad(e, "cudaMalloc(lane rows)");
     if ((e = cudaMallocHost(&w->h_ctrl, sizeof(MsCtrl))) != cudaSuccess) return bad(e, "cudaMallocHost(ms ctrl)");
     if ((e = cudaMallocHost(&w->h_lanes, 2 * 64 * 4)) != cudaSuccess) return bad(e, "cudaMallocHost(lanes)");
-    if ((e = cudaStreamCreateWithFlags(&w->stream, cudaStreamNonBlocking)) != cudaSuccess) return bad(e, "cudaStreamCreate");
+    if ((e = cudaStreamCreateWithPriority(&w->stream, cudaStreamNonBlocking, g->stream_priority)) != cudaSuccess)
+        return bad(e, "cudaStreamCreate");
     g->batch_ws = w;
     const int rc = ms_reset(g);
     if (rc != BFS_OK) return rc;

@@ -169,6 +169,18 @@ int Server::ensure_ws(GraphState &gs)
 {
     if (gs.has_ws) return BFS_OK;
     const int64_t need = workspace_bytes(gs.g);
+    // smaller graphs (shorter searches) get higher stream priorities, so
+    // that their few CTAs are scheduled ahead of the large searches' ones
+    {
+        int least = 0, greatest = 0;
+        cudaDeviceGetStreamPriorityRange(&least, &greatest);
+        int rank = 0, count = 0;
+        for (auto &o : graphs) {
+            ++count;
+            if (o->g->m < gs.g->m || (o->g->m == gs.g->m && o.get() < &gs)) ++rank;
+        }
+        gs.g->stream_priority = count > 1 ? greatest + (least - greatest) * rank / (count - 1) : least;
+    }
     if (used + need > budget) {
         evict_idle(gs, need);
         if (used + need > budget) return BFS_NOT_READY;
@@ -307,11 +319,16 @@ int Server::round(GraphState &gs)
         if (rc != BFS_OK) return rc;
     }
     if (!running) return BFS_OK;
-    // the GPU's CTAs (of 256 threads) shared among the graphs with work; a
-    // graph set to 512-thread CTAs gets half as many
+    // the GPU's CTAs (of 256 threads) shared among the graphs with work, but
+    // no more than the graph's size calls for (one CTA per 2^16 adjacency
+    // entries), so that small graphs leave room for the large ones; a graph
+    // set to 512-thread CTAs gets half as many
     const int per_cta = gs.g->opt.batch_block == 512 ? 2 : 1;
-    const int share = std::max(gs.g->num_sms, total_ctas / std::max(1, active)) / per_cta;
+    const int needed = (int)std::min<int64_t>(std::max<int64_t>(1, (gs.g->m + 65535) / 65536), total_ctas);
+    const int share = std::max(1, std::min(needed, std::max(gs.g->num_sms, total_ctas / std::max(1, active))) / per_cta);
     gs.phase = PH_STEP;
+    const bool had_last = gs.have_last;
+    const unsigned iter_before = gs.last.iter;
     int rc = ms_step_capped(gs.g, iters_per_step, share);
     if (rc != BFS_OK) return rc;
     MsCtrl &st = gs.last;
@@ -319,6 +336,13 @@ int Server::round(GraphState &gs)
     rc = ms_read_ctrl(gs.g, &st);
     if (rc != BFS_OK) return rc;
     gs.have_last = true;
+    // Backstop: a step with live lanes always advances the iteration counter
+    // unless the search has no frontier left; lanes still marked alive then
+    // can never finish, so their queries end with an error instead of the
+    // worker relaunching empty searches forever.
+    if (had_last && !add && st.iter == iter_before && (running & st.alive[st.iter & 1]) &&
+        !(st.status & (ST_TIMEOUT | ST_OVERFLOW | ST_DEPTH)))
+        return set_error(BFS_ERR_CUDA, "server: a batched search made no progress with queries still running");
     gs.last_iter = (int64_t)st.iter;
     if (st.status & (ST_TIMEOUT | ST_OVERFLOW | ST_DEPTH))
         return set_error(st.status & ST_DEPTH ? BFS_ERR_DEPTH : (st.status & ST_TIMEOUT ? BFS_ERR_TIMEOUT : BFS_ERR_CUDA),
@@ -424,6 +448,7 @@ int bfs_server_destroy(bfs_server *sh)
             ms_free(gs->g);
             cudaFree(gs->d_stage);
         }
+        gs->g->stream_priority = 0;
         gs->g->servers.fetch_sub(1);  // the graph may be destroyed again
     }
     delete s;

@@ -26,6 +26,7 @@ std::atomic<int64_t> device_free{int64_t(1) << 40};
 std::atomic<int> pull_mode{0};
 std::atomic<int> timeout_graph_n{-1};
 std::atomic<int> never_finish_root{-1};
+std::atomic<int> stuck_root{-1};
 std::atomic<int> deep_root{-1};
 std::atomic<int> deep_depth{0};
 std::atomic<int> slow_graph_n{-1};
@@ -60,6 +61,12 @@ cudaError_t cudaGetDevice(int *d)
 cudaError_t cudaDeviceGetAttribute(int *v, cudaDeviceAttr a, int)
 {
     *v = a == cudaDevAttrMultiProcessorCount ? 4 : 0;
+    return cudaSuccess;
+}
+cudaError_t cudaDeviceGetStreamPriorityRange(int *least, int *greatest)
+{
+    *least = 0;
+    *greatest = -5;
     return cudaSuccess;
 }
 cudaError_t cudaMemGetInfo(size_t *free_b, size_t *total_b)
@@ -214,6 +221,9 @@ int ms_step_capped(Graph *g, uint32_t max_iters, int max_ctas)
         c.status |= ST_TIMEOUT;
         return BFS_OK;
     }
+    // a faulty search: a lane on stuck_root stays alive while no iteration runs
+    for (int i = 0; i < 64; ++i)
+        if (((c.alive[c.iter & 1] >> i) & 1ull) && f->lanes[i].root == fake::stuck_root.load()) return BFS_OK;
     for (uint32_t it = 0; it < max_iters; ++it) {
         const int par = (int)(c.iter & 1);
         if (!c.alive[par]) break;

@@ -15,6 +15,7 @@ extern std::atomic<int64_t> device_free;      // bytes cudaMalloc may still hand
 extern std::atomic<int> pull_mode;            // batches with all lanes >= 2 iterations old look heavy
 extern std::atomic<int> timeout_graph_n;      // steps of the graph with this n report ST_TIMEOUT
 extern std::atomic<int> never_finish_root;    // a lane on this root never ends, and reports nothing
+extern std::atomic<int> stuck_root;           // a lane on this root stays alive while steps run no iteration
 extern std::atomic<int> deep_root;            // a lane on this root runs deep_depth iterations
 extern std::atomic<int> deep_depth;
 extern std::atomic<int> slow_graph_n;         // steps of the graph with this n sleep slow_step_us

@@ -416,6 +416,20 @@ void join_record()
     CHECK(bfs_ticket_info(b.s, 0, &l) == BFS_ERR_INVALID_ARG);
 }
 
+// A search that keeps a lane alive while its steps run no iteration (a
+// lost frontier) makes the worker fail the queries instead of relaunching
+// empty searches forever.
+void no_progress()
+{
+    fake::stuck_root = 5;
+    Bench b({1000}, 0);
+    Query q;
+    q.root = 5;
+    CHECK(b.submit(q) == BFS_OK);
+    CHECK(bfs_server_drain(b.s) == BFS_ERR_CUDA);
+    CHECK(bfs_poll(b.s, q.ticket) == BFS_ERR_CUDA);
+}
+
 // A graph registered with a live server may not be released (its worker may
 // still search it): graph_release_check, the guard of bfs_graph_destroy,
 // refuses it with BFS_ERR_BUSY until every server holding it is destroyed.
@@ -461,6 +475,7 @@ int main(int argc, char **argv)
     else if (s == "stress") stress();
     else if (s == "registration") registration();
     else if (s == "join_record") join_record();
+    else if (s == "no_progress") no_progress();
     else {
         fprintf(stderr, "unknown scenario %s\n", s.c_str());
         return 2;

@@ -247,3 +247,30 @@ def test_continuous_batching_queries_join_a_running_search():
     ref = oracle.bfs_batch(ro, col, np.array([deep] + others, np.int32))
     for i, r in enumerate([deep] + others):
         np.testing.assert_array_equal(bufs[r], ref[i], err_msg=f"root {r}")
+
+
+def test_queries_ending_at_vertices_without_out_edges_complete():
+    """A directed graph whose searches end at vertices without out-edges (a
+    path into a sink, a star of sinks) and a root without edges: the last
+    layer of such a query adds no frontier entry, and the query must still
+    complete with the oracle's levels instead of waiting forever."""
+    src = list(range(0, 9)) + [10] * 10 + [30, 31]
+    dst = list(range(1, 10)) + list(range(11, 21)) + [31, 32]
+    n = 40
+    ro, col = graphgen.csr_from_tuples(n, np.array(src, np.int32), np.array(dst, np.int32), symmetrize=False)
+    roots = [0, 10, 21, 5, 30, 9]
+    with gb.Graph(ro, col) as g:
+        with gb.Server() as s:
+            gid = s.add_graph(g)
+            for rnd in range(2):  # alone, then all at once
+                bufs = [np.empty(n, np.uint8) for _ in roots]
+                if rnd == 0:
+                    for r, b in zip(roots, bufs):
+                        s.wait(s.submit(gid, r, b), timeout_s=30)
+                else:
+                    ts = [s.submit(gid, r, b) for r, b in zip(roots, bufs)]
+                    for t in ts:
+                        s.wait(t, timeout_s=30)
+                ref = oracle.bfs_batch(ro, col, np.array(roots, np.int32))
+                for i, r in enumerate(roots):
+                    np.testing.assert_array_equal(bufs[i], ref[i], err_msg=f"root {r}, round {rnd}")

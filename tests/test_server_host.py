@@ -13,7 +13,8 @@ loop through its C ABI and check that:
   workspace, and fails when none does;
 - the room limit holds;
 - device timeouts and depth overflows fail the queries instead of hanging;
-- the host backstop ends a lane that never finishes;
+- the host backstops end a lane that never finishes, and a search that
+  keeps lanes alive without running an iteration;
 - the pull-phase hold is kept;
 - a graph registered with a live server cannot be released;
 - a query submitted during another's search joins it, and its record
@@ -37,7 +38,7 @@ CSRC = os.path.join(ROOT, "paper_1604_02844_gb300", "csrc")
 HOST = os.path.join(HERE, "server_host")
 SCENARIOS = ["mixed", "tight_budget", "device_oom_wait", "device_oom_fail", "room_limit", "timeout",
              "depth_backstop", "kernel_depth", "pull_hold", "stress", "registration",
-             "join_record"]
+             "join_record", "no_progress"]
 
 
 def _cuda_include():
@@ -119,6 +120,8 @@ MUTANTS = [
      "    if (rc != BFS_OK) return BFS_NOT_READY;\n    gs.has_ws = true;", "device_oom_fail"),
     ("idle workspaces never given back",
      "        evict_idle(gs, need);\n", "", "tight_budget"),
+    ("no backstop for a search without progress",
+     "if (had_last && !add && st.iter == iter_before", "if (false && st.iter == iter_before", "no_progress"),
 ]
 
 
