@@ -99,7 +99,10 @@ typedef enum {
                                    (checked at creation) the in-edges come from a
                                    transposed CSR built on the first run in this mode
                                    (4(n+m) bytes); BLOCK 256 or 512; 2 bitmaps of
-                                   workspace, allocated on first use                   */
+                                   workspace, allocated on first use;
+                                   4 = as 0 with more, lighter warps (256-thread CTAs,
+                                   BLOCK ignored) that read each item's adjacency
+                                   straight from memory and claim at once             */
     BFS_OPT_ALPHA = 12,         /* mode 3: a layer runs bottom-up once the frontier's
                                    summed degree exceeds (edges of unreached vertices)
                                    / ALPHA (0 .. 2^30, default 14; 0 = never)          */

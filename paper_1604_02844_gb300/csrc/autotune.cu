@@ -135,9 +135,11 @@ extern "C" int bfs_graph_autotune(bfs_graph *gh, int what, int32_t samples)
         auto single = [&] { return time_single(gh, roots, d_level, d_parent, s, e0, e1); };
         if (what & BFS_TUNE_MODE) {
             // the fastest expansion whose results equal every other's: top-down
-            // (mode 0) or direction-optimising (mode 3); the atomic-free and the
-            // degree-binned modes are kept for comparison, not chosen
-            if ((rc = descend({{BFS_OPT_MODE, {MODE_WARP, MODE_HYBRID}}}, single)) != BFS_OK) return cleanup(rc);
+            // with staged items (mode 0) or thin warps (mode 4, faster on
+            // graphs without hubs), or direction-optimising (mode 3); the
+            // atomic-free and the degree-binned modes are kept for comparison
+            if ((rc = descend({{BFS_OPT_MODE, {MODE_WARP, MODE_HYBRID, MODE_THIN}}}, single)) != BFS_OK)
+                return cleanup(rc);
         }
         if (what & BFS_TUNE_SINGLE) {
             std::vector<Knob> knobs;
@@ -151,6 +153,8 @@ extern "C" int bfs_graph_autotune(bfs_graph *gh, int what, int32_t samples)
             case MODE_HYBRID:
                 knobs = {{BFS_OPT_ALPHA, {2, 4, 8, 14, 32, 64}}, {BFS_OPT_BETA, {4, 8, 24, 64, 256}},
                          {BFS_OPT_BLOCK, {256, 512}}};
+                break;
+            case MODE_THIN:  // its CTA size is fixed
                 break;
             default:
                 knobs = {{BFS_OPT_BLOCK, {256, 512}}};

@@ -312,9 +312,9 @@ int bfs_graph_set_option(bfs_graph *gh, int option, int64_t v)
         o.batch_block = (int)v;
         break;
     case BFS_OPT_MODE:
-        if (v != MODE_WARP && v != MODE_BINNED && v != MODE_RESTORE && v != MODE_HYBRID)
-            return bad("MODE must be 0 (warp units), 1 (degree-binned), 2 (restoration, no atomics) "
-                       "or 3 (direction-optimising)");
+        if (v != MODE_WARP && v != MODE_BINNED && v != MODE_RESTORE && v != MODE_HYBRID && v != MODE_THIN)
+            return bad("MODE must be 0 (warp units), 1 (degree-binned), 2 (restoration, no atomics), "
+                       "3 (direction-optimising) or 4 (thin warps)");
         o.mode = (int)v;
         break;
     case BFS_OPT_ALPHA:
@@ -392,6 +392,8 @@ int bfs_run(bfs_graph *gh, int32_t root, int32_t *level_out, int32_t *parent_out
         rc = alloc_hybrid(g);
         if (rc != BFS_OK) return rc;
         rc = td_warp_launch(g, root, d_level, d_parent, s, MODE_HYBRID);
+    } else if (g->opt.mode == MODE_THIN) {
+        rc = td_warp_launch(g, root, d_level, d_parent, s, MODE_THIN);
     } else {
         rc = td_warp_launch(g, root, d_level, d_parent, s);
     }

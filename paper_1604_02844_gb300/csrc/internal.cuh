@@ -52,7 +52,7 @@ struct Ctrl {
     unsigned layers;                 // layers of the last search
 };
 
-enum { MODE_WARP = 0, MODE_BINNED = 1, MODE_RESTORE = 2, MODE_HYBRID = 3 };
+enum { MODE_WARP = 0, MODE_BINNED = 1, MODE_RESTORE = 2, MODE_HYBRID = 3, MODE_THIN = 4 };
 
 struct Options {
     int block = 512;

@@ -60,7 +60,7 @@ namespace {
 
 using namespace dev;
 
-constexpr int W = 384;       // unit edge target and hub slice length
+constexpr int W = 320;       // unit edge target and hub slice length
 constexpr int MAXI = 2 * W;  // edges of one work item are < MAXI
 constexpr int OBW = 128;     // out-buffer entries per warp
 constexpr int UA = 12;       // pass A: visited-word loads per lane in flight
@@ -255,11 +255,10 @@ __device__ __forceinline__ int stage_item(WarpSmem &ws, const WParams &p, const 
 // caller's numbering), read each one's adjacency range, queue the short
 // ones as frontier entries cut into units and the hubs as slices.  All loads
 // of a lane are issued together, so one flush costs about one round trip.
-template <int FL>
-__device__ __forceinline__ void warp_flush(WarpSmem &ws, const WParams &p, int set_out, int qo, int c,
-                                        int next_level)
+template <int FL, typename S = WarpSmem, int OB = OBW>
+__device__ __forceinline__ void warp_flush(S &ws, const WParams &p, int set_out, int qo, int c, int next_level)
 {
-    constexpr int PER = OBW / 32;
+    constexpr int PER = OB / 32;
     const int lane = threadIdx.x & 31;
     const unsigned lt = lanemask_lt();
     __syncwarp();  // winners were written to ws.wv / ws.wu by other lanes
@@ -555,15 +554,15 @@ __device__ __forceinline__ void process_item_rst(WarpSmem &ws, const WParams &p,
 // whose bit another warp sets in the meantime simply loses its atomicOr.
 
 // Claim the deferred candidates cand.v/u[0..nb) and queue the winners.
-template <int KM>
-__device__ __forceinline__ void claim_deferred(WarpSmem &ws, const WParams &p, int &nb, int set_out, int qo,
-                                               int &ocnt, int next_level, unsigned &my_new)
+template <int KM, typename S = WarpSmem, int OB = OBW>
+__device__ __forceinline__ void claim_deferred(S &ws, const WParams &p, int &nb, int set_out, int qo, int &ocnt,
+                                               int next_level, unsigned &my_new)
 {
     constexpr int FL = KM == KM_HYBRID ? (FL_LP | FL_CNT) : FL_LP;
     const int lane = threadIdx.x & 31;
     const unsigned lt = lanemask_lt();
-    if (ocnt > OBW - CB) {  // room for every winner of this round
-        warp_flush<FL>(ws, p, set_out, qo, ocnt, next_level);
+    if (ocnt > OB - CB) {  // room for every winner of this round
+        warp_flush<FL, S, OB>(ws, p, set_out, qo, ocnt, next_level);
         ocnt = 0;
     }
     __syncwarp();  // the buffer was filled by other lanes
@@ -874,39 +873,54 @@ __device__ __forceinline__ void bottom_up(CtaSmem<WPB> &cs, const WParams &p, co
     __syncthreads();  // the shared buffers go back to the top-down layers
 }
 
-template <int WPB, int KM>
-__global__ void __launch_bounds__(WPB * 32, (24 / WPB) > 0 ? (24 / WPB) : 1) td_warp_kernel(WParams p)
+// a[0..n) = -1: 16-byte stores from the first 16-byte boundary of a (an
+// int32 array is 4-byte aligned), single stores before it and after the last.
+__device__ __forceinline__ void fill_minus1(int32_t *a, int64_t n, int64_t t0, int64_t stride)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    CtaSmem<WPB> &cs = *reinterpret_cast<CtaSmem<WPB> *>(smem_raw);
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    WarpSmem &ws = cs.w[warp];
-    const unsigned G = gridDim.x;
-    const unsigned GW = G * WPB;
-    const unsigned gw = blockIdx.x * WPB + warp;
+    const int64_t head = min(n, (int64_t)((16u - (unsigned)(reinterpret_cast<uintptr_t>(a) & 15u)) & 15u) / 4);
+    const int64_t nv = (n - head) / 4;
+    int4 *v = reinterpret_cast<int4 *>(a + head);
+    for (int64_t i = t0; i < nv; i += stride) v[i] = make_int4(-1, -1, -1, -1);
+    if (t0 < head) a[t0] = -1;
+    if (t0 < n - head - 4 * nv) a[head + 4 * nv + t0] = -1;
+}
+
+// The root is its own parent at level 0 (Alg. 1), written once the grid has
+// passed the barrier after the initialisation.
+__device__ __forceinline__ void td_root_outputs(const WParams &p)
+{
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        p.level[p.root] = 0;
+        if (p.parent) p.parent[p.root] = p.root;
+    }
+}
+
+// Initialisation (Alg. 1: P = infinity except P[s] = s; vis = {s}) and the
+// root as the first frontier (an entry, or hub slices), by the whole grid.
+template <int KM>
+__device__ __forceinline__ void td_init(const WParams &p, int rint)
+{
+    const int tid = threadIdx.x;
+    const unsigned nthr = blockDim.x;
     Ctrl *c = p.ctrl;
-    const uint64_t t_start = globaltimer();
-
-    const int rint = __ldg(p.perm + p.root);  // the root in internal numbering
-
-    // ---- initialisation (Alg. 1: P = infinity except P[s] = s; vis = {s}) --
     {
-        const int64_t stride = (int64_t)G * WPB * 32;
-        for (int64_t i = (int64_t)blockIdx.x * WPB * 32 + tid; i < p.n; i += stride) {
-            const bool is_root = (i == p.root);
-            p.level[i] = is_root ? 0 : -1;
-            if (p.parent) p.parent[i] = is_root ? p.root : -1;
-            if (KM == KM_RESTORE) p.pint[i] = (i == rint) ? rint : INT_MAX;  // Alg. 3: P = infinity, P[s] = s
-        }
+        const int64_t stride = (int64_t)gridDim.x * nthr;
+        // level and parent -1 everywhere (the root's entries are written
+        // after the first grid barrier), 16 bytes per store
+        fill_minus1(p.level, p.n, (int64_t)blockIdx.x * nthr + tid, stride);
+        if (p.parent) fill_minus1(p.parent, p.n, (int64_t)blockIdx.x * nthr + tid, stride);
+        if (KM == KM_RESTORE)
+            for (int64_t i = (int64_t)blockIdx.x * nthr + tid; i < p.n; i += stride)
+                p.pint[i] = (i == rint) ? rint : INT_MAX;  // Alg. 3: P = infinity, P[s] = s
         const int rw = rint >> 5;
-        for (int64_t w = (int64_t)blockIdx.x * WPB * 32 + tid; w < p.bitmap_words; w += stride) {
+        for (int64_t w = (int64_t)blockIdx.x * nthr + tid; w < p.bitmap_words; w += stride) {
             const uint32_t b0 = (w == rw) ? (1u << (rint & 31)) : 0u;
             p.bitmap[w] = b0;
             if (KM == KM_RESTORE) p.vo[w] = make_uint2(b0, 0u);
         }
         if (blockIdx.x == 0) {
             if (p.stats)
-                for (int i = tid; i < 4 * kMaxStatLayers; i += WPB * 32) p.stats[i] = 0;
+                for (int i = tid; i < 4 * kMaxStatLayers; i += (int)nthr) p.stats[i] = 0;
             if (tid == 0) {
                 const int rb = p.ro[rint], len = p.ro[rint + 1] - rb;
                 c->eu_count[0] = 0;
@@ -932,7 +946,48 @@ __global__ void __launch_bounds__(WPB * 32, (24 / WPB) > 0 ? (24 / WPB) : 1) td_
             }
         }
     }
+}
+
+// Leaving the kernel: the last CTA out returns the control block to zero.
+__device__ __forceinline__ void td_exit(Ctrl *c)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned old = atomicAdd(&c->exit_count, 1u);
+        if (old == gridDim.x - 1) {
+            for (int j = 0; j < 3; ++j) {
+                c->eu_count[j] = 0;
+                c->hub_count[j] = 0;
+                c->work[j] = 0;
+                c->nf[j] = 0;
+                c->mf[j] = 0;
+            }
+            c->bar_count = 0;
+            c->exit_count = 0;
+            __threadfence();
+        }
+    }
+}
+
+template <int WPB, int KM>
+__global__ void __launch_bounds__(WPB * 32, (24 / WPB) > 0 ? (24 / WPB) : 1) td_warp_kernel(WParams p)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    CtaSmem<WPB> &cs = *reinterpret_cast<CtaSmem<WPB> *>(smem_raw);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    WarpSmem &ws = cs.w[warp];
+    const unsigned G = gridDim.x;
+    const unsigned GW = G * WPB;
+    const unsigned gw = blockIdx.x * WPB + warp;
+    Ctrl *c = p.ctrl;
+    const uint64_t t_start = globaltimer();
+
+    const int rint = __ldg(p.perm + p.root);  // the root in internal numbering
+
+    td_init<KM>(p, rint);
     bool ok = grid_sync(&c->bar_count, &c->bar_gen, &c->status, G, p.timeout_ns, &cs.ok);
+    td_root_outputs(p);
 
     bool bu_prev = false;               // mode 3: the previous layer ran bottom-up
     unsigned long long m_seen = 0;      // mode 3: summed degrees of the vertices reached
@@ -1148,23 +1203,229 @@ __global__ void __launch_bounds__(WPB * 32, (24 / WPB) > 0 ? (24 / WPB) : 1) td_
         bu_prev = bu;
     }
 
-    __syncthreads();
-    if (tid == 0) {
-        __threadfence();
-        const unsigned old = atomicAdd(&c->exit_count, 1u);
-        if (old == G - 1) {
-            for (int j = 0; j < 3; ++j) {
-                c->eu_count[j] = 0;
-                c->hub_count[j] = 0;
-                c->work[j] = 0;
-                c->nf[j] = 0;
-                c->mf[j] = 0;
+    td_exit(c);
+}
+
+// ---- mode 0: thin warps --------------------------------------------------
+//
+// The same layer step with more, lighter warps (8 per CTA, 4 CTAs per SM,
+// at most 64 registers) and no staging: a warp reads its item's adjacency
+// straight from global memory, 32 consecutive entries of the flattened lists
+// per step (lane -> list by two ballots, as in the staging copy), TU steps
+// in flight, bypassing L1; tests the visited words through L1 (which keeps
+// about 180 KB for them, the shared memory per warp being only the winners'
+// flush buffer); claims each candidate at once with atomicOr; and queues the
+// winners, whose sources come from the same lane -> list mapping.
+
+constexpr int TOB = 64;  // winners buffered per warp before a flush
+constexpr int TU = 4;    // 32-entry steps in flight per warp
+
+struct ThinWarpSmem {
+    int32_t wv[TOB], wu[TOB];             // claimed vertices and their sources (internal ids)
+    int32_t ou[TOB], ob[TOB], ol[TOB];    // flush: the new frontier entries
+    int32_t ust[TOB];                     // flush: unit starts
+};
+
+template <int WPB>
+struct ThinCtaSmem {
+    ThinWarpSmem w[WPB];
+    int ok;
+    unsigned nU, nH;
+    unsigned long long st[3];
+};
+
+// Adjacency entry read once: not kept in L1, which holds visited words.
+__device__ __forceinline__ int ld_col(const int32_t *q)
+{
+    int v;
+    asm volatile("ld.global.nc.L1::no_allocate.s32 %0, [%1];" : "=r"(v) : "l"(q));
+    return v;
+}
+
+// One work item: every entry of its lists tested, candidates claimed at
+// once, the winners queued (flushed whenever the buffer could overflow).
+__device__ __forceinline__ void thin_item(ThinWarpSmem &ws, const WParams &p, const Item &it_in, int set_out, int qo,
+                                          int next_level, int &ocnt, unsigned &my_new, unsigned long long &my_edges)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = lanemask_lt();
+    Item it = it_in;
+    if (it.l < 0 || it.l > MAXI) {  // cannot happen for entries this kernel wrote
+        atomicOr(&p.ctrl->status, ST_OVERFLOW);
+        it.l = 0;
+    }
+    const bool has = lane < it.cnt && it.l > 0;
+    int inc = has ? it.l : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(FULL, inc, o);
+        if (lane >= o) inc += y;
+    }
+    int et = __shfl_sync(FULL, inc, 31);
+    if (et >= MAXI) {  // cannot happen: units < 2W edges, slices <= W
+        if (lane == 0) atomicOr(&p.ctrl->status, ST_OVERFLOW);
+        et = 0;
+    }
+    const int off = inc - (has ? it.l : 0);
+    if (lane == 0) my_edges += (unsigned long long)et;
+    const bool single = it.cnt == 1;  // a hub slice or a one-list unit
+    const int b1 = __shfl_sync(FULL, it.b, 0), u1 = __shfl_sync(FULL, it.u, 0);
+    for (int g0 = 0; g0 < et; g0 += 32 * TU) {
+        int v[TU], u[TU];
+#pragma unroll
+        for (int s = 0; s < TU; ++s) {
+            const int e0 = g0 + 32 * s, e = e0 + lane;
+            int jb = b1, jo = 0;
+            u[s] = u1;
+            if (!single) {  // lane -> the last list starting at or before e
+                const unsigned starts =
+                    __reduce_or_sync(FULL, (has && off > e0 && off < e0 + 32) ? 1u << (off - e0) : 0u);
+                const int j0 = __popc(__ballot_sync(FULL, has && off <= e0)) - 1;
+                const int jj = (j0 + __popc(starts & ((2u << lane) - 1u))) & 31;
+                jb = __shfl_sync(FULL, it.b, jj);
+                jo = __shfl_sync(FULL, off, jj);
+                u[s] = __shfl_sync(FULL, it.u, jj);
             }
-            c->bar_count = 0;
-            c->exit_count = 0;
-            __threadfence();
+            v[s] = e < et ? ld_col(p.col + jb + (e - jo)) : -1;
+        }
+        unsigned w[TU];
+#pragma unroll
+        for (int s = 0; s < TU; ++s) w[s] = v[s] >= 0 ? __ldca(p.bitmap + ((unsigned)v[s] >> 5)) : 0xffffffffu;
+        bool win[TU];
+#pragma unroll
+        for (int s = 0; s < TU; ++s) {
+            win[s] = false;
+            if (v[s] >= 0 && !((w[s] >> (v[s] & 31)) & 1u)) {
+                const unsigned bit = 1u << (v[s] & 31);
+                win[s] = !(atomicOr(p.bitmap + ((unsigned)v[s] >> 5), bit) & bit);
+            }
+        }
+#pragma unroll
+        for (int s = 0; s < TU; ++s) {
+            const unsigned m = __ballot_sync(FULL, win[s]);
+            if (!m) continue;
+            if (ocnt + __popc(m) > TOB) {
+                warp_flush<FL_LP, ThinWarpSmem, TOB>(ws, p, set_out, qo, ocnt, next_level);
+                ocnt = 0;
+            }
+            if (win[s]) {
+                const int pos = ocnt + __popc(m & lt);
+                ws.wv[pos] = v[s];
+                ws.wu[pos] = u[s];
+                ++my_new;
+            }
+            ocnt += __popc(m);
         }
     }
+}
+
+template <int WPB>
+__global__ void __launch_bounds__(WPB * 32, 32 / WPB) td_thin_kernel(WParams p)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    ThinCtaSmem<WPB> &cs = *reinterpret_cast<ThinCtaSmem<WPB> *>(smem_raw);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    ThinWarpSmem &ws = cs.w[warp];
+    const unsigned G = gridDim.x;
+    const unsigned GW = G * WPB;
+    const unsigned gw = blockIdx.x * WPB + warp;
+    Ctrl *c = p.ctrl;
+    const uint64_t t_start = globaltimer();
+    const int rint = __ldg(p.perm + p.root);
+    td_init<KM_ATOMIC>(p, rint);
+    bool ok = grid_sync(&c->bar_count, &c->bar_gen, &c->status, G, p.timeout_ns, &cs.ok);
+    td_root_outputs(p);
+    for (int d = 0; ok; ++d) {
+        const int set_in = d % 3, set_out = (d + 1) % 3, set_rst = (d + 2) % 3;
+        const int qi = d & 1, qo = qi ^ 1;
+        if (tid == 0) {
+            const unsigned long long eu = ld_relaxed64(&c->eu_count[set_in]);
+            cs.nU = min((unsigned)(eu >> 32), p.ucap);
+            cs.nH = min(ld_relaxed(&c->hub_count[set_in]), p.hcap);
+            if (p.stats) cs.st[0] = cs.st[1] = cs.st[2] = 0;
+        }
+        __syncthreads();
+        const unsigned nH = cs.nH;
+        // few items: hub slices are dealt in up to 12 parts so that more warps share them
+        const unsigned split = (cs.nU + nH > 0 && cs.nU + nH < GW / 2) ? min(12u, GW / (cs.nU + nH)) : 1u;
+        const unsigned n_items = cs.nU + nH * split;
+        if (n_items == 0) {
+            if (blockIdx.x == 0 && tid == 0) c->layers = (unsigned)d;
+            break;
+        }
+        if (blockIdx.x == 0 && tid == 0) {
+            c->eu_count[set_rst] = 0;
+            c->hub_count[set_rst] = 0;
+        }
+        const int next_level = d + 1;
+        int ocnt = 0;
+        unsigned my_new = 0;
+        unsigned long long my_vertices = 0, my_edges = 0;
+        // items gw, gw + GW, ...; the next item's descriptor and entries in flight
+        unsigned id = gw;
+        Desc d0 = load_desc(p, qi, nH, n_items, id, split);
+        Item cur = load_item(p, qi, d0, id < n_items, split);
+        Desc d1 = load_desc(p, qi, nH, n_items, id + GW, split);
+        while (id < n_items) {
+            const Item nxt = load_item(p, qi, d1, id + GW < n_items, split);
+            const Desc d2 = load_desc(p, qi, nH, n_items, id + 2 * GW, split);
+            if (p.stats && lane == 0)
+                my_vertices += (d0.c < 0) ? (cur.b == __ldg(p.ro + cur.u) ? 1 : 0) : (unsigned)cur.cnt;
+            thin_item(ws, p, cur, set_out, qo, next_level, ocnt, my_new, my_edges);
+            id += GW;
+            cur = nxt;
+            d0 = d1;
+            d1 = d2;
+        }
+        if (ocnt > 0) warp_flush<FL_LP, ThinWarpSmem, TOB>(ws, p, set_out, qo, ocnt, next_level);
+        if (p.stats && d < kMaxStatLayers) {
+            unsigned long long a = my_vertices, e = my_edges, t = my_new;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                a += __shfl_down_sync(FULL, a, o);
+                e += __shfl_down_sync(FULL, e, o);
+                t += __shfl_down_sync(FULL, t, o);
+            }
+            if (lane == 0) {
+                atomicAdd(&cs.st[0], a);
+                atomicAdd(&cs.st[1], e);
+                atomicAdd(&cs.st[2], t);
+            }
+            __syncthreads();
+            if (tid == 0) {
+                atomicAdd((unsigned long long *)&p.stats[4 * d + 0], cs.st[0]);
+                atomicAdd((unsigned long long *)&p.stats[4 * d + 1], cs.st[1]);
+                atomicAdd((unsigned long long *)&p.stats[4 * d + 2], cs.st[2]);
+            }
+        }
+        ok = grid_sync(&c->bar_count, &c->bar_gen, &c->status, G, p.timeout_ns, &cs.ok);
+        if (p.stats && d < kMaxStatLayers && blockIdx.x == 0 && tid == 0)
+            p.stats[4 * d + 3] = (int64_t)(globaltimer() - t_start);
+    }
+    td_exit(c);
+}
+
+template <int WPB>
+int launch_thin(Graph *g, const WParams &prm, cudaStream_t s)
+{
+    auto kern = td_thin_kernel<WPB>;
+    const int smem = (int)sizeof(ThinCtaSmem<WPB>);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute(td_thin_kernel)");
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, WPB * 32, smem);
+    if (e != cudaSuccess) return cuda_error(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor(td_thin_kernel)");
+    if (per_sm < 1) return set_error(BFS_ERR_CUDA, "td_thin_kernel: no CTA fits on an SM");
+    per_sm = std::min(per_sm, 32 / WPB);  // up to 32 warps per SM
+    if (g->opt.ctas_per_sm > 0) per_sm = std::min(per_sm, g->opt.ctas_per_sm);
+    int grid = per_sm * g->num_sms;
+    if (g->opt.max_ctas > 0) grid = std::min(grid, g->opt.max_ctas);
+    WParams p = prm;
+    void *args[] = {&p};
+    e = cudaLaunchCooperativeKernel((const void *)kern, dim3(grid), dim3(WPB * 32), args, (size_t)smem, s);
+    if (e != cudaSuccess) return cuda_error(e, "cudaLaunchCooperativeKernel(td_thin_kernel)");
+    g->last_grid = grid;
+    return BFS_OK;
 }
 
 template <int WPB, int KM>
@@ -1241,6 +1502,7 @@ int td_warp_launch(Graph *g, int32_t root, int32_t *level, int32_t *parent, cuda
     p.hcap = (uint32_t)std::min<int64_t>(g->hcap, 0x7FFFFFFFLL);
     p.bitmap_words = (int32_t)g->bitmap_words;
     p.timeout_ns = (uint64_t)g->opt.timeout_ns;
+    if (mode == MODE_THIN) return launch_thin<8>(g, p, s);
     switch (g->opt.block) {
     case 256:
         return restore ? launch<8, KM_RESTORE>(g, p, s)

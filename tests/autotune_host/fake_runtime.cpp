@@ -42,6 +42,7 @@ double single_cost(const gbbfs::Options &o)
         break;
     case 3: t = (cost_model == 1 ? 6.0 : 12.0) + 0.5 * std::fabs(l2(o.alpha) - 3) + 0.3 * std::fabs(l2(o.beta) - 6);
         break;
+    case 4: t = cost_model == 2 ? 7.0 : 13.0; break;
     default: t = 30.0;
     }
     return t + (o.block == 512 ? 1.0 : 0.0);

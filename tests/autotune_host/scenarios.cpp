@@ -74,6 +74,16 @@ void mode_stays()
     CHECK(g->opt.mode == 0 && g->opt.block == 256);
 }
 
+// On a graph where the thin-warp expansion is fastest it is chosen, and
+// its options are left as they were.
+void mode_thin()
+{
+    fake::cost_model = 2;
+    Graph *g = make_graph();
+    CHECK(bfs_graph_autotune(H(g), BFS_TUNE_MODE | BFS_TUNE_SINGLE, 4) == BFS_OK);
+    CHECK(g->opt.mode == 4 && g->opt.block == 512);
+}
+
 // The degree-binned mode tunes its three thresholds.
 void binned()
 {
@@ -175,6 +185,7 @@ int main(int argc, char **argv)
     const std::string s = argv[1];
     if (s == "single_mode0") single_mode0();
     else if (s == "mode_then_single") mode_then_single();
+    else if (s == "mode_thin") mode_thin();
     else if (s == "mode_stays") mode_stays();
     else if (s == "binned") binned();
     else if (s == "rejected_value") rejected_value();

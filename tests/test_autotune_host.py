@@ -20,7 +20,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(ROOT, "paper_1604_02844_gb300", "csrc")
 HOST = os.path.join(HERE, "autotune_host")
-SCENARIOS = ["single_mode0", "mode_then_single", "mode_stays", "binned", "rejected_value", "failing_value",
+SCENARIOS = ["single_mode0", "mode_then_single", "mode_thin", "mode_stays", "binned", "rejected_value", "failing_value",
              "all_fail", "late_failure", "batch", "args", "samples"]
 
 

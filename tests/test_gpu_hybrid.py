@@ -237,7 +237,7 @@ def test_option_errors_and_timeout_recovery():
     ro, col = graphgen.kronecker(14, 16, 12)
     r = int(graphgen.pick_roots(ro, 1, 12)[0])
     with gb.Graph(ro, col, mode=HYB) as g:
-        for name, val in (("alpha", -1), ("beta", 0), ("alpha", (1 << 30) + 1), ("mode", 4)):
+        for name, val in (("alpha", -1), ("beta", 0), ("alpha", (1 << 30) + 1), ("mode", 5)):
             with pytest.raises(gb.BfsError):
                 g.set_option(name, val)
         assert g.get_option("alpha") == 14 and g.get_option("beta") == 24

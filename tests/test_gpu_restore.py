@@ -131,7 +131,7 @@ def test_ragged_sizes_empty_and_isolated():
 
 
 def test_units_boundaries():
-    T = 384
+    T = 320
     degs = [1, 2, 31, 32, 33, T - 1, T, T + 1, 2 * T - 1, 2 * T, 2 * T + 1, 5 * T + 3]
     edges, nxt = [], 1 + len(degs)
     for i, dgr in enumerate(degs):

@@ -100,7 +100,7 @@ def test_units_boundaries():
     """Degrees around the unit target T = 2*BLOCK and the hub slice length:
     a root whose neighbours have degrees T-1, T, T+1, 2T, 2T+1, ... exercises
     unit cutting, hub slicing and the last partial slice."""
-    for mode, block, T in ((0, 256, 384), (0, 512, 384), (1, 512, 1024)):
+    for mode, block, T in ((0, 256, 320), (0, 512, 320), (1, 512, 1024)):
         degs = [1, 2, 31, 32, 33, T - 1, T, T + 1, 2 * T - 1, 2 * T, 2 * T + 1, 5 * T + 3]
         edges, nxt = [], 1 + len(degs)
         for i, dgr in enumerate(degs):
