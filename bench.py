@@ -292,13 +292,15 @@ def run_reference(args):
 def ablation_measurement(g, gb, torch, roots, mcc, checks, level, parent, flush, stream):
     """The same searches through the other expansion modes of bfs_run: mode 3,
     direction-optimising (bottom-up layers where the frontier is large); mode
-    2, the atomic-free variant of Alg. 3 (racy output bitmap, restoration pass
-    per layer); mode 1, one item per frontier vertex binned by degree.
+    4, thin warps (adjacency read straight from memory, immediate claims);
+    mode 2, the atomic-free variant of Alg. 3 (racy output bitmap,
+    restoration pass per layer); mode 1, one item per frontier vertex binned
+    by degree.
     CUDA events around each search, L2 flushed in between; every search's
     levels are checked against the atomic path's (count reached, sum)."""
     base_mode = g.get_option("mode")
     out = {}
-    for mode, name in ((3, "direction_optimising"), (2, "restoration_alg3"), (1, "degree_binned")):
+    for mode, name in ((3, "direction_optimising"), (4, "thin_warps"), (2, "restoration_alg3"), (1, "degree_binned")):
         g.set_option("mode", mode)
         for r in roots[:4]:
             gb.bfs_run(g.handle, int(r), level, parent, stream)

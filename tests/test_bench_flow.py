@@ -44,7 +44,7 @@ def _check_contract(line):
     assert e2e["h2d_bytes_per_step"] > 0 and e2e["d2h_bytes_per_step"] > 0
     assert line["gpu_launches"] == 64
     assert set(line["clocks"]) >= {"sm_mhz", "sm_max_mhz", "reasons"}
-    assert len(line["ablation"]) == 3 and all("error" not in v for v in line["ablation"].values())
+    assert len(line["ablation"]) == 4 and all("error" not in v for v in line["ablation"].values())
     assert line["batched"]["queries_per_s"] > 0 and line["batched"]["uneven_mix"]["queries_per_s"] > 0
     lp = line["layer_profile"]
     assert "error" not in lp and lp["roots"] == 64 and lp["layers"][0]["d"] == 0
