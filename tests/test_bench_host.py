@@ -316,3 +316,12 @@ def test_batched_algorithmic_bytes_hand_count():
     # an unreached vertex (0xFF) costs nothing
     lv2 = torch.tensor([[0, 1, 255]], dtype=torch.uint8)
     assert bench.batched_algorithmic_bytes(torch, lv2, np.array([1, 1, 0]), "cpu") == 28 + 64 + 28
+
+
+def test_largest_component_stats():
+    # roots 1 and 2 in the largest component (100 edges), root 3 in a 1-edge component
+    mcc = {1: 100.0, 2: 100.0, 3: 1.0}
+    runs = [(1, 1e-9), (2, 2e-9), (3, 1e-9)]
+    st = bench.largest_component_stats(runs, mcc)
+    assert st["roots_outside_largest_component"] == 1
+    assert st["hm_gteps_largest_component"] == pytest.approx(bench.harmonic_mean([100.0, 50.0]))
