@@ -312,42 +312,67 @@ __device__ __forceinline__ void warp_flush(S &ws, const WParams &p, int set_out,
             atomicAdd(&p.ctrl->mf[set_out], (unsigned long long)esum);
         }
     }
-    unsigned hbase = 0;
-    if (lane == 0 && total_slices > 0) hbase = atomicAdd(&p.ctrl->hub_count[set_out], (unsigned)total_slices);
-    hbase = __shfl_sync(FULL, hbase, 0);
+    // the short entries into the flush buffer (their positions need no reservation)
     {
         int spos = sinc - nsmall;
-        unsigned hpos = hbase + (unsigned)(hinc - nslice);
 #pragma unroll
         for (int k = 0; k < PER; ++k) {
             const int i = i0 + k;
-            if (i < i1) {
-                const int len = re[k] - rb[k];
-                if (len >= 1 && len <= W) {
-                    ws.ou[spos] = ws.wv[i];
-                    ws.ob[spos] = rb[k];
-                    ws.ol[spos] = len;
-                    ++spos;
-                } else if (len > W) {
-                    const int nseg = (len + W - 1) / W;
-                    if (nseg <= 8) {  // a few slices: this lane writes them
-                        for (int sg = 0; sg < nseg; ++sg, ++hpos) {
-                            if (hpos < p.hcap) {
-                                p.hu[qo][hpos] = ws.wv[i];
-                                p.hb[qo][hpos] = rb[k] + sg * W;
-                                p.hl[qo][hpos] = min(W, len - sg * W);
-                            } else {
-                                atomicOr(&p.ctrl->status, ST_OVERFLOW);
-                            }
-                        }
-                    } else {
-                        hpos += (unsigned)nseg;
-                    }
-                }
+            const int len = (i < i1) ? re[k] - rb[k] : 0;
+            if (len >= 1 && len <= W) {
+                ws.ou[spos] = ws.wv[i];
+                ws.ob[spos] = rb[k];
+                ws.ol[spos] = len;
+                ++spos;
             }
         }
     }
-    // large hubs: the whole warp writes their slices
+    __syncwarp();
+    // cut the short entries into units (<= 32 entries, a new unit where the
+    // running edge count crosses a multiple of W)
+    const int j0 = min(lane * PER, cs), j1 = min(j0 + PER, cs);
+    int units = 0, uinc = 0, nu = 0;
+    if (cs > 0) {
+        int sum = 0;
+        for (int j = j0; j < j1; ++j) sum += ws.ol[j];
+        int inc = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(FULL, inc, o);
+            if (lane >= o) inc += y;
+        }
+        const int toff = inc - sum;
+        {
+            int off = toff;
+            for (int j = j0; j < j1; ++j) {
+                const bool start = (j % 32 == 0) || (off / W != (off - ws.ol[j - 1]) / W);
+                nu += start;
+                off += ws.ol[j];
+            }
+        }
+        uinc = nu;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(FULL, uinc, o);
+            if (lane >= o) uinc += y;
+        }
+        units = __shfl_sync(FULL, uinc, 31);
+        int k = uinc - nu, off = toff;
+        for (int j = j0; j < j1; ++j) {
+            const bool start = (j % 32 == 0) || (off / W != (off - ws.ol[j - 1]) / W);
+            if (start) ws.ust[k++] = j;
+            off += ws.ol[j];
+        }
+    }
+    // both reservations in one round trip: hub slices (lane 0), entries and units (lane 1)
+    unsigned hbase = 0;
+    unsigned long long base = 0;
+    if (lane == 0 && total_slices > 0) hbase = atomicAdd(&p.ctrl->hub_count[set_out], (unsigned)total_slices);
+    if (lane == 1 && cs > 0)
+        base = atomicAdd(&p.ctrl->eu_count[set_out], ((unsigned long long)units << 32) | (unsigned long long)cs);
+    hbase = __shfl_sync(FULL, hbase, 0);
+    base = __shfl_sync(FULL, base, 1);
+    // hub slices: a few per vertex by its own lane, the large hubs by the whole warp
     {
         unsigned hpos = hbase + (unsigned)(hinc - nslice);
         int big_v[PER], big_b[PER], big_l[PER];
@@ -356,11 +381,24 @@ __device__ __forceinline__ void warp_flush(S &ws, const WParams &p, int set_out,
         for (int k = 0; k < PER; ++k) {
             const int i = i0 + k;
             const int len = (i < i1) ? re[k] - rb[k] : 0;
-            big_l[k] = (len > W && (len + W - 1) / W > 8) ? len : 0;
+            const int nseg = len > W ? (len + W - 1) / W : 0;
+            big_l[k] = nseg > 8 ? len : 0;
             big_v[k] = (i < i1) ? ws.wv[i] : 0;
             big_b[k] = (i < i1) ? rb[k] : 0;
             big_at[k] = hpos;
-            if (len > W) hpos += (unsigned)((len + W - 1) / W);
+            if (nseg > 0 && nseg <= 8) {
+                for (int sg = 0; sg < nseg; ++sg) {
+                    const unsigned g = hpos + (unsigned)sg;
+                    if (g < p.hcap) {
+                        p.hu[qo][g] = big_v[k];
+                        p.hb[qo][g] = rb[k] + sg * W;
+                        p.hl[qo][g] = min(W, len - sg * W);
+                    } else {
+                        atomicOr(&p.ctrl->status, ST_OVERFLOW);
+                    }
+                }
+            }
+            hpos += (unsigned)nseg;
         }
 #pragma unroll
         for (int k = 0; k < PER; ++k) {
@@ -386,69 +424,29 @@ __device__ __forceinline__ void warp_flush(S &ws, const WParams &p, int set_out,
             }
         }
     }
-    __syncwarp();
-    if (cs == 0) return;
-    // cut the short entries into units (<= 32 entries, a new unit where the
-    // running edge count crosses a multiple of W)
-    const int j0 = min(lane * PER, cs), j1 = min(j0 + PER, cs);
-    int sum = 0;
-    for (int j = j0; j < j1; ++j) sum += ws.ol[j];
-    int inc = sum;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(FULL, inc, o);
-        if (lane >= o) inc += y;
-    }
-    const int toff = inc - sum;
-    int nu = 0;
-    {
-        int off = toff;
-        for (int j = j0; j < j1; ++j) {
-            const bool start = (j % 32 == 0) || (off / W != (off - ws.ol[j - 1]) / W);
-            nu += start;
-            off += ws.ol[j];
+    if (cs > 0) {
+        const unsigned ebase = (unsigned)(base & 0xffffffffull), ubase = (unsigned)(base >> 32);
+        __syncwarp();  // ust was written by other lanes
+        for (int j = lane; j < cs; j += 32) {
+            const unsigned gi = ebase + (unsigned)j;
+            if (gi < p.ecap) {
+                p.eu[qo][gi] = ws.ou[j];
+                p.eb[qo][gi] = ws.ob[j];
+                p.el[qo][gi] = ws.ol[j];
+            } else {
+                atomicOr(&p.ctrl->status, ST_OVERFLOW);
+            }
         }
-    }
-    int uinc = nu;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(FULL, uinc, o);
-        if (lane >= o) uinc += y;
-    }
-    const int units = __shfl_sync(FULL, uinc, 31);
-    unsigned long long base = 0;
-    if (lane == 0)
-        base = atomicAdd(&p.ctrl->eu_count[set_out], ((unsigned long long)units << 32) | (unsigned long long)cs);
-    base = __shfl_sync(FULL, base, 0);
-    const unsigned ebase = (unsigned)(base & 0xffffffffull), ubase = (unsigned)(base >> 32);
-    {
-        int k = uinc - nu, off = toff;
-        for (int j = j0; j < j1; ++j) {
-            const bool start = (j % 32 == 0) || (off / W != (off - ws.ol[j - 1]) / W);
-            if (start) ws.ust[k++] = j;
-            off += ws.ol[j];
-        }
-    }
-    __syncwarp();
-    for (int j = lane; j < cs; j += 32) {
-        const unsigned gi = ebase + (unsigned)j;
-        if (gi < p.ecap) {
-            p.eu[qo][gi] = ws.ou[j];
-            p.eb[qo][gi] = ws.ob[j];
-            p.el[qo][gi] = ws.ol[j];
-        } else {
-            atomicOr(&p.ctrl->status, ST_OVERFLOW);
-        }
-    }
-    for (int k = lane; k < units; k += 32) {
-        const int s0 = ws.ust[k];
-        const int e0 = (k + 1 < units) ? ws.ust[k + 1] : cs;
-        const unsigned gk = ubase + (unsigned)k;
-        if (gk < p.ucap) {
-            p.us[qo][gk] = (int32_t)(ebase + (unsigned)s0);
-            p.uc[qo][gk] = e0 - s0;
-        } else {
-            atomicOr(&p.ctrl->status, ST_OVERFLOW);
+        for (int k = lane; k < units; k += 32) {
+            const int s0 = ws.ust[k];
+            const int e0 = (k + 1 < units) ? ws.ust[k + 1] : cs;
+            const unsigned gk = ubase + (unsigned)k;
+            if (gk < p.ucap) {
+                p.us[qo][gk] = (int32_t)(ebase + (unsigned)s0);
+                p.uc[qo][gk] = e0 - s0;
+            } else {
+                atomicOr(&p.ctrl->status, ST_OVERFLOW);
+            }
         }
     }
     (void)lt;
