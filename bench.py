@@ -703,11 +703,16 @@ def serving_stats(recs, scales):
 
 
 def find_knee(points, tol=0.05):
-    """The sustainable rate: the highest offered rate whose steady served
-    rate is within tol of it (None if no point is)."""
-    ok = [p["offered_qps"] for p in points
-          if p.get("steady_served_qps") and p["steady_served_qps"] >= (1.0 - tol) * p["offered_qps"]]
-    return max(ok) if ok else None
+    """The sustainable rate: the highest offered rate such that it and every
+    lower swept rate are served within tol (the steady served rate at least
+    (1 - tol) x offered); None if the lowest is not."""
+    knee = None
+    for p in sorted(points, key=lambda q: q["offered_qps"]):
+        served = p.get("steady_served_qps")
+        if not served or served < (1.0 - tol) * p["offered_qps"]:
+            break
+        knee = p["offered_qps"]
+    return knee
 
 
 def serving_measurement(args, gb, torch, dev):
@@ -882,7 +887,7 @@ def serving_measurement(args, gb, torch, dev):
            "plain_p99_ms": None if plain_error else float(np.percentile(plat, 99) * 1e3),
            "how": "bfs_submit/bfs_poll (64-lane continuous batching, uint8 levels to pinned host buffers); "
                   "latency and its split from the library's ticket records (bfs_ticket_info); sustainable "
-                  "rate = highest swept offered rate whose steady served rate is within 5 %; headline at "
+                  "rate = highest swept offered rate that it and every lower one are served within 5 %; headline at "
                   "0.7 x that rate; plain = bfs_run + sync per query, int32 levels to pinned host memory, "
                   "back to back"}
     if stalls:

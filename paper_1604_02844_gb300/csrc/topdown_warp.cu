@@ -193,12 +193,12 @@ __device__ __forceinline__ Item load_item(const WParams &p, int qi, const Desc &
 }
 
 // Prefix-sum the item's lengths into off[buf], record vertices, and issue the
-// cp.async copies of its adjacency into stage[buf].  Lists of >= 32 edges
-// are copied by the whole warp striding over each (coalesced); a list of
-// < 32 edges is copied by its own lane, one edge per step (as many steps as
-// the longest short list; a search over the flattened lists costs more
-// instructions than it saves).  Commits one group per lane.  Returns the
-// item's edge count (uniform).
+// cp.async copies of its adjacency into stage[buf].  An item of >= 4 lists
+// is copied as one flattened range, 32 consecutive slots per step (lanes find
+// their list by ballots), so that its lists are copied side by side; an item
+// of fewer lists list by list: a list of >= 32 edges by the whole warp
+// striding over it, a shorter one by its own lane, one edge per step.
+// Commits one group per lane.  Returns the item's edge count (uniform).
 __device__ __forceinline__ int stage_item(WarpSmem &ws, const WParams &p, const Item &it_in, int buf, int rint)
 {
     const int lane = threadIdx.x & 31;
@@ -227,7 +227,24 @@ __device__ __forceinline__ int stage_item(WarpSmem &ws, const WParams &p, const 
         ws.iu[buf][lane] = it.u;
     }
     if (lane == 0) ws.off[buf][it.cnt] = et;
-    if (fits) {
+    if (fits && it.cnt >= 4) {
+        // Flattened copy, 32 slots per step: slot e = e0 + lane belongs to the
+        // last entry whose offset is <= e.  Entries starting inside the step
+        // are marked by their position; the entry at the step's start is the
+        // last one with offset <= e0.  Every entry has >= 1 edge, so
+        // positions are distinct.
+        const bool has = real && it.l > 0;
+#pragma unroll 4
+        for (int e0 = 0; e0 < et; e0 += 32) {
+            const unsigned starts = __reduce_or_sync(FULL, (has && off > e0 && off < e0 + 32) ? 1u << (off - e0) : 0u);
+            const int j0 = __popc(__ballot_sync(FULL, has && off <= e0)) - 1;
+            const int jj = (j0 + __popc(starts & ((2u << lane) - 1u))) & 31;
+            const int jb = __shfl_sync(FULL, it.b, jj);
+            const int jo = __shfl_sync(FULL, off, jj);
+            const int e = e0 + lane;
+            if (e < et) cp_async4(&ws.stage[buf][e], p.col + jb + (e - jo));
+        }
+    } else if (fits) {
         // long lists
         unsigned big = __ballot_sync(FULL, real && it.l >= 32);
         while (big) {
@@ -626,46 +643,31 @@ __device__ __forceinline__ void process_item_def(WarpSmem &ws, const WParams &p,
         unsigned cm = 0;  // bit k: entry k of this lane is a candidate
 #pragma unroll
         for (int k = 0; k < UA; ++k) cm |= (~__funnelshift_r(w[k], w[k], (unsigned)v[k]) & 1u) << k;
-        // at most two candidates per lane per round into the buffer
+        // one candidate per lane per round into the buffer, placed by ballot
         while (__any_sync(FULL, cm != 0u)) {
-            int k1 = -1, k2 = -1;
+            int k = -1;
             if (cm) {
-                k1 = __ffs(cm) - 1;
+                k = __ffs(cm) - 1;
                 cm &= cm - 1;
             }
-            if (cm) {
-                k2 = __ffs(cm) - 1;
-                cm &= cm - 1;
-            }
-            const int t = (k1 >= 0) + (k2 >= 0);
-            int inc = t;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int y = __shfl_up_sync(FULL, inc, o);
-                if (lane >= o) inc += y;
-            }
-            const int total = __shfl_sync(FULL, inc, 31);
+            const unsigned hasc = __ballot_sync(FULL, k >= 0);
+            const int total = __popc(hasc);
             if (nb + total > CB) claim_deferred<KM>(ws, p, nb, set_out, qo, ocnt, next_level, my_new);
-            int pos = nb + inc - t;
-#pragma unroll
-            for (int j = 0; j < 2; ++j) {
-                const int k = j == 0 ? k1 : k2;
-                if (k >= 0) {
-                    const int e = base + 128 * (k >> 2) + 4 * lane + (k & 3);  // entry inside the item
-                    int u = u_first;
-                    if (cnt > 1) {  // source entry: largest j with off[j] <= e
-                        int lo = 0, hi = cnt;
-                        while (hi - lo > 1) {
-                            const int mid = (lo + hi) >> 1;
-                            if (ws.off[buf][mid] <= e) lo = mid;
-                            else hi = mid;
-                        }
-                        u = ws.iu[buf][lo];
+            if (k >= 0) {
+                const int e = base + 128 * (k >> 2) + 4 * lane + (k & 3);  // entry inside the item
+                int u = u_first;
+                if (cnt > 1) {  // source entry: largest j with off[j] <= e
+                    int lo = 0, hi = cnt;
+                    while (hi - lo > 1) {
+                        const int mid = (lo + hi) >> 1;
+                        if (ws.off[buf][mid] <= e) lo = mid;
+                        else hi = mid;
                     }
-                    ws.cand.v[pos] = stg[e];
-                    ws.cand.u[pos] = u;
-                    ++pos;
+                    u = ws.iu[buf][lo];
                 }
+                const int pos = nb + __popc(hasc & lanemask_lt());
+                ws.cand.v[pos] = stg[e];
+                ws.cand.u[pos] = u;
             }
             nb += total;
         }

@@ -231,6 +231,9 @@ def test_find_knee():
            {"offered_qps": 300, "steady_served_qps": 240}]
     assert bench.find_knee(pts) == 200
     assert bench.find_knee([{"offered_qps": 100, "steady_served_qps": 50}]) is None
+    # a sustained point above a missed one does not count
+    pts.append({"offered_qps": 400, "steady_served_qps": 399})
+    assert bench.find_knee(pts) == 200
 
 
 def test_serving_measurement_retries_once_after_a_stall(short_deadline):
