@@ -209,11 +209,16 @@ __device__ __forceinline__ int stage_item(WarpSmem &ws, const WParams &p, const 
     }
     const bool real = lane < it.cnt;
     const int sl = (real && it.l < 32) ? it.l : 0;
-    int inc = it.l;
+    int inc;
+    if (it.cnt == 1) {  // a hub slice or a one-list unit: no scan needed
+        inc = __shfl_sync(FULL, it.l, 0);
+    } else {
+        inc = it.l;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(FULL, inc, o);
-        if (lane >= o) inc += y;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(FULL, inc, o);
+            if (lane >= o) inc += y;
+        }
     }
     int et = __shfl_sync(FULL, inc, 31);
     const bool fits = et < MAXI;  // cannot fail: units < 2W edges, slices <= W
@@ -253,6 +258,7 @@ __device__ __forceinline__ int stage_item(WarpSmem &ws, const WParams &p, const 
             const int bo = __shfl_sync(FULL, off, src);
             const int bb = __shfl_sync(FULL, it.b, src);
             const int bl = __shfl_sync(FULL, it.l, src);
+#pragma unroll 4
             for (int k = lane; k < bl; k += 32) cp_async4(&ws.stage[buf][bo + k], p.col + bb + k);
         }
         // short lists: each lane copies its own, one edge per step
