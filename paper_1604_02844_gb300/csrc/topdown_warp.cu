@@ -19,12 +19,20 @@
 // Work items of a layer (hub slices, then units) are dealt round-robin to
 // the grid's warps; a layer with fewer items than half the warps deals each
 // hub slice in up to 12 parts of >= 32 edges.  Per item a warp: stages the
-// adjacency into its shared buffer with cp.async (issued one item ahead),
-// tests the visited word of every staged edge (12 loads per lane in flight)
-// and compacts the unvisited ones in place with ballots (pass A), then claims
-// those with atomicOr and queues the winners (pass B).  Descriptors and
+// adjacency into its shared buffer with cp.async, issued one item ahead (an
+// item of >= 4 lists as one flattened copy, fewer lists list by list),
+// padded with the root's id to a multiple of 128 entries; reads the staged
+// entries 16 bytes at a time and tests each one's visited word (12 loads per
+// lane in flight), keeping the candidates as a per-lane bit mask (pass A);
+// puts the candidates and their sources into a per-warp buffer whose claims
+// (atomicOr, two per lane in flight) wait until it fills or the layer ends
+// (pass B); and queues the winners for the next flush.  Descriptors and
 // entries of the next items are prefetched into registers while the current
 // item is processed.
+//
+// Mode 4 (td_thin_kernel) runs the same layer step with 32 lighter warps
+// per SM that read each item's lists straight from memory and claim each
+// candidate at once.
 //
 // Mode 2 (RST) is the atomic-free variant of Alg. 3: pass B sets the bit of
 // the output bitmap with a plain read-modify-write (bits of other vertices in
