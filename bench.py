@@ -758,7 +758,19 @@ def serving_measurement(args, gb, torch, dev):
 
         def run(reqs, rate):
             """Submit reqs at Poisson times (rate None = all at once); returns
-            (elapsed_s, latencies_s)."""
+            (elapsed_s, ticket records).  Python's garbage collector is off
+            meanwhile: a collection pause would hold back submissions and then
+            release them as a burst the arrival process does not have."""
+            import gc
+            gc_was = gc.isenabled()
+            gc.disable()
+            try:
+                return run_submissions(reqs, rate)
+            finally:
+                if gc_was:
+                    gc.enable()
+
+        def run_submissions(reqs, rate):
             import collections
             gaps = rng.exponential(1.0 / rate, size=len(reqs)) if rate else np.zeros(len(reqs))
             inflight = collections.deque()
