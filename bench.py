@@ -32,6 +32,9 @@ import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+# before torch creates the CUDA context: one hardware work queue per serving
+# stream (the library's binding sets the same default when imported first)
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
 METRIC = "BFS GTEPS (harmonic mean, 64 roots) & batched queries/s, p50/p99 vs plain"
 UNIT = "GTEPS"
@@ -901,7 +904,8 @@ def serving_measurement(args, gb, torch, dev):
                   "latency and its split from the library's ticket records (bfs_ticket_info); sustainable "
                   "rate = highest swept offered rate that it and every lower one are served within 5 %; headline at "
                   "0.7 x that rate; plain = bfs_run + sync per query, int32 levels to pinned host memory, "
-                  "back to back"}
+                  "back to back",
+           "cuda_device_max_connections": os.environ.get("CUDA_DEVICE_MAX_CONNECTIONS")}
     if stalls:
         out["stalls_before_this_attempt"] = stalls
     if plain_error:

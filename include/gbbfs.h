@@ -299,6 +299,12 @@ int bfs_run_batch(bfs_graph *g, const int32_t *roots, int32_t k, uint8_t *level_
  * workspace (no other graph holds one that it could give back), the graph's
  * waiting queries fail with BFS_ERR_OOM.  Either way the server and its
  * other graphs keep running.
+ * The graphs' streams should not share CUDA hardware work queues: with the
+ * default of 8 queues, a small graph's result extraction can wait behind a
+ * large graph's round of several milliseconds that sits on the same queue.
+ * Set CUDA_DEVICE_MAX_CONNECTIONS=32 in the environment before the process's
+ * first CUDA call (the Python binding sets this default when it is imported
+ * first).
  */
 bfs_server *bfs_server_create(int64_t hbm_budget_bytes);
 

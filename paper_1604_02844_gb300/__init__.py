@@ -18,6 +18,14 @@ import os
 
 import numpy as np
 
+# The serving loop gives every resident graph its own CUDA stream.  With the
+# default of 8 hardware work queues, those streams (and the caller's) share
+# queues, so a small graph's result extraction waits behind a large graph's
+# multi-millisecond round that happens to sit on the same queue.  32 queues
+# (the most CUDA allows) keep the graphs apart.  The variable only counts
+# before the process's first CUDA call, and an explicit setting is kept.
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libgbbfs.so")
 

@@ -142,3 +142,20 @@ def test_ticket_info_layout_matches_the_header(tmp_path):
     got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
     assert got[0] == ctypes.sizeof(gb.TicketInfo)
     assert got[1:] == [getattr(gb.TicketInfo, f).offset for f, _ in gb.TicketInfo._fields_]
+
+
+def test_binding_sets_one_hardware_queue_per_stream_by_default():
+    """Importing the binding first gives the process 32 CUDA hardware work
+    queues (unless the caller chose a value), so that the serving loop's
+    per-graph streams do not queue behind each other; an explicit setting is
+    left alone."""
+    code = ("import os, sys; sys.path.insert(0, {root!r}); "
+            "import paper_1604_02844_gb300; print(os.environ.get('CUDA_DEVICE_MAX_CONNECTIONS'))")
+    env = {k: v for k, v in os.environ.items() if k != "CUDA_DEVICE_MAX_CONNECTIONS"}
+    out = subprocess.run(["python", "-c", code.format(root=ROOT)], env=env, capture_output=True, text=True,
+                         check=True).stdout.strip()
+    assert out == "32"
+    env["CUDA_DEVICE_MAX_CONNECTIONS"] = "4"
+    out = subprocess.run(["python", "-c", code.format(root=ROOT)], env=env, capture_output=True, text=True,
+                         check=True).stdout.strip()
+    assert out == "4"
