@@ -656,6 +656,12 @@ int ms_alloc(Graph *g, MsWs **out)
     if ((e = cudaMalloc(&w->lane_src, 64 * 4)) != cudaSuccess) return bad(e, "cudaMalloc(lane sources)");
     if ((e = cudaMalloc(&w->lane_row, 64 * 4)) != cudaSuccess) return bad(e, "cudaMalloc(lane rows)");
     if ((e = cudaMallocHost(&w->h_ctrl, sizeof(MsCtrl))) != cudaSuccess) return bad(e, "cudaMallocHost(ms ctrl)");
+    // the mirror's address as the device sees it (pinned memory is mapped
+    // under unified addressing); without one, reads fall back to a copy
+    if (cudaHostGetDevicePointer((void **)&w->d_ctrl_mirror, w->h_ctrl, 0) != cudaSuccess) {
+        w->d_ctrl_mirror = nullptr;
+        (void)cudaGetLastError();
+    }
     if ((e = cudaMallocHost(&w->h_lanes, 2 * 64 * 4)) != cudaSuccess) return bad(e, "cudaMallocHost(lanes)");
     if ((e = cudaStreamCreateWithPriority(&w->stream, cudaStreamNonBlocking, g->stream_priority)) != cudaSuccess)
         return bad(e, "cudaStreamCreate");
@@ -788,11 +794,27 @@ int ms_step_capped(Graph *g, uint32_t max_iters, int max_ctas)
 
 int ms_step(Graph *g, uint32_t max_iters) { return ms_step_capped(g, max_iters, g->opt.max_ctas); }
 
+// The control block written to its pinned host mirror by one warp: stores
+// over the host link, so that the read does not queue on a copy engine
+// behind other graphs' result copies.
+__global__ void ms_ctrl_mirror_kernel(const MsCtrl *__restrict__ c, MsCtrl *mirror)
+{
+    constexpr int kWords = (int)(sizeof(MsCtrl) / 4);
+    const uint32_t *src = reinterpret_cast<const uint32_t *>(c);
+    uint32_t *dst = reinterpret_cast<uint32_t *>(mirror);
+    for (int i = threadIdx.x; i < kWords; i += blockDim.x) dst[i] = __ldcg(src + i);
+}
+
 // Copy the control block to pinned host memory and wait for it.
 int ms_read_ctrl(Graph *g, MsCtrl *out)
 {
     MsWs *w = ws_of(g);
-    GB_CUDA(cudaMemcpyAsync(w->h_ctrl, w->ctrl, sizeof(MsCtrl), cudaMemcpyDeviceToHost, w->stream));
+    if (w->d_ctrl_mirror) {
+        ms_ctrl_mirror_kernel<<<1, 32, 0, w->stream>>>(w->ctrl, w->d_ctrl_mirror);
+        GB_CUDA(cudaGetLastError());
+    } else {
+        GB_CUDA(cudaMemcpyAsync(w->h_ctrl, w->ctrl, sizeof(MsCtrl), cudaMemcpyDeviceToHost, w->stream));
+    }
     GB_CUDA(cudaStreamSynchronize(w->stream));
     *out = *w->h_ctrl;
     return BFS_OK;

@@ -35,6 +35,7 @@ struct MsWs {
     int32_t *lane_src = nullptr;  // [64] staging for inject
     int32_t *lane_row = nullptr;  // [64] staging for extract
     MsCtrl *h_ctrl = nullptr;     // pinned
+    MsCtrl *d_ctrl_mirror = nullptr;  // h_ctrl as the device addresses it (null: read by a copy)
     int32_t *h_lanes = nullptr;   // pinned, 128 entries
     int64_t fcap = 0;
     cudaStream_t stream = nullptr;

@@ -11,8 +11,10 @@
 //      graph's own stream, its grid capped to a share of the GPU so that
 //      several graphs' searches run on the device at the same time);
 //   3. read which lanes still have a frontier; the others are finished:
-//      their level columns are copied to the callers' buffers, the lanes
-//      are reset and become free for the next queries.
+//      their level columns are extracted into staging rows and the lanes
+//      reset, free for the next queries at once; the rows are copied to the
+//      callers' buffers on a second stream while the next round runs, and
+//      the queries complete when that copy has landed.
 // A workspace is created only while the device memory it needs fits the
 // server's budget; a graph with no running or waiting query gives its
 // workspace back when another graph needs the room.  Queries wait at most
@@ -76,6 +78,11 @@ struct GraphState {
     bool has_ws = false;              // (under Server::mu)
     int64_t ws_bytes = 0;
     uint8_t *d_stage = nullptr;       // [64][n] extraction rows
+    cudaStream_t copy_stream = nullptr;  // result copies of finished lanes
+    cudaEvent_t ev_rows = nullptr, ev_copied = nullptr;  // rows extracted; rows copied out
+    unsigned long long pending = 0;   // lanes whose rows are being copied out (under Server::mu)
+    uint64_t pending_ticket[64] = {};
+    int64_t pending_iter = -1;
     MsCtrl last{};                    // counters after the previous round (worker thread only)
     bool have_last = false;
     int64_t room_wait_since = 0;      // start of the current wait for room, 0 = none (under Server::mu)
@@ -118,6 +125,8 @@ struct Server {
     void run(GraphState &gs);
     int round(GraphState &gs);
     int finish(GraphState &gs, unsigned long long mask);
+    int deliver(GraphState &gs);
+    static void free_ws(GraphState &gs);
     int ensure_ws(GraphState &gs);                 // with mu held
     void evict_idle(GraphState &gs, int64_t need);  // with mu held
     int alloc_ws(GraphState &gs);
@@ -132,14 +141,28 @@ void Server::evict_idle(GraphState &gs, int64_t need)
 {
     for (auto &o : graphs) {
         if (need >= 0 && used + need <= budget) break;
-        if (o.get() != &gs && o->has_ws && o->running == 0 && o->waiting.empty()) {
-            ms_free(o->g);
-            cudaFree(o->d_stage);
-            o->d_stage = nullptr;
-            o->has_ws = false;
+        if (o.get() != &gs && o->has_ws && o->running == 0 && o->waiting.empty() && o->pending == 0) {
+            free_ws(*o);
             used -= o->ws_bytes;
         }
     }
+}
+
+// A graph's workspace, staging rows, copy stream and events, given back.
+void Server::free_ws(GraphState &gs)
+{
+    if (gs.copy_stream) {
+        cudaStreamSynchronize(gs.copy_stream);
+        cudaStreamDestroy(gs.copy_stream);
+    }
+    if (gs.ev_rows) cudaEventDestroy(gs.ev_rows);
+    if (gs.ev_copied) cudaEventDestroy(gs.ev_copied);
+    gs.copy_stream = nullptr;
+    gs.ev_rows = gs.ev_copied = nullptr;
+    ms_free(gs.g);
+    cudaFree(gs.d_stage);
+    gs.d_stage = nullptr;
+    gs.has_ws = false;
 }
 
 // The batched-search workspace and the extraction rows of one graph.
@@ -151,11 +174,19 @@ int Server::alloc_ws(GraphState &gs)
         ms_free(gs.g);  // a workspace left without its reset is not reused
         return rc;
     }
-    const cudaError_t e = cudaMalloc(&gs.d_stage, (size_t)64 * gs.g->n);
+    cudaError_t e = cudaMalloc(&gs.d_stage, (size_t)64 * gs.g->n);
     if (e != cudaSuccess) {
         rc = cuda_error(e, "server: extraction rows");
         gs.d_stage = nullptr;
         ms_free(gs.g);
+        return rc;
+    }
+    if ((e = cudaStreamCreateWithPriority(&gs.copy_stream, cudaStreamNonBlocking, gs.g->stream_priority)) !=
+            cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&gs.ev_rows, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&gs.ev_copied, cudaEventDisableTiming)) != cudaSuccess) {
+        rc = cuda_error(e, "server: copy stream");
+        free_ws(gs);
         return rc;
     }
     return BFS_OK;
@@ -217,15 +248,23 @@ void Server::fail_waiting(GraphState &gs, int rc)
     done_cv.notify_all();
 }
 
-// Copy finished lanes to their callers and free the lanes.
+// Finished lanes: their rows go to the staging buffer and the lanes are
+// reset (free for new queries at once); the rows are then copied to the
+// callers' buffers on the copy stream, which overlaps the graph's next round.
+// The staging rows of an earlier delivery are released first.
 int Server::finish(GraphState &gs, unsigned long long mask)
 {
     if (!mask) return BFS_OK;
+    int rc = deliver(gs);
+    if (rc != BFS_OK) return rc;
     int32_t rows[64];
     for (int i = 0; i < 64; ++i) rows[i] = ((mask >> i) & 1ull) ? i : -1;
-    int rc = ms_extract(gs.g, mask, rows, gs.d_stage, gs.g->n, true);
+    rc = ms_extract(gs.g, mask, rows, gs.d_stage, gs.g->n, true);
     if (rc != BFS_OK) return rc;
     MsWs *w = reinterpret_cast<MsWs *>(gs.g->batch_ws);
+    cudaError_t e = cudaEventRecord(gs.ev_rows, w->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(gs.copy_stream, gs.ev_rows, 0);
+    if (e != cudaSuccess) return cuda_error(e, "server: result copy");
     for (int i = 0; i < 64; ++i) {
         if (!((mask >> i) & 1ull)) continue;
         uint8_t *out;
@@ -233,24 +272,42 @@ int Server::finish(GraphState &gs, unsigned long long mask)
             std::lock_guard<std::mutex> lk(mu);
             out = reqs[gs.lane_ticket[i] - 1]->out;
         }
-        cudaError_t e = cudaMemcpyAsync(out, gs.d_stage + (size_t)i * gs.g->n, (size_t)gs.g->n,
-                                        cudaMemcpyDeviceToHost, w->stream);
+        e = cudaMemcpyAsync(out, gs.d_stage + (size_t)i * gs.g->n, (size_t)gs.g->n, cudaMemcpyDeviceToHost,
+                            gs.copy_stream);
         if (e != cudaSuccess) return cuda_error(e, "server: result copy");
     }
-    cudaError_t e = cudaStreamSynchronize(w->stream);
+    e = cudaEventRecord(gs.ev_copied, gs.copy_stream);
+    if (e != cudaSuccess) return cuda_error(e, "server: result copy");
+    std::lock_guard<std::mutex> lk(mu);
+    for (int i = 0; i < 64; ++i) {
+        if (!((mask >> i) & 1ull)) continue;
+        gs.pending_ticket[i] = gs.lane_ticket[i];
+        gs.lane_ticket[i] = 0;
+    }
+    gs.pending_iter = gs.have_last ? (int64_t)gs.last.iter : -1;
+    gs.pending = mask;
+    gs.running &= ~mask;
+    return BFS_OK;
+}
+
+// Wait for the rows being copied out, then complete their queries.
+int Server::deliver(GraphState &gs)
+{
+    if (!gs.pending) return BFS_OK;  // written by this worker only
+    const cudaError_t e = cudaEventSynchronize(gs.ev_copied);
     if (e != cudaSuccess) return cuda_error(e, "server: result copy");
     const int64_t t = now_ns();
     std::lock_guard<std::mutex> lk(mu);
     for (int i = 0; i < 64; ++i) {
-        if (!((mask >> i) & 1ull)) continue;
-        Request &r = *reqs[gs.lane_ticket[i] - 1];
+        if (!((gs.pending >> i) & 1ull)) continue;
+        Request &r = *reqs[gs.pending_ticket[i] - 1];
         r.t_done = t;
-        r.done_iter = gs.have_last ? (int64_t)gs.last.iter : -1;
+        r.done_iter = gs.pending_iter;
         r.status.store(BFS_OK);
-        gs.lane_ticket[i] = 0;
+        gs.pending_ticket[i] = 0;
         --outstanding;
     }
-    gs.running &= ~mask;
+    gs.pending = 0;
     done_cv.notify_all();
     return BFS_OK;
 }
@@ -318,7 +375,7 @@ int Server::round(GraphState &gs)
         const int rc = ms_inject(gs.g, src, add);
         if (rc != BFS_OK) return rc;
     }
-    if (!running) return BFS_OK;
+    if (!running) return deliver(gs);
     // the GPU's CTAs (of 256 threads) shared among the graphs with work, but
     // no more than the graph's size calls for (one CTA per 2^16 adjacency
     // entries), so that small graphs leave room for the large ones; a graph
@@ -330,6 +387,10 @@ int Server::round(GraphState &gs)
     const bool had_last = gs.have_last;
     const unsigned iter_before = gs.last.iter;
     int rc = ms_step_capped(gs.g, iters_per_step, share);
+    if (rc != BFS_OK) return rc;
+    // the previous round's results land while these iterations run
+    gs.phase = PH_FINISH;
+    rc = deliver(gs);
     if (rc != BFS_OK) return rc;
     MsCtrl &st = gs.last;
     gs.phase = PH_READ;
@@ -363,16 +424,28 @@ void Server::fail_all(int rc)
 {
     std::lock_guard<std::mutex> lk(mu);
     if (error == BFS_OK) error = rc;
-    for (auto &r : reqs)
-        if (r->status.load() == BFS_NOT_READY) {
-            r->status.store(rc);
-            r->t_done = now_ns();
+    // queries whose rows are being copied out end when their copy has landed
+    // (their workers see to it as they stop): the buffers are in use till then
+    std::vector<char> copying(reqs.size(), 0);
+    int64_t in_copy = 0;
+    for (auto &gs : graphs)
+        for (int i = 0; i < 64; ++i)
+            if ((gs->pending >> i) & 1ull) {
+                copying[gs->pending_ticket[i] - 1] = 1;
+                ++in_copy;
+            }
+    for (size_t k = 0; k < reqs.size(); ++k) {
+        Request &r = *reqs[k];
+        if (!copying[k] && r.status.load() == BFS_NOT_READY) {
+            r.status.store(rc);
+            r.t_done = now_ns();
         }
+    }
     for (auto &gs : graphs) {
         gs->waiting.clear();
         gs->running = 0;
     }
-    outstanding = 0;
+    outstanding = in_copy;
     done_cv.notify_all();
     for (auto &gs : graphs) gs->cv.notify_all();
 }
@@ -384,7 +457,7 @@ void Server::run(GraphState &gs)
         gs.phase = PH_IDLE;
         {
             std::unique_lock<std::mutex> lk(mu);
-            gs.cv.wait(lk, [&] { return stop || error != BFS_OK || !gs.waiting.empty() || gs.running; });
+            gs.cv.wait(lk, [&] { return stop || error != BFS_OK || !gs.waiting.empty() || gs.running || gs.pending; });
             if (stop || error != BFS_OK) break;
         }
         const int rc = round(gs);
@@ -399,6 +472,20 @@ void Server::run(GraphState &gs)
             fail_all(rc);
             break;
         }
+    }
+    // rows still being copied out: their queries end once the copy has landed
+    if (gs.pending && deliver(gs) != BFS_OK) {
+        std::lock_guard<std::mutex> lk(mu);
+        for (int i = 0; i < 64; ++i) {
+            if (!((gs.pending >> i) & 1ull)) continue;
+            Request &r = *reqs[gs.pending_ticket[i] - 1];
+            r.t_done = now_ns();
+            r.status.store(BFS_ERR_CUDA);
+            gs.pending_ticket[i] = 0;
+            --outstanding;
+        }
+        gs.pending = 0;
+        done_cv.notify_all();
     }
     gs.phase = PH_STOPPED;
 }
@@ -444,10 +531,7 @@ int bfs_server_destroy(bfs_server *sh)
     for (auto &gs : s->graphs)
         if (gs->worker.joinable()) gs->worker.join();
     for (auto &gs : s->graphs) {
-        if (gs->has_ws) {
-            ms_free(gs->g);
-            cudaFree(gs->d_stage);
-        }
+        if (gs->has_ws) Server::free_ws(*gs);
         gs->g->stream_priority = 0;
         gs->g->servers.fetch_sub(1);  // the graph may be destroyed again
     }

@@ -15,10 +15,13 @@
 #include <string.h>
 
 #include <chrono>
+#include <functional>
 #include <map>
 #include <mutex>
+#include <set>
 #include <string>
 #include <thread>
+#include <vector>
 
 namespace fake {
 
@@ -39,6 +42,34 @@ std::atomic<int> jitter_us{0};
 
 static std::mutex alloc_mu;
 static std::map<void *, size_t> allocs;
+
+// Streams that the server creates itself defer their copies until an event
+// recorded after them, or the stream, is synchronised: a copy then reads its
+// source as it is at that moment, so a source overwritten before the wait
+// delivers wrong rows.  The workspace streams (null here) run at once.
+struct Stream {
+    std::mutex mu;
+    std::vector<std::function<void()>> ops;
+    size_t done = 0;
+};
+struct Event {
+    Stream *s = nullptr;
+    size_t upto = 0;
+};
+static std::mutex streams_mu;
+static std::set<const void *> streams;
+
+static Stream *as_stream(cudaStream_t st)
+{
+    std::lock_guard<std::mutex> lk(streams_mu);
+    return streams.count((const void *)st) ? reinterpret_cast<Stream *>(st) : nullptr;
+}
+
+static void run_until(Stream *s, size_t upto)
+{
+    std::lock_guard<std::mutex> lk(s->mu);
+    while (s->done < upto && s->done < s->ops.size()) s->ops[s->done++]();
+}
 
 int depth(int32_t root) { return root == deep_root.load() ? deep_depth.load() : 1 + (int)(root % 9); }
 
@@ -98,12 +129,68 @@ cudaError_t cudaFree(void *p)
     free(p);
     return cudaSuccess;
 }
-cudaError_t cudaMemcpyAsync(void *dst, const void *src, size_t count, cudaMemcpyKind, cudaStream_t)
+cudaError_t cudaMemcpyAsync(void *dst, const void *src, size_t count, cudaMemcpyKind, cudaStream_t st)
 {
+    if (fake::Stream *s = fake::as_stream(st)) {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->ops.push_back([dst, src, count] { memcpy(dst, src, count); });
+        return cudaSuccess;
+    }
     memcpy(dst, src, count);
     return cudaSuccess;
 }
-cudaError_t cudaStreamSynchronize(cudaStream_t) { return cudaSuccess; }
+cudaError_t cudaStreamSynchronize(cudaStream_t st)
+{
+    if (fake::Stream *s = fake::as_stream(st)) fake::run_until(s, SIZE_MAX);
+    return cudaSuccess;
+}
+cudaError_t cudaStreamCreateWithPriority(cudaStream_t *st, unsigned int, int)
+{
+    fake::Stream *s = new fake::Stream();
+    std::lock_guard<std::mutex> lk(fake::streams_mu);
+    fake::streams.insert(s);
+    *st = reinterpret_cast<cudaStream_t>(s);
+    return cudaSuccess;
+}
+cudaError_t cudaStreamDestroy(cudaStream_t st)
+{
+    fake::Stream *s = fake::as_stream(st);
+    if (!s) return cudaErrorInvalidValue;
+    fake::run_until(s, SIZE_MAX);
+    {
+        std::lock_guard<std::mutex> lk(fake::streams_mu);
+        fake::streams.erase(s);
+    }
+    delete s;
+    return cudaSuccess;
+}
+cudaError_t cudaEventCreateWithFlags(cudaEvent_t *ev, unsigned int)
+{
+    *ev = reinterpret_cast<cudaEvent_t>(new fake::Event());
+    return cudaSuccess;
+}
+cudaError_t cudaEventDestroy(cudaEvent_t ev)
+{
+    delete reinterpret_cast<fake::Event *>(ev);
+    return cudaSuccess;
+}
+cudaError_t cudaEventRecord(cudaEvent_t ev, cudaStream_t st)
+{
+    fake::Event *e = reinterpret_cast<fake::Event *>(ev);
+    e->s = fake::as_stream(st);
+    if (e->s) {
+        std::lock_guard<std::mutex> lk(e->s->mu);
+        e->upto = e->s->ops.size();
+    }
+    return cudaSuccess;
+}
+cudaError_t cudaStreamWaitEvent(cudaStream_t, cudaEvent_t, unsigned int) { return cudaSuccess; }
+cudaError_t cudaEventSynchronize(cudaEvent_t ev)
+{
+    fake::Event *e = reinterpret_cast<fake::Event *>(ev);
+    if (e->s) fake::run_until(e->s, e->upto);
+    return cudaSuccess;
+}
 cudaError_t cudaGetLastError(void) { return cudaSuccess; }
 const char *cudaGetErrorName(cudaError_t) { return "fake"; }
 const char *cudaGetErrorString(cudaError_t) { return "fake"; }

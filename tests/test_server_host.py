@@ -18,7 +18,9 @@ loop through its C ABI and check that:
 - the pull-phase hold is kept;
 - a graph registered with a live server cannot be released;
 - a query submitted during another's search joins it, and its record
-  (bfs_ticket_info) says so.
+  (bfs_ticket_info) says so;
+- a query completes only once its result copy has landed (the stand-in's
+  copy streams defer each copy until it is waited for).
 
 The loop's wait for room is shortened to 1.5 s in this build. A stress
 scenario mixes eight graphs, bursts of queries, steps of random length, the
@@ -122,6 +124,8 @@ MUTANTS = [
      "        evict_idle(gs, need);\n", "", "tight_budget"),
     ("no backstop for a search without progress",
      "if (had_last && !add && st.iter == iter_before", "if (false && st.iter == iter_before", "no_progress"),
+    ("queries completed before their result copy has landed",
+     "const cudaError_t e = cudaEventSynchronize(gs.ev_copied);", "const cudaError_t e = cudaSuccess;", "mixed"),
 ]
 
 
@@ -144,11 +148,11 @@ def test_planted_race_is_caught(tmp_path):
     if not _sanitizer_usable(tmp_path, "thread"):
         pytest.skip("g++ cannot build with -fsanitize=thread here")
     src = open(os.path.join(CSRC, "server.cu")).read()
-    old = "    const int64_t t = now_ns();\n    std::lock_guard<std::mutex> lk(mu);\n    for (int i = 0; i < 64; ++i) {"
+    old = "    std::lock_guard<std::mutex> lk(mu);\n    for (int i = 0; i < 64; ++i) {\n" \
+          "        if (!((mask >> i) & 1ull)) continue;\n        gs.pending_ticket[i] = gs.lane_ticket[i];"
     assert src.count(old) == 1, "the planted race no longer applies"
     mutated = tmp_path / "server.cu"
-    mutated.write_text(src.replace(old, "    const int64_t t = now_ns();\n    gs.running &= ~mask;\n"
-                                        "    std::lock_guard<std::mutex> lk(mu);\n    for (int i = 0; i < 64; ++i) {"))
+    mutated.write_text(src.replace(old, "    gs.running &= ~mask;\n" + old))
     exe = _build(str(mutated), str(tmp_path / "racy"), ["-fsanitize=thread"])
     env = dict(os.environ, TSAN_OPTIONS="halt_on_error=1 exitcode=66")
     r = subprocess.run([exe, "stress"], capture_output=True, text=True, timeout=300, env=env)
