@@ -39,6 +39,7 @@ os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 METRIC = "BFS GTEPS (harmonic mean, 64 roots) & batched queries/s, p50/p99 vs plain"
 UNIT = "GTEPS"
 L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
+NOMINAL_HBM_GBS = 7900.0     # HBM3e nominal bandwidth, beside the measured copy peak
 
 
 def parse_args(argv=None):
@@ -1056,7 +1057,9 @@ def run_ours(args):
                          "traffic": profiled_traffic(args, options),
                          "kernel": "td_kernel" if options.get("mode") == 1 else f"td_warp_kernel (mode {options.get('mode')})",
                          "algorithmic_bytes_per_launch": mean_bytes,
-                         "mean_launch_s": mean_t},
+                         "mean_launch_s": mean_t,
+                         "nominal_peak": NOMINAL_HBM_GBS, "frac_of_nominal": achieved / NOMINAL_HBM_GBS,
+                         "gteps_at_peak": value / (achieved / peak) if achieved > 0 else None},
             "cpu_baseline": cpu,
             "e2e": e2e,
             "layer_profile": layers,
