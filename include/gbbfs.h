@@ -219,7 +219,17 @@ int bfs_run_noalloc(const int32_t *row_offsets, const int32_t *col_idx, int64_t 
 
 /* Wait for the graph's last run (any bfs_run of Alg. 1-3) and return its
  * device-side status (BFS_OK, BFS_ERR_TIMEOUT or BFS_ERR_CUDA); clears the
- * status word. */
+ * status word.
+ * Bounds-checking build: the same sources compiled with -DBFS_BOUNDS_CHECK
+ * give a library (libgbbfs_check.so) with this same ABI whose kernels check
+ * the index of every main array access (adjacency, row offsets, visited
+ * bitmap, level, parent, id maps, frontier queues; for the batched search
+ * and the serving loop its frontier, seen words and level rows; modes 0, 2,
+ * 3 and 4).  The first index out of range is recorded with its array and
+ * replaced by 0, so that the access stays inside the array; the call that
+ * reads the status (this one, bfs_run_batch, bfs_run_noalloc, the server's
+ * queries) returns BFS_ERR_CUDA and bfs_last_error() names the array and the
+ * index.  No trap or device assert is used. */
 int bfs_graph_status(bfs_graph *g);
 
 /*

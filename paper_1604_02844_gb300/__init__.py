@@ -116,11 +116,14 @@ class BfsError(RuntimeError):
 _lib = None
 
 
-def load(path: str = LIB_PATH) -> ctypes.CDLL:
-    """Load libgbbfs.so; raises if it has not been built (no fallback)."""
+def load(path: str | None = None) -> ctypes.CDLL:
+    """Load libgbbfs.so (or the library GBBFS_LIB names, e.g. the
+    bounds-checking build libgbbfs_check.so); raises if it has not been built
+    (no fallback)."""
     global _lib
     if _lib is not None:
         return _lib
+    path = path or os.environ.get("GBBFS_LIB") or LIB_PATH
     if not os.path.exists(path):
         raise RuntimeError(f"{path} is missing: build it first (python -c 'import __graft_entry__ as g; "
                            "g.build()'); this package has no CPU fallback")

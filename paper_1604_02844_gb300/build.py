@@ -1,5 +1,10 @@
 """Build libgbbfs.so in-tree: nvcc for sm_103a, one object per .cu, compiled
-in parallel, linked against the shared CUDA runtime."""
+in parallel, linked against the shared CUDA runtime.
+
+build_checked() makes libgbbfs_check.so, the same sources compiled with
+-DBFS_BOUNDS_CHECK: every index of the kernels' main array accesses is
+checked, the first one out of range is recorded with the array it was for,
+and the call that launched the search returns BFS_ERR_CUDA naming it."""
 from __future__ import annotations
 
 import concurrent.futures as cf
@@ -12,6 +17,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgbbfs.so")
+CHECK_OBJ = os.path.join(HERE, "_build", "check")
+CHECK_LIB = os.path.join(HERE, "libgbbfs_check.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O2", "-I", INCLUDE,
@@ -33,21 +40,30 @@ def _deps():
     return _sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(INCLUDE, "*.h"))
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
 def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
-    if not force and up_to_date():
+    return _build(LIB, OBJ, force, verbose, tuple(extra_flags))
+
+
+def build_checked(force: bool = False, verbose: bool = False) -> str:
+    return _build(CHECK_LIB, CHECK_OBJ, force, verbose, ("-DBFS_BOUNDS_CHECK",))
+
+
+def _build(lib: str, objdir: str, force: bool, verbose: bool, extra_flags: tuple) -> str:
+    LIB = lib  # noqa: N806 (the target of this build)
+    if not force and up_to_date(LIB):
         return LIB
-    os.makedirs(OBJ, exist_ok=True)
+    os.makedirs(objdir, exist_ok=True)
     cc = nvcc()
 
     def compile_one(src):
-        obj = os.path.join(OBJ, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(objdir, os.path.basename(src)[:-3] + ".o")
         cmd = [cc, *NVCC_FLAGS, *extra_flags, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:

@@ -52,6 +52,26 @@ __device__ __forceinline__ unsigned lanemask_lt()
     return m;
 }
 
+// Index check of the bounds-checking build (-DBFS_BOUNDS_CHECK): an index
+// outside [0, bound) records the first violation, (site << 48) | index, in the
+// control block's `bounds` word, sets ST_BOUNDS and is replaced by 0, so the
+// access stays inside the array and the search ends with an error status
+// (no trap, no assert).  Without the define GB_IX is the index itself.
+#ifdef BFS_BOUNDS_CHECK
+__device__ __forceinline__ int64_t bounds_checked(int64_t i, int64_t bound, int site, unsigned long long *first,
+                                                  unsigned *status)
+{
+    if (i >= 0 && i < bound) return i;
+    atomicCAS(first, 0ull, ((unsigned long long)site << 48) | ((unsigned long long)i & 0xFFFFFFFFFFFFull));
+    atomicOr(status, ST_BOUNDS);
+    return 0;
+}
+#define GB_IX(i, bound, site, ctrl) \
+    ::gbbfs::dev::bounds_checked((int64_t)(i), (int64_t)(bound), (site), &(ctrl)->bounds, &(ctrl)->status)
+#else
+#define GB_IX(i, bound, site, ctrl) (i)
+#endif
+
 // 4-byte asynchronous global -> shared copy (no register staging).
 __device__ __forceinline__ void cp_async4(void *smem_dst, const void *gmem_src)
 {

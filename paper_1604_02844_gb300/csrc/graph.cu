@@ -416,6 +416,13 @@ int bfs_graph_status(bfs_graph *gh)
     unsigned st = 0;
     GB_CUDA(cudaMemcpy(&st, &g->d_ctrl->status, sizeof(unsigned), cudaMemcpyDeviceToHost));
     if (st) GB_CUDA(cudaMemset(&g->d_ctrl->status, 0, sizeof(unsigned)));
+    if (st & ST_BOUNDS) {
+        unsigned long long w = 0;
+        GB_CUDA(cudaMemcpy(&w, &g->d_ctrl->bounds, sizeof(w), cudaMemcpyDeviceToHost));
+        GB_CUDA(cudaMemset(&g->d_ctrl->bounds, 0, sizeof(w)));
+        return set_error(BFS_ERR_CUDA, std::string("bfs_run: index out of range in ") + bounds_site_name(w) +
+                                           " (index " + std::to_string((long long)(w & 0xFFFFFFFFFFFFull)) + ")");
+    }
     if (st & ST_TIMEOUT) return set_error(BFS_ERR_TIMEOUT, "bfs_run: a device-side wait ran out (BFS_OPT_TIMEOUT_NS)");
     if (st & ST_OVERFLOW) return set_error(BFS_ERR_CUDA, "bfs_run: a frontier queue append ran past its capacity");
     return BFS_OK;

@@ -30,7 +30,29 @@ enum : unsigned {
     ST_TIMEOUT = 1u,   // a bounded wait gave up
     ST_OVERFLOW = 2u,  // a queue append would have run past its capacity
     ST_DEPTH = 4u,     // a level did not fit the uint8 batch encoding
+    ST_BOUNDS = 8u,    // bounds-checking build: an index left its array (first one in `bounds`)
 };
+
+// Where an out-of-range index was caught (bounds-checking build).
+enum : int { BS_COL = 1, BS_ROW = 2, BS_VISITED = 3, BS_LEVEL = 4, BS_PARENT = 5, BS_ORIG = 6, BS_QUEUE = 7,
+             BS_FRONTIER = 8, BS_LANE_ROW = 9 };
+
+// Text of a recorded violation word: (site << 48) | index.
+inline const char *bounds_site_name(unsigned long long w)
+{
+    switch ((int)(w >> 48)) {
+        case BS_COL: return "col_idx";
+        case BS_ROW: return "row_offsets";
+        case BS_VISITED: return "visited bitmap";
+        case BS_LEVEL: return "level";
+        case BS_PARENT: return "parent";
+        case BS_ORIG: return "internal-to-caller id map";
+        case BS_QUEUE: return "frontier queue";
+        case BS_FRONTIER: return "frontier / seen words";
+        case BS_LANE_ROW: return "level rows";
+        default: return "unknown array";
+    }
+}
 
 // ---- control block of the persistent single-source kernels ----------------
 // Counters rotate over three sets: layer d reads set d%3, appends to set
@@ -50,6 +72,7 @@ struct Ctrl {
     unsigned exit_count;             // CTAs that left the kernel
     unsigned status;                 // ST_* bits
     unsigned layers;                 // layers of the last search
+    unsigned long long bounds;       // bounds-checking build: first violation, (site << 48) | index
 };
 
 enum { MODE_WARP = 0, MODE_BINNED = 1, MODE_RESTORE = 2, MODE_HYBRID = 3, MODE_THIN = 4 };

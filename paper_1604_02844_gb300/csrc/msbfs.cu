@@ -192,7 +192,7 @@ __device__ __forceinline__ void ms_expand(const MsParams &p, int par, unsigned n
             u = __ldcg(p.fu[par] + j);
             b = __ldcg(p.fb[par] + j);
             l = __ldcg(p.fl[par] + j);
-            f = __ldcg(p.front[par] + u);
+            f = __ldcg(p.front[par] + GB_IX(u, p.n, BS_FRONTIER, p.ctrl));
             if (l < 0 || l > H) l = 0;  // cannot happen: slices hold <= H edges
         }
         int inc = l;
@@ -217,7 +217,9 @@ __device__ __forceinline__ void ms_expand(const MsParams &p, int par, unsigned n
                 const int jo = __shfl_sync(FULL, off, jj);
                 const unsigned long long jf = __shfl_sync(FULL, f, jj);
                 const int e = bb + lane;
-                v[x] = (e < E) ? __ldg(p.col + jb + (e - jo)) : -1;
+                v[x] = (e < E) ? (int)GB_IX(__ldg(p.col + GB_IX(jb + (e - jo), p.m, BS_COL, p.ctrl)), p.n, BS_FRONTIER,
+                                            p.ctrl)
+                               : -1;
                 nb[x] = jf;
             }
             // lanes that neither reached v before nor already reach it now:
@@ -288,7 +290,7 @@ __device__ __forceinline__ void ms_update(const MsParams &p, int par, unsigned n
 #pragma unroll
         for (int k = 0; k < UU; ++k) {
             const unsigned i = i0 + k * 32 + lane;
-            v[k] = (i < nT) ? __ldcg(p.touched + i) : -1;
+            v[k] = (i < nT) ? (int)GB_IX(__ldcg(p.touched + i), p.n, BS_FRONTIER, p.ctrl) : -1;
         }
 #pragma unroll
         for (int k = 0; k < UU; ++k) {
@@ -308,7 +310,7 @@ __device__ __forceinline__ void ms_update(const MsParams &p, int par, unsigned n
                     p.front[q][v[k]] = nn[k];
                     alive |= nn[k];
                     if (nn[k] & over) atomicOr(&c->status, ST_DEPTH);
-                    const int ov = __ldg(p.orig + v[k]);
+                    const int64_t ov = GB_IX(__ldg(p.orig + v[k]), p.n, BS_LANE_ROW, p.ctrl);
                     merge_levels(reinterpret_cast<uint4 *>(p.lvl + (size_t)ov * 64), nn[k], s_lv);
                     rb[k] = __ldg(p.ro + v[k]);
                     len[k] = __ldg(p.ro + v[k] + 1) - rb[k];
@@ -381,7 +383,7 @@ __device__ __forceinline__ void ms_pull(const MsParams &p, int par, unsigned lon
         unsigned long long acc = 0;
         for (int k0 = b; k0 < e; k0 += 32) {
             const int k = k0 + lane;
-            if (k < e) acc |= __ldcg(p.front[par] + __ldg(p.col + k));
+            if (k < e) acc |= __ldcg(p.front[par] + GB_IX(__ldg(p.col + GB_IX(k, p.m, BS_COL, p.ctrl)), p.n, BS_FRONTIER, p.ctrl));
             if ((warp_or64(acc) & need) == need) break;
         }
         const unsigned long long nn = warp_or64(acc) & need;
@@ -391,7 +393,7 @@ __device__ __forceinline__ void ms_pull(const MsParams &p, int par, unsigned lon
             p.front[q][v] = nn;
             alive |= nn;
             if (nn & over) atomicOr(&c->status, ST_DEPTH);
-            merge_levels(reinterpret_cast<uint4 *>(p.lvl + (size_t)__ldg(p.orig + v) * 64), nn, s_lv);
+            merge_levels(reinterpret_cast<uint4 *>(p.lvl + (size_t)GB_IX(__ldg(p.orig + v), p.n, BS_LANE_ROW, p.ctrl) * 64), nn, s_lv);
         }
         append_frontier(p, q, nn != 0ull && lane == 0, v, b, e - b);
     }
@@ -408,7 +410,7 @@ __device__ __forceinline__ void ms_pull(const MsParams &p, int par, unsigned lon
                 e = __ldg(p.ro + v + 1);
                 unsigned long long acc = 0;
                 for (int k = b; k < e; ++k) {
-                    acc |= __ldcg(p.front[par] + __ldg(p.col + k));
+                    acc |= __ldcg(p.front[par] + GB_IX(__ldg(p.col + GB_IX(k, p.m, BS_COL, p.ctrl)), p.n, BS_FRONTIER, p.ctrl));
                     if ((acc & need) == need) break;
                 }
                 nn = acc & need;
@@ -417,7 +419,7 @@ __device__ __forceinline__ void ms_pull(const MsParams &p, int par, unsigned lon
                     p.front[q][v] = nn;
                     alive |= nn;
                     if (nn & over) atomicOr(&c->status, ST_DEPTH);
-                    merge_levels(reinterpret_cast<uint4 *>(p.lvl + (size_t)__ldg(p.orig + v) * 64), nn, s_lv);
+                    merge_levels(reinterpret_cast<uint4 *>(p.lvl + (size_t)GB_IX(__ldg(p.orig + v), p.n, BS_LANE_ROW, p.ctrl) * 64), nn, s_lv);
                 }
             }
         }
@@ -963,6 +965,9 @@ int ms_run_batch(Graph *g, const int32_t *roots, int32_t k, uint8_t *level_out)
     }
     MsCtrl st;
     if ((rc = ms_read_ctrl(g, &st)) != BFS_OK) return rc;
+    if (st.status & ST_BOUNDS)
+        return set_error(BFS_ERR_CUDA, std::string("bfs_run_batch: index out of range in ") + bounds_site_name(st.bounds) +
+                                           " (index " + std::to_string((long long)(st.bounds & 0xFFFFFFFFFFFFull)) + ")");
     if (st.status & ST_TIMEOUT) return set_error(BFS_ERR_TIMEOUT, "bfs_run_batch: a device-side wait ran out");
     if (st.status & ST_OVERFLOW) return set_error(BFS_ERR_CUDA, "bfs_run_batch: a frontier append ran past its capacity");
     if (st.status & ST_DEPTH) return set_error(BFS_ERR_DEPTH, "bfs_run_batch: a level exceeds 254");

@@ -23,6 +23,7 @@ struct MsCtrl {
     unsigned iter;                // global iteration number (persists across launches)
     unsigned pad;
     unsigned long long alive[2];  // lanes present in frontier buffer p
+    unsigned long long bounds;    // bounds-checking build: first violation, (site << 48) | index
 };
 
 struct MsWs {

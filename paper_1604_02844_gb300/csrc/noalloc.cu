@@ -167,6 +167,12 @@ extern "C" int bfs_run_noalloc(const int32_t *row_offsets, const int32_t *col_id
     GB_CUDA(cudaMemcpy(&st, &g.d_ctrl->status, sizeof(unsigned), cudaMemcpyDeviceToHost));
     if (st) {
         GB_CUDA(cudaMemset(&g.d_ctrl->status, 0, sizeof(unsigned)));
+        if (st & ST_BOUNDS) {
+            unsigned long long w = 0;
+            GB_CUDA(cudaMemcpy(&w, &g.d_ctrl->bounds, sizeof(w), cudaMemcpyDeviceToHost));
+            GB_CUDA(cudaMemset(&g.d_ctrl->bounds, 0, sizeof(w)));
+            return set_error(BFS_ERR_CUDA, std::string("bfs_run_noalloc: index out of range in ") + bounds_site_name(w));
+        }
         if (st & ST_TIMEOUT) return set_error(BFS_ERR_TIMEOUT, "bfs_run_noalloc: a device-side wait ran out");
         return set_error(BFS_ERR_CUDA, "bfs_run_noalloc: a frontier queue append ran past its capacity");
     }

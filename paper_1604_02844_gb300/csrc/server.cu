@@ -402,10 +402,10 @@ int Server::round(GraphState &gs)
     // can never finish, so their queries end with an error instead of the
     // worker relaunching empty searches forever.
     if (had_last && !add && st.iter == iter_before && (running & st.alive[st.iter & 1]) &&
-        !(st.status & (ST_TIMEOUT | ST_OVERFLOW | ST_DEPTH)))
+        !(st.status & (ST_TIMEOUT | ST_OVERFLOW | ST_DEPTH | ST_BOUNDS)))
         return set_error(BFS_ERR_CUDA, "server: a batched search made no progress with queries still running");
     gs.last_iter = (int64_t)st.iter;
-    if (st.status & (ST_TIMEOUT | ST_OVERFLOW | ST_DEPTH))
+    if (st.status & (ST_TIMEOUT | ST_OVERFLOW | ST_DEPTH | ST_BOUNDS))
         return set_error(st.status & ST_DEPTH ? BFS_ERR_DEPTH : (st.status & ST_TIMEOUT ? BFS_ERR_TIMEOUT : BFS_ERR_CUDA),
                          "server: device-side error in a batched search");
     // Backstop: a lane still searching 300 iterations after it joined would

@@ -163,8 +163,9 @@ __device__ __forceinline__ Desc load_desc(const WParams &p, int qi, unsigned nH,
         d.a = (int)(id / split);
         d.c = -1 - (int)(id % split);
     } else {
-        d.a = __ldcg(p.us[qi] + (id - nH * split));
-        d.c = __ldcg(p.uc[qi] + (id - nH * split));
+        const int64_t ui = GB_IX(id - nH * split, p.ucap, BS_QUEUE, p.ctrl);
+        d.a = __ldcg(p.us[qi] + ui);
+        d.c = __ldcg(p.uc[qi] + ui);
     }
     return d;  // checked where it is used, so the loads stay in flight
 }
@@ -177,9 +178,10 @@ __device__ __forceinline__ Item load_item(const WParams &p, int qi, const Desc &
     if (d.c < 0) {
         it.cnt = 1;
         if (lane == 0) {
-            it.u = __ldcg(p.hu[qi] + d.a);
-            it.b = __ldcg(p.hb[qi] + d.a);
-            it.l = __ldcg(p.hl[qi] + d.a);
+            const int64_t hi = GB_IX(d.a, p.hcap, BS_QUEUE, p.ctrl);
+            it.u = __ldcg(p.hu[qi] + hi);
+            it.b = __ldcg(p.hb[qi] + hi);
+            it.l = __ldcg(p.hl[qi] + hi);
             if (split > 1) {  // a part of at least 32 edges
                 const int part = -1 - d.c;
                 const int sub = max(32, (it.l + (int)split - 1) / (int)split);
@@ -192,9 +194,10 @@ __device__ __forceinline__ Item load_item(const WParams &p, int qi, const Desc &
         it.cnt = (d.c < 0 || d.c > 32) ? 0 : d.c;  // a unit holds <= 32 entries
         if (it.cnt != d.c && lane == 0) atomicOr(&p.ctrl->status, ST_OVERFLOW);
         if (lane < it.cnt) {
-            it.u = __ldcg(p.eu[qi] + d.a + lane);
-            it.b = __ldcg(p.eb[qi] + d.a + lane);
-            it.l = __ldcg(p.el[qi] + d.a + lane);
+            const int64_t ei = GB_IX(d.a + lane, p.ecap, BS_QUEUE, p.ctrl);
+            it.u = __ldcg(p.eu[qi] + ei);
+            it.b = __ldcg(p.eb[qi] + ei);
+            it.l = __ldcg(p.el[qi] + ei);
         }
     }
     return it;  // lengths are checked in stage_item, so the loads stay in flight
@@ -255,7 +258,7 @@ __device__ __forceinline__ int stage_item(WarpSmem &ws, const WParams &p, const 
             const int jb = __shfl_sync(FULL, it.b, jj);
             const int jo = __shfl_sync(FULL, off, jj);
             const int e = e0 + lane;
-            if (e < et) cp_async4(&ws.stage[buf][e], p.col + jb + (e - jo));
+            if (e < et) cp_async4(&ws.stage[buf][e], p.col + GB_IX(jb + (e - jo), p.m, BS_COL, p.ctrl));
         }
     } else if (fits) {
         // long lists
@@ -267,12 +270,12 @@ __device__ __forceinline__ int stage_item(WarpSmem &ws, const WParams &p, const 
             const int bb = __shfl_sync(FULL, it.b, src);
             const int bl = __shfl_sync(FULL, it.l, src);
 #pragma unroll 4
-            for (int k = lane; k < bl; k += 32) cp_async4(&ws.stage[buf][bo + k], p.col + bb + k);
+            for (int k = lane; k < bl; k += 32) cp_async4(&ws.stage[buf][bo + k], p.col + GB_IX(bb + k, p.m, BS_COL, p.ctrl));
         }
         // short lists: each lane copies its own, one edge per step
         const int maxl = (int)__reduce_max_sync(FULL, (unsigned)sl);
         for (int k = 0; k < maxl; ++k)
-            if (k < sl) cp_async4(&ws.stage[buf][off + k], p.col + it.b + k);
+            if (k < sl) cp_async4(&ws.stage[buf][off + k], p.col + GB_IX(it.b + k, p.m, BS_COL, p.ctrl));
     }
     // pad to a multiple of 128 entries with the root, whose visited bit is
     // set from the start: the padding never becomes a candidate
@@ -299,11 +302,11 @@ __device__ __forceinline__ void warp_flush(S &ws, const WParams &p, int set_out,
     for (int k = 0; k < PER; ++k) {
         const int i = i0 + k;
         if (i < i1) {
-            const int v = ws.wv[i];
+            const int v = (int)GB_IX(ws.wv[i], p.n, BS_ROW, p.ctrl);
             rb[k] = __ldg(p.ro + v);
             re[k] = __ldg(p.ro + v + 1);
             ov[k] = (FL & FL_LP) ? __ldg(p.orig + v) : 0;
-            ou[k] = ((FL & FL_LP) && p.parent) ? __ldg(p.orig + ws.wu[i]) : 0;
+            ou[k] = ((FL & FL_LP) && p.parent) ? __ldg(p.orig + GB_IX(ws.wu[i], p.n, BS_ORIG, p.ctrl)) : 0;
         }
     }
     int nsmall = 0, nslice = 0;
@@ -313,8 +316,8 @@ __device__ __forceinline__ void warp_flush(S &ws, const WParams &p, int set_out,
         const int i = i0 + k;
         if (i < i1) {
             if (FL & FL_LP) {
-                p.level[ov[k]] = next_level;
-                if (p.parent) p.parent[ov[k]] = ou[k];
+                p.level[GB_IX(ov[k], p.n, BS_LEVEL, p.ctrl)] = next_level;
+                if (p.parent) p.parent[GB_IX(ov[k], p.n, BS_PARENT, p.ctrl)] = ou[k];
             }
             const int len = re[k] - rb[k];
             esum += len;
@@ -506,7 +509,7 @@ __device__ __forceinline__ void process_item_rst(WarpSmem &ws, const WParams &p,
 #pragma unroll
         for (int k = 0; k < UA; ++k) {
             if (v[k] >= 0) {
-                const uint2 x = __ldca(p.vo + ((unsigned)v[k] >> 5));
+                const uint2 x = __ldca(p.vo + GB_IX((unsigned)v[k] >> 5, p.bitmap_words, BS_VISITED, p.ctrl));
                 w[k] = x.x | x.y;
             } else {
                 w[k] = 0xffffffffu;
@@ -563,7 +566,7 @@ __device__ __forceinline__ void process_item_rst(WarpSmem &ws, const WParams &p,
                         if (ws.off[buf][mid] <= e[k]) lo = mid;
                         else hi = mid;
                     }
-                    st_relaxed_s32(p.pint + v[k], ws.iu[buf][lo] - p.n);
+                    st_relaxed_s32(p.pint + GB_IX(v[k], p.n, BS_LEVEL, p.ctrl), ws.iu[buf][lo] - p.n);
                 }
             }
         }
@@ -602,11 +605,11 @@ __device__ __forceinline__ void claim_deferred(S &ws, const WParams &p, int &nb,
     bool w0 = false, w1 = false;
     if (v0 >= 0) {
         const unsigned bit = 1u << (v0 & 31);
-        w0 = !(atomicOr(p.bitmap + ((unsigned)v0 >> 5), bit) & bit);
+        w0 = !(atomicOr(p.bitmap + GB_IX((unsigned)v0 >> 5, p.bitmap_words, BS_VISITED, p.ctrl), bit) & bit);
     }
     if (v1 >= 0) {
         const unsigned bit = 1u << (v1 & 31);
-        w1 = !(atomicOr(p.bitmap + ((unsigned)v1 >> 5), bit) & bit);
+        w1 = !(atomicOr(p.bitmap + GB_IX((unsigned)v1 >> 5, p.bitmap_words, BS_VISITED, p.ctrl), bit) & bit);
     }
     const unsigned m0 = __ballot_sync(FULL, w0), m1 = __ballot_sync(FULL, w1);
     if (w0) {
@@ -653,7 +656,7 @@ __device__ __forceinline__ void process_item_def(WarpSmem &ws, const WParams &p,
         // word can only send an already visited vertex on to the atomicOr
         unsigned w[UA];
 #pragma unroll
-        for (int k = 0; k < UA; ++k) w[k] = __ldca(p.bitmap + ((unsigned)v[k] >> 5));
+        for (int k = 0; k < UA; ++k) w[k] = __ldca(p.bitmap + GB_IX((unsigned)v[k] >> 5, p.bitmap_words, BS_VISITED, p.ctrl));
         unsigned cm = 0;  // bit k: entry k of this lane is a candidate
 #pragma unroll
         for (int k = 0; k < UA; ++k) cm |= (~__funnelshift_r(w[k], w[k], (unsigned)v[k]) & 1u) << k;
@@ -801,7 +804,7 @@ __device__ __forceinline__ void bottom_up(CtaSmem<WPB> &cs, const WParams &p, co
             }
 #pragma unroll
             for (int j = 0; j < VW; ++j) {
-                beg[j] = unv[j] ? __ldg(p.bro + v[j]) : 0;
+                beg[j] = unv[j] ? __ldg(p.bro + GB_IX(v[j], p.n, BS_ROW, p.ctrl)) : 0;
                 end[j] = unv[j] ? __ldg(p.bro + v[j] + 1) : 0;
                 par[j] = -1;
                 e[j] = beg[j];
@@ -821,7 +824,7 @@ __device__ __forceinline__ void bottom_up(CtaSmem<WPB> &cs, const WParams &p, co
                 for (int j = 0; j < VW; ++j)
 #pragma unroll
                     for (int t = 0; t < PK; ++t)
-                        u[j][t] = (act[j] && e[j] + t < end[j]) ? __ldg(p.bcol + e[j] + t) : -1;
+                        u[j][t] = (act[j] && e[j] + t < end[j]) ? __ldg(p.bcol + GB_IX(e[j] + t, p.m, BS_COL, p.ctrl)) : -1;
 #pragma unroll
                 for (int j = 0; j < VW; ++j)
 #pragma unroll
@@ -847,7 +850,7 @@ __device__ __forceinline__ void bottom_up(CtaSmem<WPB> &cs, const WParams &p, co
                     int found = -1;
                     for (int e0 = hb; e0 < he; e0 += 32) {
                         const int ee = e0 + lane;
-                        const int u = ee < he ? __ldg(p.bcol + ee) : -1;
+                        const int u = ee < he ? __ldg(p.bcol + GB_IX(ee, p.m, BS_COL, p.ctrl)) : -1;
                         const bool f = u >= 0 && in_front(sF, ncache, F, u);
                         const unsigned m = __ballot_sync(FULL, f);
                         if (lane == 0) my_edges += (unsigned long long)min(32, he - e0);
@@ -863,16 +866,16 @@ __device__ __forceinline__ void bottom_up(CtaSmem<WPB> &cs, const WParams &p, co
             int ov[VW], ou[VW];
 #pragma unroll
             for (int j = 0; j < VW; ++j) {
-                ov[j] = par[j] >= 0 ? __ldg(p.orig + v[j]) : 0;
-                ou[j] = (par[j] >= 0 && p.parent) ? __ldg(p.orig + par[j]) : 0;
+                ov[j] = par[j] >= 0 ? __ldg(p.orig + GB_IX(v[j], p.n, BS_ORIG, p.ctrl)) : 0;
+                ou[j] = (par[j] >= 0 && p.parent) ? __ldg(p.orig + GB_IX(par[j], p.n, BS_ORIG, p.ctrl)) : 0;
             }
 #pragma unroll
             for (int j = 0; j < VW; ++j) {
                 const bool found = par[j] >= 0;
                 const unsigned m = __ballot_sync(FULL, found);
                 if (found) {
-                    p.level[ov[j]] = next_level;
-                    if (p.parent) p.parent[ov[j]] = ou[j];
+                    p.level[GB_IX(ov[j], p.n, BS_LEVEL, p.ctrl)] = next_level;
+                    if (p.parent) p.parent[GB_IX(ov[j], p.n, BS_PARENT, p.ctrl)] = ou[j];
                     my_mf += (unsigned long long)(end[j] - beg[j]);
                 }
                 if (lane == 0 && src[j] >= 0) {
@@ -1300,18 +1303,19 @@ __device__ __forceinline__ void thin_item(ThinWarpSmem &ws, const WParams &p, co
                 jo = __shfl_sync(FULL, off, jj);
                 u[s] = __shfl_sync(FULL, it.u, jj);
             }
-            v[s] = e < et ? ld_col(p.col + jb + (e - jo)) : -1;
+            v[s] = e < et ? ld_col(p.col + GB_IX(jb + (e - jo), p.m, BS_COL, p.ctrl)) : -1;
         }
         unsigned w[TU];
 #pragma unroll
-        for (int s = 0; s < TU; ++s) w[s] = v[s] >= 0 ? __ldca(p.bitmap + ((unsigned)v[s] >> 5)) : 0xffffffffu;
+        for (int s = 0; s < TU; ++s)
+            w[s] = v[s] >= 0 ? __ldca(p.bitmap + GB_IX((unsigned)v[s] >> 5, p.bitmap_words, BS_VISITED, p.ctrl)) : 0xffffffffu;
         bool win[TU];
 #pragma unroll
         for (int s = 0; s < TU; ++s) {
             win[s] = false;
             if (v[s] >= 0 && !((w[s] >> (v[s] & 31)) & 1u)) {
                 const unsigned bit = 1u << (v[s] & 31);
-                win[s] = !(atomicOr(p.bitmap + ((unsigned)v[s] >> 5), bit) & bit);
+                win[s] = !(atomicOr(p.bitmap + GB_IX((unsigned)v[s] >> 5, p.bitmap_words, BS_VISITED, p.ctrl), bit) & bit);
             }
         }
 #pragma unroll

@@ -159,3 +159,15 @@ def test_binding_sets_one_hardware_queue_per_stream_by_default():
     out = subprocess.run(["python", "-c", code.format(root=ROOT)], env=env, capture_output=True, text=True,
                          check=True).stdout.strip()
     assert out == "4"
+
+
+def test_bounds_checking_build_exports_every_declared_symbol():
+    """The bounds-checking build (-DBFS_BOUNDS_CHECK) compiles from the same
+    sources and exports the same C ABI, so any caller can load it instead
+    (GBBFS_LIB for the Python binding)."""
+    path = lib_build.build_checked()
+    assert path != gb.LIB_PATH
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True, check=True).stdout
+    exported = set(line.split()[-1] for line in out.splitlines() if line.strip())
+    missing = [n for n in header_functions() if n not in exported]
+    assert not missing, missing
