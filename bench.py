@@ -553,7 +553,7 @@ def batched_measurement(args, gb, torch, dev):
     roots = graphgen.pick_roots(ro, args.batched_sources, args.seed + 7)
     n = len(ro) - 1
     g = gb.Graph(ro, col)
-    tuned = g.autotune(gb.BFS_TUNE_BATCH, samples=16)  # batch width and CTA size for this graph
+    tuned = g.autotune(gb.BFS_TUNE_BATCH, samples=16)  # batch width, CTA size, batches in flight
     out = torch.empty((len(roots), n), dtype=torch.uint8, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
     gb.bfs_run_batch(g.handle, roots, out)  # warm-up
@@ -585,6 +585,7 @@ def batched_measurement(args, gb, torch, dev):
     g.close()
     return {"workload": f"kronecker_scale{args.batched_scale}_ef{args.edgefactor}_{len(roots)}sources",
             "batch_width": tuned["batch_width"], "batch_block": tuned["batch_block"],
+            "batch_streams": tuned["batch_streams"],
             "tuned_by": "bfs_graph_autotune(BFS_TUNE_BATCH)", "queries_per_s": len(roots) / t_batch,
             "plain_queries_per_s": len(roots) / t_plain, "speedup_vs_plain": t_plain / t_batch,
             "s_per_1024_batched": t_batch, "s_per_1024_plain": t_plain,

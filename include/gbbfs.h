@@ -106,8 +106,13 @@ typedef enum {
     BFS_OPT_ALPHA = 12,         /* mode 3: a layer runs bottom-up once the frontier's
                                    summed degree exceeds (edges of unreached vertices)
                                    / ALPHA (0 .. 2^30, default 14; 0 = never)          */
-    BFS_OPT_BETA = 13           /* mode 3: back to top-down once the frontier has fewer
+    BFS_OPT_BETA = 13,          /* mode 3: back to top-down once the frontier has fewer
                                    than n / BETA vertices (1 .. 2^30, default 24)       */
+    BFS_OPT_BATCH_STREAMS = 14  /* bfs_run_batch: batches run this many at a time, each
+                                   on its own stream and workspace with an equal share
+                                   of the GPU's CTAs (1..8, default 4); while one batch
+                                   waits at a grid barrier the others run.  Each extra
+                                   stream allocates one more batch workspace          */
 } bfs_option;
 
 /* ---- library ------------------------------------------------------------ */
@@ -259,13 +264,13 @@ int bfs_graph_layer_times(bfs_graph *g, int64_t *t_end_ns, int32_t max_layers);
  *   BFS_TUNE_SINGLE : the current BFS_OPT_MODE's tunables -- BLOCK; in mode 1
  *                     also WARP_DEGREE, CTA_DEGREE and SEGMENT; in mode 3
  *                     also ALPHA and BETA
- *   BFS_TUNE_BATCH  : BATCH_WIDTH and BATCH_BLOCK, timed on bfs_run_batch
- *                     over 128 sources
+ *   BFS_TUNE_BATCH  : BATCH_WIDTH, BATCH_BLOCK and BATCH_STREAMS, timed on
+ *                     bfs_run_batch over 512 sources
  *   BFS_TUNE_MODE   : BFS_OPT_MODE 0 or 3, whichever is faster (applied
  *                     before BFS_TUNE_SINGLE)
  * Results never depend on the options, only the time does.  Synchronous;
  * allocates its own scratch (two int32[n] and, for BFS_TUNE_BATCH, uint8
- * [128][n]) and frees it.  On an error the options are restored and the
+ * [512][n]) and frees it.  On an error the options are restored and the
  * status returned.
  */
 #define BFS_TUNE_SINGLE 1

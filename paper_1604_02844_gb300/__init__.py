@@ -54,6 +54,7 @@ BFS_OPT_BATCH_BLOCK = 10
 BFS_OPT_MODE = 11
 BFS_OPT_ALPHA = 12
 BFS_OPT_BETA = 13
+BFS_OPT_BATCH_STREAMS = 14
 MODE_WARP, MODE_BINNED, MODE_RESTORE, MODE_HYBRID = 0, 1, 2, 3
 
 OPTION_NAMES = {
@@ -65,6 +66,7 @@ OPTION_NAMES = {
     "mode": BFS_OPT_MODE,
     "alpha": BFS_OPT_ALPHA,
     "beta": BFS_OPT_BETA,
+    "batch_streams": BFS_OPT_BATCH_STREAMS,
 }
 
 # every symbol include/gbbfs.h declares, with (restype, argtypes)

@@ -164,13 +164,17 @@ extern "C" int bfs_graph_autotune(bfs_graph *gh, int what, int32_t samples)
         }
     }
     if (what & BFS_TUNE_BATCH) {
-        // the same sources for every width, so that the times compare
+        // the same sources for every width, so that the times compare; 512
+        // of them, so that several batches can be in flight (BATCH_STREAMS)
         std::vector<int32_t> broots;
-        for (int i = 0; i < 128; ++i) broots.push_back(roots[i % roots.size()]);
+        for (int i = 0; i < 512; ++i) broots.push_back(roots[i % roots.size()]);
         if ((e = cudaMalloc(&d_batch, (size_t)broots.size() * (size_t)g->n)) != cudaSuccess)
             return cleanup(cuda_error(e, "bfs_graph_autotune: batch output"));
         auto batch = [&] { return time_batch(gh, broots, d_batch); };
-        if ((rc = descend({{BFS_OPT_BATCH_WIDTH, {16, 32, 64}}, {BFS_OPT_BATCH_BLOCK, {256, 512}}}, batch)) != BFS_OK)
+        if ((rc = descend({{BFS_OPT_BATCH_WIDTH, {16, 32, 64}},
+                           {BFS_OPT_BATCH_BLOCK, {256, 512}},
+                           {BFS_OPT_BATCH_STREAMS, {1, 2, 4, 8}}},
+                          batch)) != BFS_OK)
             return cleanup(rc);
     }
     return cleanup(BFS_OK);

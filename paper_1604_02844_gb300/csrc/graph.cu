@@ -325,6 +325,10 @@ int bfs_graph_set_option(bfs_graph *gh, int option, int64_t v)
         if (v < 1 || v > (1 << 30)) return bad("BETA must be in [1, 2^30]");
         o.beta = (int)v;
         break;
+    case BFS_OPT_BATCH_STREAMS:
+        if (v < 1 || v > 8) return bad("BATCH_STREAMS must be in [1, 8]");
+        o.batch_streams = (int)v;
+        break;
     default:
         return bad("unknown option");
     }
@@ -349,6 +353,7 @@ int64_t bfs_graph_get_option(const bfs_graph *gh, int option)
     case BFS_OPT_MODE: return o.mode;
     case BFS_OPT_ALPHA: return o.alpha;
     case BFS_OPT_BETA: return o.beta;
+    case BFS_OPT_BATCH_STREAMS: return o.batch_streams;
     default: return set_error(BFS_ERR_INVALID_ARG, "bfs_graph_get_option: unknown option");
     }
 }

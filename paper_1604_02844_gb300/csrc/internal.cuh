@@ -88,6 +88,7 @@ struct Options {
     int max_ctas = 0;
     int batch_width = 64;
     int batch_block = 256;  // 8-warp CTAs: the server's grid shares are counted in them
+    int batch_streams = 4;  // bfs_run_batch: batches in flight at once (1 = one after another)
     int mode = MODE_WARP;
     int alpha = 14;  // hybrid: go bottom-up when frontier edges > unexplored edges / alpha
     int beta = 24;   // hybrid: back to top-down when frontier vertices < n / beta

@@ -627,21 +627,52 @@ __global__ void ms_extract_kernel(uint8_t *lvl, unsigned long long *seen, const 
 
 static MsWs *ws_of(Graph *g) { return reinterpret_cast<MsWs *>(g->batch_ws); }
 
-int ms_alloc(Graph *g, MsWs **out)
+// Release one workspace (its peers first).
+static void ws_release(MsWs *w)
 {
-    if (g->batch_ws) {
-        *out = ws_of(g);
-        return BFS_OK;
+    if (!w) return;
+    for (MsWs *&q : w->peer) {
+        ws_release(q);
+        q = nullptr;
     }
+    if (w->stream) cudaStreamSynchronize(w->stream);
+    cudaFree(w->seen);
+    cudaFree(w->next);
+    for (int b = 0; b < 2; ++b) {
+        cudaFree(w->front[b]);
+        for (int j = 0; j < 3; ++j) cudaFree(w->fq[b][j]);
+    }
+    cudaFree(w->lvl);
+    cudaFree(w->touched);
+    cudaFree(w->ctrl);
+    cudaFree(w->start);
+    cudaFree(w->lane_src);
+    cudaFree(w->lane_row);
+    if (w->h_ctrl) cudaFreeHost(w->h_ctrl);
+    if (w->h_lanes) cudaFreeHost(w->h_lanes);
+    if (w->b_exec) cudaGraphExecDestroy(w->b_exec);
+    cudaFree(w->b_lanes);
+    if (w->h_roots) cudaFreeHost(w->h_roots);
+    cudaFree(w->b_tmp);
+    if (w->ev) cudaEventDestroy(w->ev);
+    if (w->stream) cudaStreamDestroy(w->stream);
+    delete w;
+}
+
+// A new workspace with its own stream; nullptr (error recorded) on failure.
+static MsWs *ws_create(Graph *g, int *rc_out)
+{
     MsWs *w = new (std::nothrow) MsWs();
-    if (!w) return set_error(BFS_ERR_OOM, "bfs_run_batch: host allocation");
+    if (!w) {
+        *rc_out = set_error(BFS_ERR_OOM, "bfs_run_batch: host allocation");
+        return nullptr;
+    }
     const int64_t n = g->n;
     w->fcap = n + 2 * (g->m / H) + 2;
-    auto bad = [&](cudaError_t e, const char *what) {
-        const int rc = cuda_error(e, what);
-        g->batch_ws = w;  // let ms_free release what exists
-        ms_free(g);
-        return rc;
+    auto bad = [&](cudaError_t e, const char *what) -> MsWs * {
+        *rc_out = cuda_error(e, what);
+        ws_release(w);
+        return nullptr;
     };
     cudaError_t e;
     if ((e = cudaMalloc(&w->seen, (size_t)n * 8)) != cudaSuccess) return bad(e, "cudaMalloc(seen)");
@@ -667,45 +698,41 @@ int ms_alloc(Graph *g, MsWs **out)
     if ((e = cudaMallocHost(&w->h_lanes, 2 * 64 * 4)) != cudaSuccess) return bad(e, "cudaMallocHost(lanes)");
     if ((e = cudaStreamCreateWithPriority(&w->stream, cudaStreamNonBlocking, g->stream_priority)) != cudaSuccess)
         return bad(e, "cudaStreamCreate");
+    if ((e = cudaEventCreateWithFlags(&w->ev, cudaEventDisableTiming)) != cudaSuccess) return bad(e, "cudaEventCreate");
+    const int rc = ms_reset_ws(g, w);
+    if (rc != BFS_OK) {
+        *rc_out = rc;
+        ws_release(w);
+        return nullptr;
+    }
+    return w;
+}
+
+int ms_alloc(Graph *g, MsWs **out)
+{
+    if (g->batch_ws) {
+        *out = ws_of(g);
+        return BFS_OK;
+    }
+    int rc = BFS_OK;
+    MsWs *w = ws_create(g, &rc);
+    if (!w) return rc;
     g->batch_ws = w;
-    const int rc = ms_reset(g);
-    if (rc != BFS_OK) return rc;
     *out = w;
     return BFS_OK;
 }
 
 void ms_free(Graph *g)
 {
-    MsWs *w = ws_of(g);
-    if (!w) return;
-    if (w->stream) cudaStreamSynchronize(w->stream);
-    cudaFree(w->seen);
-    cudaFree(w->next);
-    for (int b = 0; b < 2; ++b) {
-        cudaFree(w->front[b]);
-        for (int j = 0; j < 3; ++j) cudaFree(w->fq[b][j]);
-    }
-    cudaFree(w->lvl);
-    cudaFree(w->touched);
-    cudaFree(w->ctrl);
-    cudaFree(w->start);
-    cudaFree(w->lane_src);
-    cudaFree(w->lane_row);
-    if (w->h_ctrl) cudaFreeHost(w->h_ctrl);
-    if (w->h_lanes) cudaFreeHost(w->h_lanes);
-    if (w->b_exec) cudaGraphExecDestroy(w->b_exec);
-    cudaFree(w->b_lanes);
-    if (w->h_roots) cudaFreeHost(w->h_roots);
-    cudaFree(w->b_tmp);
-    if (w->stream) cudaStreamDestroy(w->stream);
-    delete w;
+    ws_release(ws_of(g));
     g->batch_ws = nullptr;
 }
 
 // All lanes free: clear the bit words, levels 0xFF, counters zero.
-int ms_reset(Graph *g)
+int ms_reset(Graph *g) { return ms_reset_ws(g, ws_of(g)); }
+
+int ms_reset_ws(Graph *g, MsWs *w)
 {
-    MsWs *w = ws_of(g);
     const int64_t n = g->n;
     cudaStream_t s = w->stream;
     GB_CUDA(cudaMemsetAsync(w->seen, 0, (size_t)n * 8, s));
@@ -766,18 +793,35 @@ int ms_inject(Graph *g, const int32_t *lane_src_caller, unsigned long long mask)
     return BFS_OK;
 }
 
+// CTAs of ms_kernel<MS_WPB> that fit on the GPU at once (up to 32 warps
+// per SM); 0 with the error recorded if none fits.
+template <int MS_WPB>
+static int ms_full_grid(Graph *g)
+{
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ms_kernel<MS_WPB>, MS_WPB * 32, 0);
+    if (e != cudaSuccess) {
+        cuda_error(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor(ms_kernel)");
+        return 0;
+    }
+    if (per_sm < 1) {
+        set_error(BFS_ERR_CUDA, "ms_kernel: no CTA fits on an SM");
+        return 0;
+    }
+    return std::min(per_sm, 32 / MS_WPB) * g->num_sms;
+}
+
+static int ms_full_grid(Graph *g) { return g->opt.batch_block == 512 ? ms_full_grid<16>(g) : ms_full_grid<8>(g); }
+
 // One cooperative launch of ms_kernel with CTAs of MS_WPB warps.
 template <int MS_WPB>
 static int launch_ms(Graph *g, MsWs *w, const MsParams &prm, int max_ctas)
 {
     auto kern = ms_kernel<MS_WPB>;
-    int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, MS_WPB * 32, 0);
-    if (e != cudaSuccess) return cuda_error(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor(ms_kernel)");
-    if (per_sm < 1) return set_error(BFS_ERR_CUDA, "ms_kernel: no CTA fits on an SM");
-    per_sm = std::min(per_sm, 32 / MS_WPB);  // up to 32 warps per SM
-    int grid = per_sm * g->num_sms;
+    int grid = ms_full_grid<MS_WPB>(g);
+    if (grid < 1) return bfs_last_status() < 0 ? bfs_last_status() : BFS_ERR_CUDA;
     if (max_ctas > 0) grid = std::min(grid, max_ctas);
+    cudaError_t e;
     MsParams p = prm;
     void *args[] = {&p};
     e = cudaLaunchCooperativeKernel((const void *)kern, dim3(grid), dim3(MS_WPB * 32), args, 0, w->stream);
@@ -787,12 +831,13 @@ static int launch_ms(Graph *g, MsWs *w, const MsParams &prm, int max_ctas)
 
 // Run up to max_iters iterations (stops early when no lane has a frontier),
 // with at most max_ctas CTAs (0 = as many as fit) of BATCH_BLOCK threads.
-int ms_step_capped(Graph *g, uint32_t max_iters, int max_ctas)
+static int ms_step_ws(Graph *g, MsWs *w, uint32_t max_iters, int max_ctas)
 {
-    MsWs *w = ws_of(g);
     const MsParams p = make_params(g, w, max_iters);
     return g->opt.batch_block == 512 ? launch_ms<16>(g, w, p, max_ctas) : launch_ms<8>(g, w, p, max_ctas);
 }
+
+int ms_step_capped(Graph *g, uint32_t max_iters, int max_ctas) { return ms_step_ws(g, ws_of(g), max_iters, max_ctas); }
 
 int ms_step(Graph *g, uint32_t max_iters) { return ms_step_capped(g, max_iters, g->opt.max_ctas); }
 
@@ -808,9 +853,8 @@ __global__ void ms_ctrl_mirror_kernel(const MsCtrl *__restrict__ c, MsCtrl *mirr
 }
 
 // Copy the control block to pinned host memory and wait for it.
-int ms_read_ctrl(Graph *g, MsCtrl *out)
+static int ms_read_ctrl_ws(MsWs *w, MsCtrl *out)
 {
-    MsWs *w = ws_of(g);
     if (w->d_ctrl_mirror) {
         ms_ctrl_mirror_kernel<<<1, 32, 0, w->stream>>>(w->ctrl, w->d_ctrl_mirror);
         GB_CUDA(cudaGetLastError());
@@ -821,6 +865,8 @@ int ms_read_ctrl(Graph *g, MsCtrl *out)
     *out = *w->h_ctrl;
     return BFS_OK;
 }
+
+int ms_read_ctrl(Graph *g, MsCtrl *out) { return ms_read_ctrl_ws(ws_of(g), out); }
 
 // Level columns of the lanes in `mask` -> rows of `out` (device memory,
 // out_stride bytes apart; lane_row_host[lane] = row, -1 = skip); with
@@ -862,7 +908,7 @@ __global__ void batch_lanes_kernel(const int32_t *__restrict__ roots, const int3
 // inject the lanes from device memory, run to completion, extract the level
 // rows with lane recycling (which leaves the workspace clean for the next
 // batch) and, for host outputs, copy the rows back.  No host round trip.
-static int enqueue_batches(Graph *g, MsWs *w, int32_t k, uint8_t *level_out, bool out_dev, uint8_t *d_out)
+static int enqueue_batches(Graph *g, MsWs *w, int32_t k, uint8_t *level_out, bool out_dev, int groups, int cap)
 {
     const int64_t n = g->n;
     cudaStream_t s = w->stream;
@@ -872,20 +918,38 @@ static int enqueue_batches(Graph *g, MsWs *w, int32_t k, uint8_t *level_out, boo
     batch_lanes_kernel<<<(unsigned)((k + 255) / 256), 256, 0, s>>>(d_roots, g->d_perm, k, out_dev ? 1 : 0, width, d_src,
                                                                  d_rows);
     GB_CUDA(cudaGetLastError());
-    int rc = ms_reset(g);
-    if (rc != BFS_OK) return rc;
-    const MsParams p0 = make_params(g, w, 0);
-    for (int32_t b0 = 0; b0 < k; b0 += width) {
-        const int kb = std::min<int32_t>(width, k - b0);
-        const unsigned long long mask = (kb == 64) ? ~0ull : ((1ull << kb) - 1ull);
-        ms_inject_kernel<<<8, 256, 0, s>>>(p0, d_src + b0, mask, w->start);
-        GB_CUDA(cudaGetLastError());
-        if ((rc = ms_step(g, 0x7FFFFFFFu)) != BFS_OK) return rc;
-        ms_extract_kernel<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(w->lvl, w->seen, g->d_perm, n, mask, d_rows + b0,
-                                                                     d_out, n, 1, w->ctrl);
-        GB_CUDA(cudaGetLastError());
-        if (!out_dev)
-            GB_CUDA(cudaMemcpyAsync(level_out + (size_t)b0 * n, d_out, (size_t)kb * n, cudaMemcpyDeviceToHost, s));
+    // the other groups start once the sources are mapped (fork) ...
+    if (groups > 1) {
+        GB_CUDA(cudaEventRecord(w->ev, s));
+        for (int gi = 1; gi < groups; ++gi) GB_CUDA(cudaStreamWaitEvent(w->peer[gi - 1]->stream, w->ev, 0));
+    }
+    // ... and batch b runs on group b % groups, each group's batches in turn
+    const int nb = (int)((k + width - 1) / width);
+    for (int gi = 0; gi < groups; ++gi) {
+        MsWs *wg = gi == 0 ? w : w->peer[gi - 1];
+        cudaStream_t sg = wg->stream;
+        int rc = ms_reset_ws(g, wg);
+        if (rc != BFS_OK) return rc;
+        uint8_t *d_out = out_dev ? level_out : wg->b_tmp;
+        const MsParams p0 = make_params(g, wg, 0);
+        for (int b = gi; b < nb; b += groups) {
+            const int32_t b0 = (int32_t)b * width;
+            const int kb = std::min<int32_t>(width, k - b0);
+            const unsigned long long mask = (kb == 64) ? ~0ull : ((1ull << kb) - 1ull);
+            ms_inject_kernel<<<8, 256, 0, sg>>>(p0, d_src + b0, mask, wg->start);
+            GB_CUDA(cudaGetLastError());
+            if ((rc = ms_step_ws(g, wg, 0x7FFFFFFFu, cap)) != BFS_OK) return rc;
+            ms_extract_kernel<<<(unsigned)((n + 127) / 128), 128, 0, sg>>>(wg->lvl, wg->seen, g->d_perm, n, mask,
+                                                                          d_rows + b0, d_out, n, 1, wg->ctrl);
+            GB_CUDA(cudaGetLastError());
+            if (!out_dev)
+                GB_CUDA(cudaMemcpyAsync(level_out + (size_t)b0 * n, d_out, (size_t)kb * n, cudaMemcpyDeviceToHost, sg));
+        }
+    }
+    // (join) the first stream waits for the others
+    for (int gi = 1; gi < groups; ++gi) {
+        GB_CUDA(cudaEventRecord(w->peer[gi - 1]->ev, w->peer[gi - 1]->stream));
+        GB_CUDA(cudaStreamWaitEvent(s, w->peer[gi - 1]->ev, 0));
     }
     return BFS_OK;
 }
@@ -906,12 +970,27 @@ int ms_run_batch(Graph *g, const int32_t *roots, int32_t k, uint8_t *level_out)
     cudaStream_t s = w->stream;
     const bool out_dev = is_device_pointer(level_out);
     const int width = g->opt.batch_width;
+    // batches run `groups` at a time, each group on its own workspace and
+    // stream with an equal share of the GPU
+    const int nb = (int)((k + width - 1) / width);
+    const int groups = std::max(1, std::min(std::min(g->opt.batch_streams, kMaxBatchStreams), nb));
+    const int full = ms_full_grid(g);
+    if (full < 1) return bfs_last_status() < 0 ? bfs_last_status() : BFS_ERR_CUDA;
+    const int grid = g->opt.max_ctas > 0 ? std::min(g->opt.max_ctas, full) : full;
+    const int cap = std::max(1, grid / groups);
     // buffers sized for this call (a new buffer invalidates the captured graph)
     auto drop_graph = [&] {
         if (w->b_exec) cudaGraphExecDestroy(w->b_exec);
         w->b_exec = nullptr;
         w->b_key = MsWs::Key{};
     };
+    for (int gi = 1; gi < groups; ++gi)
+        if (!w->peer[gi - 1]) {
+            drop_graph();
+            MsWs *q = ws_create(g, &rc);
+            if (!q) return rc;
+            w->peer[gi - 1] = q;
+        }
     if (w->b_cap < k) {
         drop_graph();
         cudaFree(w->b_lanes);
@@ -923,15 +1002,17 @@ int ms_run_batch(Graph *g, const int32_t *roots, int32_t k, uint8_t *level_out)
         GB_CUDA(cudaMallocHost(&w->h_roots, (size_t)k * 4));
         w->b_cap = k;
     }
-    if (!out_dev && w->b_tmp_width < width) {
-        drop_graph();
-        cudaFree(w->b_tmp);
-        w->b_tmp = nullptr;
-        w->b_tmp_width = 0;
-        GB_CUDA(cudaMalloc(&w->b_tmp, (size_t)width * n));
-        w->b_tmp_width = width;
+    for (int gi = 0; gi < groups && !out_dev; ++gi) {
+        MsWs *wg = gi == 0 ? w : w->peer[gi - 1];
+        if (wg->b_tmp_width < width) {  // each group's staging rows for host outputs
+            drop_graph();
+            cudaFree(wg->b_tmp);
+            wg->b_tmp = nullptr;
+            wg->b_tmp_width = 0;
+            GB_CUDA(cudaMalloc(&wg->b_tmp, (size_t)width * n));
+            wg->b_tmp_width = width;
+        }
     }
-    uint8_t *d_out = out_dev ? level_out : w->b_tmp;
     memcpy(w->h_roots, roots, (size_t)k * 4);
 
     MsWs::Key key;
@@ -941,13 +1022,14 @@ int ms_run_batch(Graph *g, const int32_t *roots, int32_t k, uint8_t *level_out)
     key.width = width;
     key.block = g->opt.batch_block;
     key.max_ctas = g->opt.max_ctas;
+    key.streams = groups;
     key.timeout_ns = g->opt.timeout_ns;
     if (!(w->b_exec && w->b_key == key)) {
         drop_graph();
         cudaGraph_t graph = nullptr;
         bool captured = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
         if (captured) {
-            const int erc = enqueue_batches(g, w, k, level_out, out_dev, d_out);
+            const int erc = enqueue_batches(g, w, k, level_out, out_dev, groups, cap);
             captured = cudaStreamEndCapture(s, &graph) == cudaSuccess && erc == BFS_OK && graph;
             if (captured) captured = cudaGraphInstantiate(&w->b_exec, graph, 0) == cudaSuccess;
             if (graph) cudaGraphDestroy(graph);
@@ -959,18 +1041,29 @@ int ms_run_batch(Graph *g, const int32_t *roots, int32_t k, uint8_t *level_out)
     }
     if (w->b_exec) {
         GB_CUDA(cudaGraphLaunch(w->b_exec, s));
-    } else if ((rc = enqueue_batches(g, w, k, level_out, out_dev, d_out)) != BFS_OK) {
+    } else if ((rc = enqueue_batches(g, w, k, level_out, out_dev, groups, cap)) != BFS_OK) {
         cudaStreamSynchronize(s);
+        for (int gi = 1; gi < groups; ++gi) cudaStreamSynchronize(w->peer[gi - 1]->stream);
         return rc;
     }
-    MsCtrl st;
-    if ((rc = ms_read_ctrl(g, &st)) != BFS_OK) return rc;
-    if (st.status & ST_BOUNDS)
-        return set_error(BFS_ERR_CUDA, std::string("bfs_run_batch: index out of range in ") + bounds_site_name(st.bounds) +
-                                           " (index " + std::to_string((long long)(st.bounds & 0xFFFFFFFFFFFFull)) + ")");
-    if (st.status & ST_TIMEOUT) return set_error(BFS_ERR_TIMEOUT, "bfs_run_batch: a device-side wait ran out");
-    if (st.status & ST_OVERFLOW) return set_error(BFS_ERR_CUDA, "bfs_run_batch: a frontier append ran past its capacity");
-    if (st.status & ST_DEPTH) return set_error(BFS_ERR_DEPTH, "bfs_run_batch: a level exceeds 254");
+    // every group's status, read once all groups are done: the first stream
+    // has joined the others (a replayed graph runs every group on it)
+    GB_CUDA(cudaStreamSynchronize(s));
+    unsigned status = 0;
+    unsigned long long bounds = 0;
+    for (int gi = 0; gi < groups; ++gi) {
+        MsWs *wg = gi == 0 ? w : w->peer[gi - 1];
+        MsCtrl st;
+        if ((rc = ms_read_ctrl_ws(wg, &st)) != BFS_OK) return rc;
+        status |= st.status;
+        if (st.bounds) bounds = st.bounds;
+    }
+    if (status & ST_BOUNDS)
+        return set_error(BFS_ERR_CUDA, std::string("bfs_run_batch: index out of range in ") + bounds_site_name(bounds) +
+                                           " (index " + std::to_string((long long)(bounds & 0xFFFFFFFFFFFFull)) + ")");
+    if (status & ST_TIMEOUT) return set_error(BFS_ERR_TIMEOUT, "bfs_run_batch: a device-side wait ran out");
+    if (status & ST_OVERFLOW) return set_error(BFS_ERR_CUDA, "bfs_run_batch: a frontier append ran past its capacity");
+    if (status & ST_DEPTH) return set_error(BFS_ERR_DEPTH, "bfs_run_batch: a level exceeds 254");
     return BFS_OK;
 }
 

@@ -26,6 +26,8 @@ struct MsCtrl {
     unsigned long long bounds;    // bounds-checking build: first violation, (site << 48) | index
 };
 
+constexpr int kMaxBatchStreams = 8;  // BFS_OPT_BATCH_STREAMS upper bound
+
 struct MsWs {
     unsigned long long *seen = nullptr, *next = nullptr, *front[2] = {};
     uint8_t *lvl = nullptr;       // [n][64] levels, caller numbering, 0xFF = unreached
@@ -40,6 +42,8 @@ struct MsWs {
     int32_t *h_lanes = nullptr;   // pinned, 128 entries
     int64_t fcap = 0;
     cudaStream_t stream = nullptr;
+    cudaEvent_t ev = nullptr;     // bfs_run_batch: fork (first workspace) / join (the others)
+    MsWs *peer[kMaxBatchStreams - 1] = {};  // bfs_run_batch: the workspaces of the other streams
     // bfs_run_batch: buffers and the captured launch sequence of the last call shape
     int32_t *b_lanes = nullptr;   // [3][b_cap] roots, internal sources, output rows
     int32_t *h_roots = nullptr;   // pinned staging of the roots
@@ -50,18 +54,19 @@ struct MsWs {
     struct Key {
         int32_t k = -1;
         uint8_t *out = nullptr;
-        int out_dev = 0, width = 0, block = 0, max_ctas = 0;
+        int out_dev = 0, width = 0, block = 0, max_ctas = 0, streams = 0;
         int64_t timeout_ns = 0;
         bool operator==(const Key &o) const
         {
             return k == o.k && out == o.out && out_dev == o.out_dev && width == o.width && block == o.block &&
-                   max_ctas == o.max_ctas && timeout_ns == o.timeout_ns;
+                   max_ctas == o.max_ctas && streams == o.streams && timeout_ns == o.timeout_ns;
         }
     } b_key;
 };
 
 int ms_alloc(Graph *g, MsWs **out);
 int ms_reset(Graph *g);
+int ms_reset_ws(Graph *g, MsWs *w);
 // sources in the caller's numbering, one per lane of `mask`
 int ms_inject(Graph *g, const int32_t *lane_src_caller, unsigned long long mask);
 // up to max_iters iterations, stopping when no lane has a frontier

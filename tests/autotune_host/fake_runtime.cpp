@@ -51,7 +51,9 @@ double single_cost(const gbbfs::Options &o)
 double batch_cost(const gbbfs::Options &o)
 {
     const double w = o.batch_width == 64 ? 4.0 : o.batch_width == 32 ? 8.0 : 12.0;
-    return w - (o.batch_block == 512 ? 2.0 : 0.0);
+    // batches in flight at once help up to four, then the shares get small
+    const double streams = o.batch_streams == 4 ? 0.0 : o.batch_streams == 2 ? 0.5 : 1.0;
+    return w - (o.batch_block == 512 ? 2.0 : 0.0) + streams;
 }
 
 }  // namespace fake
@@ -140,6 +142,7 @@ int bfs_graph_set_option(bfs_graph *gh, int option, int64_t v)
     case BFS_OPT_BETA: o.beta = (int)v; break;
     case BFS_OPT_BATCH_WIDTH: o.batch_width = (int)v; break;
     case BFS_OPT_BATCH_BLOCK: o.batch_block = (int)v; break;
+    case BFS_OPT_BATCH_STREAMS: o.batch_streams = (int)v; break;
     default: return gbbfs::set_error(BFS_ERR_INVALID_ARG, "unknown option");
     }
     return BFS_OK;
@@ -158,6 +161,7 @@ int64_t bfs_graph_get_option(const bfs_graph *gh, int option)
     case BFS_OPT_BETA: return o.beta;
     case BFS_OPT_BATCH_WIDTH: return o.batch_width;
     case BFS_OPT_BATCH_BLOCK: return o.batch_block;
+    case BFS_OPT_BATCH_STREAMS: return o.batch_streams;
     default: return -1;
     }
 }

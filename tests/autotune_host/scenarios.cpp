@@ -139,12 +139,14 @@ void late_failure()
     CHECK(g->opt.block == 512);
 }
 
-// The batched path: width 64 and 512-thread CTAs, timed on the host clock.
+// The batched path: width 64, 512-thread CTAs and four batches in flight,
+// timed on the host clock.
 void batch()
 {
     Graph *g = make_graph();
+    g->opt.batch_streams = 1;  // the descent has to find the four
     CHECK(bfs_graph_autotune(H(g), BFS_TUNE_BATCH, 4) == BFS_OK);
-    CHECK(g->opt.batch_width == 64 && g->opt.batch_block == 512);
+    CHECK(g->opt.batch_width == 64 && g->opt.batch_block == 512 && g->opt.batch_streams == 4);
     CHECK(fake::batch_calls > 0 && fake::roots_run.empty());
 }
 

@@ -79,7 +79,8 @@ import test_bench_host  # noqa: E402  (its stand-in server)
 lib = types.ModuleType("paper_1604_02844_gb300")
 lib.BFS_OK = 0
 lib.BFS_TUNE_BATCH = 2
-lib.OPTION_NAMES = {k: i for i, k in enumerate(["block", "mode", "alpha", "beta", "batch_width", "batch_block"])}
+lib.OPTION_NAMES = {k: i for i, k in enumerate(["block", "mode", "alpha", "beta", "batch_width", "batch_block",
+                                                     "batch_streams"])}
 lib.BfsError = test_bench_host._FakeBfsError
 lib.last_error = lambda: ""
 lib.load = lambda: None
@@ -98,7 +99,8 @@ class _Graph:
     def __init__(self, ro, col, **kw):
         self.ro, self.col = np.asarray(ro), np.asarray(col)
         self.n = len(ro) - 1
-        self.opts = {"block": 512, "mode": 0, "alpha": 14, "beta": 24, "batch_width": 64, "batch_block": 256}
+        self.opts = {"block": 512, "mode": 0, "alpha": 14, "beta": 24, "batch_width": 64, "batch_block": 256,
+                     "batch_streams": 4}
         self.handle = id(self)
         _handles[self.handle] = self
 

@@ -59,6 +59,36 @@ def test_batch_width_and_host_output(width):
     np.testing.assert_array_equal(got_d, ref)
 
 
+@pytest.mark.parametrize("streams", [1, 2, 3, 4, 8])
+def test_batches_in_flight_together(streams):
+    """BATCH_STREAMS: batch b runs on stream b % streams with its own
+    workspace and 1/streams of the grid.  Every row equals the oracle's for
+    device and host outputs, with a partial last batch, fewer batches than
+    streams, and a replay of the captured launch sequence with new sources."""
+    ro, col = graphgen.kronecker(14, 16, 35)
+    n = len(ro) - 1
+    for k in (1, 70, 300):
+        roots = graphgen.pick_roots(ro, k, 35 + k, distinct=False)
+        ref = oracle.bfs_batch(ro, col, roots)
+        with gb.Graph(ro, col, batch_streams=streams, batch_width=32 if k == 300 else 64) as g:
+            np.testing.assert_array_equal(batch_levels(g, roots), ref)
+            np.testing.assert_array_equal(batch_levels(g, roots, on_device=False), ref)
+            out = torch.empty((k, n), dtype=torch.uint8, device="cuda")
+            gb.bfs_run_batch(g.handle, roots, out)  # captured shape: replayed below
+            roots2 = graphgen.pick_roots(ro, k, 99 + k, distinct=False)
+            gb.bfs_run_batch(g.handle, roots2, out)
+            np.testing.assert_array_equal(out.cpu().numpy(), oracle.bfs_batch(ro, col, roots2))
+
+
+def test_batch_streams_option_bounds():
+    ro, col, _ = path_graph(10, 0)
+    with gb.Graph(ro, col) as g:
+        assert g.get_option("batch_streams") == 4
+        for bad in (0, 9):
+            with pytest.raises(gb.BfsError):
+                g.set_option("batch_streams", bad)
+
+
 def test_duplicate_isolated_and_directed_sources():
     rng = np.random.default_rng(4)
     n, ne = 3000, 12000
