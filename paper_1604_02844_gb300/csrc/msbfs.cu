@@ -973,10 +973,11 @@ int ms_run_batch(Graph *g, const int32_t *roots, int32_t k, uint8_t *level_out)
     // batches run `groups` at a time, each group on its own workspace and
     // stream with an equal share of the GPU
     const int nb = (int)((k + width - 1) / width);
-    const int groups = std::max(1, std::min(std::min(g->opt.batch_streams, kMaxBatchStreams), nb));
     const int full = ms_full_grid(g);
     if (full < 1) return bfs_last_status() < 0 ? bfs_last_status() : BFS_ERR_CUDA;
     const int grid = g->opt.max_ctas > 0 ? std::min(g->opt.max_ctas, full) : full;
+    // no more groups than batches or CTAs, so that the groups' grids add up to at most `grid`
+    const int groups = std::max(1, std::min(std::min(std::min(g->opt.batch_streams, kMaxBatchStreams), nb), grid));
     const int cap = std::max(1, grid / groups);
     // buffers sized for this call (a new buffer invalidates the captured graph)
     auto drop_graph = [&] {

@@ -80,7 +80,7 @@ lib = types.ModuleType("paper_1604_02844_gb300")
 lib.BFS_OK = 0
 lib.BFS_TUNE_BATCH = 2
 lib.OPTION_NAMES = {k: i for i, k in enumerate(["block", "mode", "alpha", "beta", "batch_width", "batch_block",
-                                                     "batch_streams"])}
+                                                     "batch_streams", "max_ctas"])}
 lib.BfsError = test_bench_host._FakeBfsError
 lib.last_error = lambda: ""
 lib.load = lambda: None
@@ -100,7 +100,7 @@ class _Graph:
         self.ro, self.col = np.asarray(ro), np.asarray(col)
         self.n = len(ro) - 1
         self.opts = {"block": 512, "mode": 0, "alpha": 14, "beta": 24, "batch_width": 64, "batch_block": 256,
-                     "batch_streams": 4}
+                     "batch_streams": 4, "max_ctas": 0}
         self.handle = id(self)
         _handles[self.handle] = self
 

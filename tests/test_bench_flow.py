@@ -46,6 +46,8 @@ def _check_contract(line):
     assert set(line["clocks"]) >= {"sm_mhz", "sm_max_mhz", "reasons"}
     assert len(line["ablation"]) == 4 and all("error" not in v for v in line["ablation"].values())
     assert line["batched"]["queries_per_s"] > 0 and line["batched"]["uneven_mix"]["queries_per_s"] > 0
+    conc = line["batched"]["uneven_mix"]["concurrent"]
+    assert conc["queries_per_s"] > 0 and conc["levels_match_sequential"] is True
     lp = line["layer_profile"]
     assert "error" not in lp and lp["roots"] == 64 and lp["layers"][0]["d"] == 0
     assert sum(x["edges_share"] for x in lp["layers"]) == pytest.approx(1.0)

@@ -80,6 +80,16 @@ def test_batches_in_flight_together(streams):
             np.testing.assert_array_equal(out.cpu().numpy(), oracle.bfs_batch(ro, col, roots2))
 
 
+def test_batch_streams_with_a_tiny_grid():
+    """MAX_CTAS below BATCH_STREAMS: fewer groups, each with at least one CTA,
+    so the grids still add up to MAX_CTAS."""
+    ro, col = graphgen.kronecker(12, 16, 36)
+    roots = graphgen.pick_roots(ro, 200, 36, distinct=False)
+    for cap in (1, 3):
+        with gb.Graph(ro, col, batch_streams=8, max_ctas=cap) as g:
+            np.testing.assert_array_equal(batch_levels(g, roots), oracle.bfs_batch(ro, col, roots))
+
+
 def test_batch_streams_option_bounds():
     ro, col, _ = path_graph(10, 0)
     with gb.Graph(ro, col) as g:
