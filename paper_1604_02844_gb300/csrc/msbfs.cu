@@ -655,7 +655,6 @@ static void ws_release(MsWs *w)
     if (w->h_roots) cudaFreeHost(w->h_roots);
     cudaFree(w->b_tmp);
     if (w->ev) cudaEventDestroy(w->ev);
-    if (w->ev_done) cudaEventDestroy(w->ev_done);
     if (w->stream) cudaStreamDestroy(w->stream);
     delete w;
 }
@@ -700,8 +699,6 @@ static MsWs *ws_create(Graph *g, int *rc_out)
     if ((e = cudaStreamCreateWithPriority(&w->stream, cudaStreamNonBlocking, g->stream_priority)) != cudaSuccess)
         return bad(e, "cudaStreamCreate");
     if ((e = cudaEventCreateWithFlags(&w->ev, cudaEventDisableTiming)) != cudaSuccess) return bad(e, "cudaEventCreate");
-    if ((e = cudaEventCreateWithFlags(&w->ev_done, cudaEventDisableTiming | cudaEventBlockingSync)) != cudaSuccess)
-        return bad(e, "cudaEventCreate");
     const int rc = ms_reset_ws(g, w);
     if (rc != BFS_OK) {
         *rc_out = rc;
@@ -864,10 +861,7 @@ static int ms_read_ctrl_ws(MsWs *w, MsCtrl *out)
     } else {
         GB_CUDA(cudaMemcpyAsync(w->h_ctrl, w->ctrl, sizeof(MsCtrl), cudaMemcpyDeviceToHost, w->stream));
     }
-    // a blocking wait: the serving loop's worker threads sleep while their
-    // graphs' iterations run instead of each spinning on a host core
-    GB_CUDA(cudaEventRecord(w->ev_done, w->stream));
-    GB_CUDA(cudaEventSynchronize(w->ev_done));
+    GB_CUDA(cudaStreamSynchronize(w->stream));
     *out = *w->h_ctrl;
     return BFS_OK;
 }

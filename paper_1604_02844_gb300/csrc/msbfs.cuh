@@ -43,7 +43,6 @@ struct MsWs {
     int64_t fcap = 0;
     cudaStream_t stream = nullptr;
     cudaEvent_t ev = nullptr;     // bfs_run_batch: fork (first workspace) / join (the others)
-    cudaEvent_t ev_done = nullptr;  // control-block reads: a blocking wait (the host thread sleeps)
     MsWs *peer[kMaxBatchStreams - 1] = {};  // bfs_run_batch: the workspaces of the other streams
     // bfs_run_batch: buffers and the captured launch sequence of the last call shape
     int32_t *b_lanes = nullptr;   // [3][b_cap] roots, internal sources, output rows

@@ -184,7 +184,7 @@ int Server::alloc_ws(GraphState &gs)
     if ((e = cudaStreamCreateWithPriority(&gs.copy_stream, cudaStreamNonBlocking, gs.g->stream_priority)) !=
             cudaSuccess ||
         (e = cudaEventCreateWithFlags(&gs.ev_rows, cudaEventDisableTiming)) != cudaSuccess ||
-        (e = cudaEventCreateWithFlags(&gs.ev_copied, cudaEventDisableTiming | cudaEventBlockingSync)) != cudaSuccess) {
+        (e = cudaEventCreateWithFlags(&gs.ev_copied, cudaEventDisableTiming)) != cudaSuccess) {
         rc = cuda_error(e, "server: copy stream");
         free_ws(gs);
         return rc;
