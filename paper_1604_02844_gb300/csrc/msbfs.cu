@@ -886,6 +886,45 @@ int ms_extract(Graph *g, unsigned long long mask, const int32_t *lane_row_host, 
     return BFS_OK;
 }
 
+// One row per blockIdx.y; 16-byte loads and stores when the row length and
+// the destination allow them, bytes otherwise.
+__global__ void rows_to_host_kernel(const uint8_t *__restrict__ stage, int64_t n, RowsToHost job)
+{
+    const int i = blockIdx.y;
+    const uint8_t *src = stage + (size_t)job.rows[i] * n;
+    uint8_t *dst = job.dst[i];
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if ((n & 15) == 0 && (reinterpret_cast<uintptr_t>(dst) & 15) == 0 && (reinterpret_cast<uintptr_t>(src) & 15) == 0) {
+        const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
+        uint4 *d4 = reinterpret_cast<uint4 *>(dst);
+        for (int64_t k = t0; k < n / 16; k += stride) d4[k] = __ldcg(s4 + k);
+    } else {
+        for (int64_t k = t0; k < n; k += stride) dst[k] = src[k];
+    }
+}
+
+bool ms_host_addressable(const void *p, uint8_t **dev_ptr)
+{
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    if (a.type != cudaMemoryTypeHost || !a.devicePointer) return false;
+    *dev_ptr = static_cast<uint8_t *>(a.devicePointer);
+    return true;
+}
+
+int ms_rows_to_host(const uint8_t *stage, int64_t n, const RowsToHost &job, cudaStream_t stream)
+{
+    if (job.count <= 0) return BFS_OK;
+    const unsigned gx = (unsigned)std::max<int64_t>(1, std::min<int64_t>(64, (n / 16 + 255) / 256));
+    rows_to_host_kernel<<<dim3(gx, (unsigned)job.count), 256, 0, stream>>>(stage, n, job);
+    GB_CUDA(cudaGetLastError());
+    return BFS_OK;
+}
+
 __global__ void map_ids_kernel(int32_t *ids, const int32_t *__restrict__ perm, int k)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;

@@ -77,4 +77,17 @@ int ms_extract(Graph *g, unsigned long long mask, const int32_t *lane_row_host, 
                bool recycle);
 __global__ void map_ids_kernel(int32_t *ids, const int32_t *__restrict__ perm, int k);
 
+// Rows of a staging buffer (row r at stage + r * n) stored by a kernel into
+// host buffers that the device can address (pinned memory under unified
+// addressing): dst[i] receives row rows[i], for i < count.  Asynchronous on
+// `stream`.  Returns false (nothing enqueued) when a destination is not
+// device-addressable, so that the caller copies instead.
+struct RowsToHost {
+    uint8_t *dst[64];
+    int32_t rows[64];
+    int count;
+};
+bool ms_host_addressable(const void *p, uint8_t **dev_ptr);
+int ms_rows_to_host(const uint8_t *stage, int64_t n, const RowsToHost &job, cudaStream_t stream);
+
 }  // namespace gbbfs

@@ -265,6 +265,10 @@ int Server::finish(GraphState &gs, unsigned long long mask)
     cudaError_t e = cudaEventRecord(gs.ev_rows, w->stream);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(gs.copy_stream, gs.ev_rows, 0);
     if (e != cudaSuccess) return cuda_error(e, "server: result copy");
+    // rows for pinned (device-addressable) buffers are stored by one kernel,
+    // the others copied
+    RowsToHost job;
+    job.count = 0;
     for (int i = 0; i < 64; ++i) {
         if (!((mask >> i) & 1ull)) continue;
         uint8_t *out;
@@ -272,10 +276,19 @@ int Server::finish(GraphState &gs, unsigned long long mask)
             std::lock_guard<std::mutex> lk(mu);
             out = reqs[gs.lane_ticket[i] - 1]->out;
         }
+        uint8_t *dev = nullptr;
+        if (ms_host_addressable(out, &dev)) {
+            job.dst[job.count] = dev;
+            job.rows[job.count] = i;
+            ++job.count;
+            continue;
+        }
         e = cudaMemcpyAsync(out, gs.d_stage + (size_t)i * gs.g->n, (size_t)gs.g->n, cudaMemcpyDeviceToHost,
                             gs.copy_stream);
         if (e != cudaSuccess) return cuda_error(e, "server: result copy");
     }
+    rc = ms_rows_to_host(gs.d_stage, gs.g->n, job, gs.copy_stream);
+    if (rc != BFS_OK) return rc;
     e = cudaEventRecord(gs.ev_copied, gs.copy_stream);
     if (e != cudaSuccess) return cuda_error(e, "server: result copy");
     std::lock_guard<std::mutex> lk(mu);

@@ -346,6 +346,26 @@ int ms_read_ctrl(Graph *g, MsCtrl *out)
     return BFS_OK;
 }
 
+// Half of the callers' buffers (by address) count as device-addressable, so
+// that every scenario runs both delivery paths: rows stored by the kernel
+// (deferred on the copy stream like a copy) and rows copied.
+bool ms_host_addressable(const void *p, uint8_t **dev_ptr)
+{
+    if (!((reinterpret_cast<uintptr_t>(p) >> 4) & 1u)) return false;
+    *dev_ptr = static_cast<uint8_t *>(const_cast<void *>(p));
+    return true;
+}
+
+int ms_rows_to_host(const uint8_t *stage, int64_t n, const RowsToHost &job, cudaStream_t stream)
+{
+    for (int i = 0; i < job.count; ++i) {
+        const cudaError_t e = cudaMemcpyAsync(job.dst[i], stage + (size_t)job.rows[i] * n, (size_t)n,
+                                              cudaMemcpyDeviceToHost, stream);
+        if (e != cudaSuccess) return set_error(BFS_ERR_CUDA, "fake: row store");
+    }
+    return BFS_OK;
+}
+
 int ms_extract(Graph *g, unsigned long long mask, const int32_t *row, uint8_t *out, int64_t stride, bool recycle)
 {
     FakeWs *f = fws(g);
