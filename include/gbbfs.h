@@ -339,7 +339,9 @@ int bfs_server_add_graph(bfs_server *s, bfs_graph *g);
 /* Queue one BFS query: the search of Sec. 3 from `root` on graph graph_id,
  * levels only.  level_out: host uint8[n] of that graph (caller-owned),
  * written as in bfs_run_batch (0xFF = unreached); it must stay valid until
- * bfs_poll reports completion or failure.  *ticket receives the query's id
+ * bfs_poll reports completion or failure.  Into page-locked (pinned) memory
+ * the row is stored by a kernel over the host link; into pageable memory it
+ * is copied, which is slower under load.  *ticket receives the query's id
  * (>= 1).  Returns BFS_ERR_INVALID_ARG (NULL pointer, unknown graph, root
  * outside [0, n)), BFS_ERR_BUSY if the graph's workspace can never fit the
  * HBM budget, or the server's error once it has stopped after one. */
