@@ -12,9 +12,10 @@
 //      several graphs' searches run on the device at the same time);
 //   3. read which lanes still have a frontier; the others are finished:
 //      their level columns are extracted into staging rows and the lanes
-//      reset, free for the next queries at once; the rows are copied to the
-//      callers' buffers on a second stream while the next round runs, and
-//      the queries complete when that copy has landed.
+//      reset, free for the next queries at once; on a second stream, while
+//      the next round runs, the rows reach the callers' buffers (stored by
+//      one kernel into pinned buffers, copied into pageable ones), and the
+//      queries complete once they have landed.
 // A workspace is created only while the device memory it needs fits the
 // server's budget; a graph with no running or waiting query gives its
 // workspace back when another graph needs the room.  Queries wait at most
@@ -78,7 +79,7 @@ struct GraphState {
     bool has_ws = false;              // (under Server::mu)
     int64_t ws_bytes = 0;
     uint8_t *d_stage = nullptr;       // [64][n] extraction rows
-    cudaStream_t copy_stream = nullptr;  // result copies of finished lanes
+    cudaStream_t copy_stream = nullptr;  // delivery of finished lanes' rows (kernel stores, copies)
     cudaEvent_t ev_rows = nullptr, ev_copied = nullptr;  // rows extracted; rows copied out
     unsigned long long pending = 0;   // lanes whose rows are being copied out (under Server::mu)
     uint64_t pending_ticket[64] = {};
@@ -249,8 +250,9 @@ void Server::fail_waiting(GraphState &gs, int rc)
 }
 
 // Finished lanes: their rows go to the staging buffer and the lanes are
-// reset (free for new queries at once); the rows are then copied to the
-// callers' buffers on the copy stream, which overlaps the graph's next round.
+// reset (free for new queries at once); the rows then reach the callers'
+// buffers on the copy stream (kernel stores into pinned buffers, copies into
+// pageable ones), which overlaps the graph's next round.
 // The staging rows of an earlier delivery are released first.
 int Server::finish(GraphState &gs, unsigned long long mask)
 {
